@@ -1,0 +1,224 @@
+"""Block Krylov pieces of the vectorised solve (oracle, test-only).
+
+The paper solves the matrix equation (1/tau M + beta K) Y = RHS of
+Eq. matrix-fixed-point-equation with a block Krylov method (Sec. 2.1, and
+Sec. 1 "AX = B ... Block Krylov methods"); it is silent on
+orthogonalisation and preconditioning side. The readings used here and on
+the device are:
+  * block GMRES with restart m (default 30), right preconditioning, X0 = 0;
+  * block classical Gram-Schmidt applied twice (BCGS2) against the basis;
+  * CholQR2 for the new basis block: G = W^T W, upper Cholesky G = R^T R in
+    natural column order, W <- W R^{-1}, done twice; a column whose Cholesky
+    pivot falls to <= defl * G_kk (or G_kk == 0) is deflated: its row of R is
+    zero and its basis column is zero;
+  * the block Hessenberg least-squares problem is reduced by Householder
+    reflectors of length s+1, one per column; the per-column residual
+    estimates are the norms of the last s rows of the rotated right-hand side;
+  * Jacobi: P^{-1} = diag(J)^{-1}; ILU(0): incomplete LU in natural order on
+    the pattern of J (IKJ variant), applied by forward / backward substitution.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.sparse.linalg import spsolve_triangular
+
+
+# --------------------------------------------------------------------------
+# CholQR with deflation
+# --------------------------------------------------------------------------
+def cholesky_deflating(G, defl):
+    """Upper R with G = R^T R (natural order). Deflated rows are zero.
+    Returns (R, deflated mask)."""
+    s = G.shape[0]
+    R = np.zeros_like(G)
+    dead = np.zeros(s, dtype=bool)
+    for k in range(s):
+        d = G[k, k] - np.dot(R[:k, k], R[:k, k])
+        if G[k, k] <= 0.0 or d <= defl * G[k, k]:
+            dead[k] = True
+            continue
+        R[k, k] = np.sqrt(d)
+        for j in range(k + 1, s):
+            R[k, j] = (G[k, j] - np.dot(R[:k, k], R[:k, j])) / R[k, k]
+    return R, dead
+
+
+def cholqr(W, defl=1e-14):
+    """One CholQR pass: W = Q R, Q = W R^{-1} column by column."""
+    G = W.T @ W
+    R, dead = cholesky_deflating(G, defl)
+    s = W.shape[1]
+    Q = np.zeros_like(W)
+    for k in range(s):
+        if dead[k]:
+            continue
+        Q[:, k] = (W[:, k] - Q[:, :k] @ R[:k, k]) / R[k, k]
+    return Q, R
+
+
+def cholqr2(W, defl=1e-14):
+    """CholQR applied twice; R = R2 R1."""
+    Q1, R1 = cholqr(W, defl)
+    Q, R2 = cholqr(Q1, defl)
+    return Q, R2 @ R1
+
+
+def bcgs2(Vs, W):
+    """Two passes of block classical Gram-Schmidt of W against the blocks Vs.
+    Returns (W_orth, H) with W = W_orth + [V] H."""
+    Vm = np.hstack(Vs)
+    H = np.zeros((Vm.shape[1], W.shape[1]))
+    for _ in range(2):
+        Hp = Vm.T @ W
+        W = W - Vm @ Hp
+        H = H + Hp
+    return W, H
+
+
+# --------------------------------------------------------------------------
+# Householder reduction of the block Hessenberg matrix
+# --------------------------------------------------------------------------
+def householder(x):
+    """Unit v and beta with (I - 2 v v^T) x = beta e_1; v = 0 if x = 0."""
+    nx = np.linalg.norm(x)
+    if nx == 0.0:
+        return np.zeros_like(x), 0.0
+    beta = -nx if x[0] >= 0.0 else nx
+    v = x.copy()
+    v[0] -= beta
+    v /= np.linalg.norm(v)
+    return v, beta
+
+
+def apply_reflector(v, Yblk):
+    """Yblk <- (I - 2 v v^T) Yblk (rows of Yblk match v)."""
+    Yblk -= 2.0 * np.outer(v, v @ Yblk)
+
+
+# --------------------------------------------------------------------------
+# Block GMRES(m), right preconditioned
+# --------------------------------------------------------------------------
+def block_gmres(apply_J, apply_Pinv, R, tol, restart=30, maxit=1000, defl=1e-14):
+    """Solve J X = R for X (N x s) to per-column relative residual `tol`.
+
+    apply_J(X) and apply_Pinv(X) act on N x s blocks. Returns (X, info) with
+    info = {iters, restarts, est (final per-column estimates), converged}.
+    """
+    N, s = R.shape
+    X = np.zeros_like(R)
+    r0 = np.linalg.norm(R, axis=0)
+    target = tol * r0
+    its = 0
+    cycles = 0
+    Rc = R.copy()
+    est = r0.copy()
+    converged = bool(np.all(r0 == 0.0))
+    while not converged and its < maxit:
+        cycles += 1
+        V0, S = cholqr2(Rc, defl)
+        V = [V0]
+        m = restart
+        Hb = np.zeros(((m + 1) * s, m * s))
+        G = np.zeros(((m + 1) * s, s))
+        G[:s] = S
+        refl = []
+        j_done = 0
+        for j in range(m):
+            W = apply_J(apply_Pinv(V[j]))
+            W, H = bcgs2(V, W)
+            Vn, Rn = cholqr2(W, defl)
+            col = np.zeros(((m + 1) * s, s))
+            col[:(j + 1) * s] = H
+            col[(j + 1) * s:(j + 2) * s] = Rn
+            for c, v in enumerate(refl):                 # earlier reflectors
+                apply_reflector(v, col[c:c + s + 1])
+            for l in range(s):                           # this block's columns
+                c = j * s + l
+                v, beta = householder(col[c:c + s + 1, l].copy())
+                if l + 1 < s:
+                    apply_reflector(v, col[c:c + s + 1, l + 1:])
+                col[c, l] = beta
+                col[c + 1:c + s + 1, l] = 0.0
+                apply_reflector(v, G[c:c + s + 1])
+                refl.append(v)
+            Hb[:, j * s:(j + 1) * s] = col
+            V.append(Vn)
+            its += 1
+            j_done = j + 1
+            est = np.linalg.norm(G[(j + 1) * s:(j + 2) * s], axis=0)
+            if np.all(est <= target) or its >= maxit:
+                break
+        k = j_done * s
+        Rt = Hb[:k, :k]
+        Y = np.zeros((k, s))
+        scale = np.max(np.abs(np.diag(Rt))) if k else 0.0
+        for i in range(k - 1, -1, -1):                  # back substitution
+            if abs(Rt[i, i]) <= 1e-300 + 1e-14 * scale:
+                continue
+            Y[i] = (G[i] - Rt[i, i + 1:] @ Y[i + 1:]) / Rt[i, i]
+        X = X + apply_Pinv(np.hstack(V[:j_done]) @ Y)
+        converged = bool(np.all(est <= target))
+        if not converged:
+            Rc = R - apply_J(X)
+    return X, {"iters": its, "restarts": cycles, "est": est, "converged": converged}
+
+
+# --------------------------------------------------------------------------
+# Preconditioners
+# --------------------------------------------------------------------------
+def jacobi(J):
+    """P^{-1} X = diag(J)^{-1} X."""
+    d = J.diagonal().copy()
+    return lambda X: X / d[:, None]
+
+
+def ilu0(J):
+    """ILU(0) of CSR J in natural order (IKJ): for each row i and each k < i in
+    its pattern, l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for j > k in both
+    rows' patterns. Returns (L unit lower, U upper) as CSR."""
+    J = sp.csr_matrix(J, dtype=np.float64, copy=True)
+    J.sort_indices()
+    ptr, col, val = J.indptr, J.indices, J.data.copy()
+    n = J.shape[0]
+    diag = np.empty(n, dtype=np.int64)
+    for i in range(n):
+        pos = np.searchsorted(col[ptr[i]:ptr[i + 1]], i)
+        diag[i] = ptr[i] + pos
+    for i in range(n):
+        a, b = ptr[i], ptr[i + 1]
+        where = {int(col[p]): p for p in range(a, b)}
+        for p in range(a, b):
+            k = int(col[p])
+            if k >= i:
+                break
+            val[p] /= val[diag[k]]
+            for q in range(diag[k] + 1, ptr[k + 1]):
+                j = int(col[q])
+                t = where.get(j)
+                if t is not None:
+                    val[t] -= val[p] * val[q]
+    F = sp.csr_matrix((val, col.copy(), ptr.copy()), shape=J.shape)
+    L = sp.tril(F, k=-1, format="csr") + sp.identity(n, format="csr")
+    U = sp.triu(F, k=0, format="csr")
+    L.sort_indices()
+    U.sort_indices()
+    return L, U
+
+
+def ilu0_apply(L, U):
+    """P^{-1} X = U^{-1} L^{-1} X."""
+    def f(X):
+        Y = spsolve_triangular(L, X, lower=True, unit_diagonal=True)
+        return spsolve_triangular(U, Y, lower=False)
+    return f
+
+
+def make_preconditioner(J, kind):
+    if kind == "none":
+        return lambda X: X.copy()
+    if kind == "jacobi":
+        return jacobi(J)
+    if kind == "ilu0":
+        return ilu0_apply(*ilu0(J))
+    raise ValueError(kind)

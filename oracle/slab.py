@@ -1,0 +1,135 @@
+"""Linear time slab: coupled residual, Kronecker system, sequential stepping
+and the splitting / defect-correction solve (oracle, test-only).
+
+* Coupled residual, linear case (Sec. 2.2, residual R(Y) with f = K y - b,
+  sign read as "+ F A2^T", consistent with Eq. matrix-fixed-point-equation):
+      R(Y) = M Y A1^T + (K Y - B) A2^T - B0.
+* Kronecker system, Eq. general-system-time-steps, with the column-stacking
+  vec: [A1 (x) M + A2 (x) K] vec(Y) = [A2 (x) I] vec(B) + vec(B0), using
+  (C (x) M) vec(Y) = vec(M Y C^T).
+* Sequential stepping, Eq. stiffly-accurate-DIRK: one stage at a time,
+  (M/tau + a_kk K) y_k = M y^n / tau - sum_{j<k} a_kj (K y_j - b_j) + a_kk b_k.
+* Slab solve, Eq. matrix-fixed-point-equation written as defect correction:
+      R = R(Y);  solve (alpha M + beta K) V = R;  Y <- Y - V,
+  alpha = A1[0,0], beta = A2[0,0]; stop when every column k has
+  ||R_k||_2 <= tol ||F_k||_2 with F = B A2^T + B0 (absolute if ||F_k|| = 0).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.sparse.linalg import splu
+
+from . import krylov
+
+
+def coupled_residual(K, Mdiag, A1, A2, Y, B=None, B0=None):
+    """R = M Y A1^T + (K Y - B) A2^T - B0 (B, B0 may be None = 0)."""
+    KY = K @ Y
+    if B is not None:
+        KY = KY - B
+    R = (Mdiag[:, None] * Y) @ A1.T + KY @ A2.T
+    if B0 is not None:
+        R = R - B0
+    return R
+
+
+def rhs_F(A2, B=None, B0=None, shape=None):
+    """F = B A2^T + B0."""
+    F = np.zeros(shape) if B is None else B @ A2.T
+    if B0 is not None:
+        F = F + B0
+    return F
+
+
+def vec(X):
+    """Column-stacking vec (Sec. 2.1, read as column stacking)."""
+    return np.asarray(X).reshape(-1, order="F")
+
+
+def unvec(x, n, s):
+    return np.asarray(x).reshape(n, s, order="F")
+
+
+def kron_operator(K, Mdiag, A1, A2):
+    """Dense A1 (x) M + A2 (x) K (tiny grids only)."""
+    Kd = K.toarray() if sp.issparse(K) else np.asarray(K)
+    return np.kron(A1, np.diag(Mdiag)) + np.kron(A2, Kd)
+
+
+def solve_all_at_once_dense(K, Mdiag, A1, A2, B=None, B0=None):
+    """Dense LU solve of the Kronecker system (Eq. general-system-time-steps)."""
+    n, s = K.shape[0], A1.shape[0]
+    F = rhs_F(A2, B, B0, (n, s))
+    y = np.linalg.solve(kron_operator(K, Mdiag, A1, A2), vec(F))
+    return unvec(y, n, s)
+
+
+def sequential_dirk_linear(K, Mdiag, A, tau, y0, Bstages):
+    """Step the stiffly accurate DIRK (Eq. stiffly-accurate-DIRK) one stage at
+    a time. Bstages[:, g] is b(t) at global stage g (0-based, step-major).
+    Returns the stage values (N x #stages); stages with a_kk = 0 are the
+    explicit y^{(n,1)} = y^n."""
+    A = np.asarray(A, dtype=np.float64)
+    m = A.shape[0]
+    N, G = Bstages.shape
+    Y = np.zeros((N, G))
+    yn = np.asarray(y0, dtype=np.float64).copy()
+    Mdg = sp.diags(Mdiag)
+    cache = {}
+    for g in range(G):
+        n, k = divmod(g, m)
+        k += 1
+        akk = A[k - 1, k - 1]
+        rhs = Mdiag * yn / tau + akk * Bstages[:, g]
+        for j in range(1, k):
+            gj = n * m + j - 1
+            rhs -= A[k - 1, j - 1] * (K @ Y[:, gj] - Bstages[:, gj])
+        if akk == 0.0:
+            Y[:, g] = yn
+        else:
+            if akk not in cache:
+                cache[akk] = splu(sp.csc_matrix(Mdg / tau + akk * K))
+            Y[:, g] = cache[akk].solve(rhs)
+        if k == m:
+            yn = Y[:, g].copy()
+    return Y
+
+
+def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
+               precond="jacobi", restart=30, max_outer=200, inner_maxit=2000,
+               exact_inner=False, Y0=None):
+    """The method for a linear slab: defect correction around the splitting
+    (Eq. matrix-splitting, Eq. matrix-fixed-point-equation) with a block GMRES
+    inner solve on J = alpha M + beta K. Returns (Y, info)."""
+    n, s = K.shape[0], A1.shape[0]
+    alpha, beta, _, _ = _split(A1, A2)
+    J = sp.csr_matrix(sp.diags(alpha * Mdiag) + beta * K)
+    J.sort_indices()
+    F = rhs_F(A2, B, B0, (n, s))
+    Fn = np.linalg.norm(F, axis=0)
+    thr = np.where(Fn > 0.0, tol * Fn, tol)
+    Y = np.zeros((n, s)) if Y0 is None else np.array(Y0, dtype=np.float64)
+    Pinv = krylov.make_preconditioner(J, precond)
+    lu = splu(sp.csc_matrix(J)) if exact_inner else None
+    hist, inner_its = [], 0
+    for it in range(max_outer + 1):
+        R = coupled_residual(K, Mdiag, A1, A2, Y, B, B0)
+        rn = np.linalg.norm(R, axis=0)
+        hist.append(rn / np.where(Fn > 0.0, Fn, 1.0))
+        if np.all(rn <= thr) or it == max_outer:
+            break
+        if exact_inner:
+            V = lu.solve(R)
+        else:
+            V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R, inner_tol, restart,
+                                         inner_maxit)
+            inner_its += info["iters"]
+        Y = Y - V
+    return Y, {"outer": len(hist) - 1, "inner": inner_its, "relres": hist[-1],
+               "history": hist, "converged": bool(np.all(rn <= thr))}
+
+
+def _split(A1, A2):
+    from .coupling import splitting
+    return splitting(A1, A2)

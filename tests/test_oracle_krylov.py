@@ -1,0 +1,150 @@
+"""Pins of oracle.krylov: CholQR2, minimal-residual property of block GMRES,
+exact termination, ILU(0) definition (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import fv, krylov
+
+
+def _J(n=6, seed=0, d3=False, tau=0.01):
+    dims = (n, n, n) if d3 else (n, n, 1)
+    rng = np.random.default_rng(seed)
+    D = np.exp(rng.standard_normal(dims[::-1]))
+    K = fv.convdiff_matrix(dims, D, (1.0, 0.5, 0.0))
+    N = int(np.prod(dims))
+    J = sp.csr_matrix(sp.identity(N) / tau + K)
+    J.sort_indices()
+    return J, rng
+
+
+def test_cholqr2_orthonormal_and_factor():
+    rng = np.random.default_rng(1)
+    W = rng.standard_normal((200, 6)) @ np.diag([1, 1e-3, 1, 1e3, 1, 1])
+    Q, R = krylov.cholqr2(W)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(6), atol=1e-13)
+    np.testing.assert_allclose(Q @ R, W, rtol=1e-12, atol=1e-10)
+    assert np.allclose(np.tril(R, -1), 0.0)
+
+
+def test_cholqr_deflates_dependent_columns():
+    rng = np.random.default_rng(2)
+    W = rng.standard_normal((100, 4))
+    W[:, 2] = W[:, 0]                 # duplicate column
+    W[:, 3] = 0.0                     # zero column
+    Q, R = krylov.cholqr2(W)
+    assert np.all(np.isfinite(Q)) and np.all(np.isfinite(R))
+    np.testing.assert_allclose(Q[:, 2], 0.0)
+    np.testing.assert_allclose(Q[:, 3], 0.0)
+    np.testing.assert_allclose(Q @ R, W, atol=1e-12)
+    np.testing.assert_allclose(Q[:, :2].T @ Q[:, :2], np.eye(2), atol=1e-13)
+
+
+def _krylov_min_residual(J, R, k):
+    """Per-column minimum of ||R_i - J Z c|| over the block Krylov space
+    span{R, J R, ..., J^{k-1} R} (explicit basis + least squares)."""
+    blocks = [R]
+    for _ in range(k - 1):
+        blocks.append(J @ blocks[-1])
+    Z = np.hstack(blocks)
+    Zq, _ = np.linalg.qr(Z)
+    JZ = J @ Zq
+    res = []
+    for i in range(R.shape[1]):
+        c, *_ = np.linalg.lstsq(JZ, R[:, i], rcond=None)
+        res.append(np.linalg.norm(R[:, i] - JZ @ c))
+    return np.array(res)
+
+
+@pytest.mark.parametrize("s", [1, 3])
+def test_block_gmres_minimal_residual_property(s):
+    """After k block steps (no restart, no preconditioner) each column's residual
+    is the minimum over the block Krylov space: the defining property of
+    (block) GMRES; for s = 1 this is textbook GMRES."""
+    J, rng = _J(5, 3)
+    R = rng.standard_normal((J.shape[0], s))
+    ident = lambda X: X.copy()
+    for k in (1, 2, 4):
+        X, info = krylov.block_gmres(lambda X: J @ X, ident, R, tol=0.0, restart=30, maxit=k)
+        true = np.linalg.norm(R - J @ X, axis=0)
+        best = _krylov_min_residual(J, R, k)
+        np.testing.assert_allclose(true, best, rtol=1e-7, atol=1e-10)
+        np.testing.assert_allclose(info["est"], true, rtol=1e-7, atol=1e-10)
+
+
+def test_block_gmres_exact_termination_and_diagonal():
+    J, rng = _J(3, 4)                   # N = 9
+    N = J.shape[0]
+    R = rng.standard_normal((N, 3))
+    X, info = krylov.block_gmres(lambda X: J @ X, lambda X: X.copy(), R, tol=1e-12,
+                                 restart=30)
+    assert info["converged"] and info["iters"] <= 3
+    np.testing.assert_allclose(J @ X, R, rtol=1e-9, atol=1e-9)
+    D = sp.diags(rng.uniform(1, 10, 50)).tocsr()
+    R = rng.standard_normal((50, 4))
+    X, info = krylov.block_gmres(lambda X: D @ X, krylov.jacobi(D), R, tol=1e-12)
+    assert info["iters"] == 1
+    np.testing.assert_allclose(D @ X, R, rtol=1e-12)
+
+
+def test_block_gmres_restarted_preconditioned():
+    J, rng = _J(6, 5, d3=True)
+    R = rng.uniform(-1, 1, (J.shape[0], 4))
+    for kind in ("jacobi", "ilu0"):
+        X, info = krylov.block_gmres(lambda X: J @ X, krylov.make_preconditioner(J, kind),
+                                     R, tol=1e-10, restart=5)
+        assert info["converged"]
+        rel = np.linalg.norm(R - J @ X, axis=0) / np.linalg.norm(R, axis=0)
+        assert np.all(rel < 2e-10)
+
+
+def test_block_gmres_zero_and_duplicate_columns():
+    J, rng = _J(5, 6)
+    R = rng.standard_normal((J.shape[0], 4))
+    R[:, 1] = 0.0
+    R[:, 3] = 2.0 * R[:, 0]
+    X, info = krylov.block_gmres(lambda X: J @ X, krylov.jacobi(J), R, tol=1e-10)
+    assert info["converged"] and np.all(np.isfinite(X))
+    np.testing.assert_allclose(X[:, 1], 0.0)
+    np.testing.assert_allclose(X[:, 3], 2.0 * X[:, 0], rtol=1e-8, atol=1e-12)
+
+
+def test_ilu0_tridiagonal_is_exact_lu():
+    n = 30
+    rng = np.random.default_rng(7)
+    T = sp.diags([rng.uniform(-1, 0, n - 1), rng.uniform(3, 4, n), rng.uniform(-1, 0, n - 1)],
+                 [-1, 0, 1], format="csr")
+    L, U = krylov.ilu0(T)
+    np.testing.assert_allclose((L @ U).toarray(), T.toarray(), atol=1e-13)
+    b = rng.standard_normal((n, 2))
+    np.testing.assert_allclose(T @ krylov.ilu0_apply(L, U)(b), b, atol=1e-12)
+
+
+def _dense_ilu0(A):
+    """Brute force ILU(0) on a dense copy with the sparsity mask (IKJ)."""
+    A = A.copy()
+    n = A.shape[0]
+    mask = A != 0
+    for i in range(1, n):
+        for k in range(i):
+            if not mask[i, k]:
+                continue
+            A[i, k] /= A[k, k]
+            for j in range(k + 1, n):
+                if mask[i, j]:
+                    A[i, j] -= A[i, k] * A[k, j]
+    return np.tril(A, -1) + np.eye(n), np.triu(A)
+
+
+def test_ilu0_matches_brute_force_and_pattern_property():
+    J, _ = _J(5, 8, d3=True)
+    L, U = krylov.ilu0(J)
+    Ld, Ud = _dense_ilu0(J.toarray())
+    np.testing.assert_allclose(L.toarray(), Ld, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(U.toarray(), Ud, rtol=1e-12, atol=1e-12)
+    # defining property of ILU(0): (L U)_ij = a_ij on the pattern of A
+    LU = (L @ U).toarray()
+    Jd = J.toarray()
+    mask = Jd != 0
+    np.testing.assert_allclose(LU[mask], Jd[mask], rtol=1e-12, atol=1e-9)
+    assert L.nnz + U.nnz == J.nnz + J.shape[0]

@@ -1,0 +1,146 @@
+"""Pins of oracle.slab: Kronecker identity, all-at-once == sequential
+stepping, nilpotent splitting, slab solve to tolerance (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import coupling, fv, krylov, slab
+
+
+def _problem(n=5, seed=0, v=(1.0, 0.5, 0.0), d3=False):
+    dims = (n, n, n) if d3 else (n, n, 1)
+    rng = np.random.default_rng(seed)
+    D = np.exp(rng.standard_normal(dims[::-1]))
+    K = fv.convdiff_matrix(dims, D, v)
+    Md = 1.0 + 0.5 * rng.random(int(np.prod(dims)))
+    return K, Md, rng
+
+
+def test_kronecker_vec_identity():
+    """(C (x) M) vec(Y) = vec(M Y C^T) for the column-stacking vec."""
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((5, 5))
+    C = rng.standard_normal((3, 3))
+    Y = rng.standard_normal((5, 3))
+    lhs = np.kron(C, M) @ slab.vec(Y)
+    rhs = slab.vec(M @ Y @ C.T)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-13, atol=1e-13)
+    # and the block-diagonal statement of Sec. 2.1: (I (x) A) vec(X) = vec(A X)
+    np.testing.assert_allclose(np.kron(np.eye(3), M) @ slab.vec(Y), slab.vec(M @ Y), atol=1e-13)
+
+
+def test_coupled_residual_is_kronecker_defect():
+    K, Md, rng = _problem(4, 1)
+    n = K.shape[0]
+    s = 3
+    A1 = rng.standard_normal((s, s))
+    A2 = rng.standard_normal((s, s))
+    Y, B, B0 = rng.standard_normal((3, n, s))
+    R = slab.coupled_residual(K, Md, A1, A2, Y, B, B0)
+    Kr = slab.kron_operator(K, Md, A1, A2)
+    rhs = np.kron(A2, np.eye(n)) @ slab.vec(B) + slab.vec(B0)
+    np.testing.assert_allclose(slab.vec(R), Kr @ slab.vec(Y) - rhs, rtol=1e-12, atol=1e-10)
+
+
+@pytest.mark.parametrize("tab,steps", [("ie", 4), ("sdirk2", 3), ("theta", 3)])
+def test_all_at_once_equals_sequential(tab, steps):
+    """Stiffly accurate: the s-step all-at-once solve equals s sequential steps
+    (Eq. time-stepping-matrices-multiple-parallel-time-steps and the identity
+    y^{n+i} = y^{(n+i-1,m)})."""
+    K, Md, rng = _problem(4, 2)
+    n = K.shape[0]
+    tau = 0.05
+    y0 = rng.standard_normal(n)
+    if tab == "ie":
+        A, b, c = coupling.implicit_euler()
+    elif tab == "sdirk2":
+        A, b, c = coupling.sdirk2()
+    else:
+        A, b, c = coupling.theta_method(0.5)
+    m = A.shape[0]
+    Bst = rng.standard_normal((n, steps * m))
+    if tab == "theta":            # b(t^{n+1}) is shared by stages (n,2) and (n+1,1)
+        for k in range(1, steps):
+            Bst[:, 2 * k] = Bst[:, 2 * k - 1]
+    Yseq = slab.sequential_dirk_linear(K, Md, A, tau, y0, Bst)
+    if tab == "theta":
+        A1, A2, e = coupling.multistep_matrices(A, steps, tau, eliminate_first=True)
+        B = Bst[:, 1::2]
+        B0 = np.zeros((n, steps))
+        B0[:, 0] = Md * y0 / tau + e[0] * (Bst[:, 0] - K @ y0)
+        Y = slab.solve_all_at_once_dense(K, Md, A1, A2, B, B0)
+        np.testing.assert_allclose(Y, Yseq[:, 1::2], rtol=1e-10, atol=1e-11)
+    else:
+        A1, A2, _ = coupling.multistep_matrices(A, steps, tau)
+        B0 = np.zeros((n, steps * m))
+        B0[:, :m] = (Md * y0 / tau)[:, None]
+        Y = slab.solve_all_at_once_dense(K, Md, A1, A2, Bst, B0)
+        np.testing.assert_allclose(Y, Yseq, rtol=1e-10, atol=1e-11)
+
+
+def test_fixed_point_exact_after_s_iterations():
+    """With exact inner solves the split-off parts are strictly lower
+    triangular, so column k is exact after k+1 outer iterations and the whole
+    slab after s (derived from Eq. matrix-fixed-point-equation)."""
+    K, Md, rng = _problem(5, 4)
+    n = K.shape[0]
+    s, tau = 5, 0.02
+    A, _, _ = coupling.implicit_euler()
+    A1, A2, _ = coupling.multistep_matrices(A, s, tau)
+    B = rng.standard_normal((n, s))
+    y0 = rng.standard_normal(n)
+    B0 = np.zeros((n, s))
+    B0[:, 0] = Md * y0 / tau
+    Yex = slab.solve_all_at_once_dense(K, Md, A1, A2, B, B0)
+    for outer in range(1, s + 1):
+        Y, info = slab.slab_solve(K, Md, A1, A2, B, B0, tol=0.0, exact_inner=True,
+                                  max_outer=outer)
+        err = np.linalg.norm(Y - Yex, axis=0) / np.linalg.norm(Yex, axis=0)
+        assert np.all(err[:outer] < 1e-12)
+        if outer < s:
+            assert err[outer] > 1e-6
+    # s = 1 needs exactly one outer iteration (Sec. 4.1 remark on s = 1)
+    A1b, A2b, _ = coupling.multistep_matrices(A, 1, tau)
+    Y1, info = slab.slab_solve(K, Md, A1b, A2b, B[:, :1], B0[:, :1], tol=1e-12,
+                               exact_inner=True)
+    assert info["outer"] == 1
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "ilu0"])
+def test_slab_solve_block_gmres_reaches_tolerance(precond):
+    K, Md, rng = _problem(6, 5, d3=True)
+    n = K.shape[0]
+    s, tau = 4, 1e-2
+    A, _, _ = coupling.implicit_euler()
+    A1, A2, _ = coupling.multistep_matrices(A, s, tau)
+    B = rng.uniform(-1, 1, (n, s))
+    Y, info = slab.slab_solve(K, Md, A1, A2, B, None, tol=1e-12, inner_tol=1e-2,
+                              precond=precond, restart=10)
+    assert info["converged"]
+    Yex = slab.sequential_dirk_linear(K, Md, A, tau, np.zeros(n), B)
+    err = np.linalg.norm(Y - Yex, axis=0) / np.linalg.norm(Yex, axis=0)
+    assert np.all(err < 1e-9)
+
+
+def test_planted_transpose_in_coupling_is_caught(monkeypatch):
+    """A plausible mistake (A2 used without transpose in the residual) breaks
+    the all-at-once == sequential pin."""
+    orig = slab.coupled_residual
+
+    def wrong(K, Mdiag, A1, A2, Y, B=None, B0=None):
+        return orig(K, Mdiag, A1.T, A2.T, Y, B, B0)
+
+    K, Md, rng = _problem(4, 6)
+    n = K.shape[0]
+    s, tau = 3, 0.05
+    A, _, _ = coupling.sdirk2()
+    A1, A2, _ = coupling.multistep_matrices(A, 2, tau)
+    y0 = rng.standard_normal(n)
+    Bst = rng.standard_normal((n, 4))
+    B0 = np.zeros((n, 4))
+    B0[:, :2] = (Md * y0 / tau)[:, None]
+    Yseq = slab.sequential_dirk_linear(K, Md, A, tau, y0, Bst)
+    monkeypatch.setattr(slab, "coupled_residual", wrong)
+    Y, info = slab.slab_solve(K, Md, A1, A2, Bst, B0, tol=1e-12, exact_inner=True,
+                              max_outer=30)
+    assert not np.allclose(Y, Yseq, rtol=1e-6)
