@@ -1,0 +1,249 @@
+/*
+ * pint.h -- C ABI of the GB300 (sm_103a) library for the vectorised
+ * parallel-in-time block solve of
+ *     Engwer, Schell & Dreier, "Vectorized Parallel in Time methods for
+ *     low-order discretizations with application to Porous Media problems",
+ *     arXiv 2504.02117.
+ *
+ * Problem (Sec. 1, Eq. problem):  M y'(t) + K y(t) = b(t), M diagonal here.
+ * s coupled time steps / DIRK stages give the matrix equation of
+ * Eq. general-system-time-steps / Eq. time-stepping-matrices-multiple-
+ * parallel-time-steps, in residual form (Sec. 2.2, sign read as "+F A2^T"):
+ *     R(Y) = M Y A1^T + (K Y - B) A2^T - B0,         Y, B, B0, R in R^{N x s}.
+ * It is solved by the splitting of Eq. matrix-splitting and the fixed point of
+ * Eq. matrix-fixed-point-equation, written as defect correction
+ *     R = R(Y);  (alpha M + beta K) V = R  (block GMRES);  Y <- Y - V,
+ * alpha = A1[0][0] (= 1/tau), beta = A2[0][0].
+ *
+ * Conventions
+ *  - Every call returns an int status (PINT_OK = 0 or a PINT_ERR_* code);
+ *    pint_last_error(ctx) returns a message for the last failing call.
+ *  - Block vectors (Y, B, B0, R, ...) are N x s ROW-MAJOR float64 arrays: the
+ *    s values of one row are contiguous (one row = the s "SIMD lanes" of
+ *    Sec. 3, one per coupled step). Unless a call says otherwise they are
+ *    DEVICE pointers, borrowed: the caller owns them and keeps them alive until
+ *    the work enqueued on `stream` has completed. A NULL B or B0 means zero.
+ *  - Small coupling matrices (A1, A2, tableaux) are HOST row-major arrays,
+ *    copied by the call.
+ *  - Handles are opaque and owned by the library; free them with the matching
+ *    *_destroy call. A context serves one device; calls on the same handle
+ *    must not run concurrently from several host threads.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is enqueued on it. Calls documented "synchronous" wait for
+ *    their own work on that stream before returning (they read convergence
+ *    words on the host).
+ *  - Device memory is accounted against the context's hbm_budget; a call that
+ *    would exceed it fails with PINT_ERR_NOMEM before launching anything.
+ */
+#ifndef PINT_H
+#define PINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  PINT_OK = 0,
+  PINT_ERR_INVALID = 1,       /* bad argument (size, NULL, s out of range) */
+  PINT_ERR_NOMEM = 2,         /* budget or cudaMalloc exhausted             */
+  PINT_ERR_CUDA = 3,          /* a CUDA runtime call failed                 */
+  PINT_ERR_NOT_CONVERGED = 4, /* iteration limit reached; stats are filled  */
+  PINT_ERR_BREAKDOWN = 5,     /* NaN/Inf met in a residual or factorisation */
+  PINT_ERR_TIMEOUT = 6        /* a device-side wait exceeded its time limit */
+};
+
+#define PINT_MAX_S 16         /* maximum block width s                      */
+#define PINT_MAX_RESTART 64   /* maximum GMRES restart length               */
+
+enum { PINT_MEM_HOST = 0, PINT_MEM_DEVICE = 1 };
+enum { PINT_PC_NONE = 0, PINT_PC_JACOBI = 1, PINT_PC_ILU0 = 2 };
+/* Arithmetic of the inner block GMRES. Outer residuals, updates, column norms
+ * and the s x s / Hessenberg factorisations are always float64. */
+enum {
+  PINT_FP64 = 0,   /* matrix, vectors, Gram products in float64               */
+  PINT_FP32 = 1,   /* float32 matrix + vectors, float32 products, float64
+                      cross-block Gram reduction; float64 refinement outside */
+  PINT_BF16 = 2    /* as PINT_FP32 but the SpMM matrix values are bfloat16    */
+};
+
+typedef struct pint_ctx_s* pint_ctx;
+typedef struct pint_op_s* pint_op;
+typedef struct pint_problem_s* pint_problem;
+
+typedef struct {
+  double tol;        /* outer: ||R_k||_2 <= tol ||F_k||_2, F = B A2^T + B0   */
+  double inner_tol;  /* inner block GMRES: per-column relative reduction    */
+  int restart;       /* GMRES restart length m, 1..PINT_MAX_RESTART (30)    */
+  int max_outer;     /* outer (defect-correction / Newton) iteration limit  */
+  int max_inner;     /* block Arnoldi steps per inner solve                 */
+  int precond;       /* PINT_PC_*                                           */
+  int precision;     /* PINT_FP64 / PINT_FP32 / PINT_BF16                   */
+  int reserved[3];
+} pint_opts;
+
+typedef struct {
+  int status;                   /* status of the call                        */
+  int outer_its;                /* outer / Newton iterations                 */
+  int inner_its;                /* block Arnoldi steps, all inner solves     */
+  int restarts;                 /* GMRES restart cycles                      */
+  int deflations;               /* CholQR columns deflated                   */
+  int kernel_launches;          /* kernels this call enqueued                */
+  double setup_ms;              /* preconditioner set-up (host clock)        */
+  double solve_ms;              /* whole call (host clock)                   */
+  double col_relres[PINT_MAX_S];/* final ||R_k|| / ||F_k|| per column        */
+} pint_stats;
+
+/* Fill `o` with the defaults: tol 1e-10, inner_tol 1e-2, restart 30,
+ * max_outer 200, max_inner 3000, Jacobi, FP64. */
+void pint_opts_default(pint_opts* o);
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on CUDA device `device`. hbm_budget bounds the device
+ * bytes the library allocates (0 = 90% of free memory). */
+int pint_create(pint_ctx* ctx, int device, size_t hbm_budget);
+int pint_destroy(pint_ctx ctx);
+const char* pint_last_error(pint_ctx ctx);
+/* Device bytes currently held by the library in this context. */
+size_t pint_bytes_in_use(pint_ctx ctx);
+
+/* --------------------------------------------------------------- operator */
+/* Assemble the operator pair (K, M) of Eq. problem. K: CSR with n rows,
+ * int32 rowptr[n+1], colind[nnz] (column indices sorted in each row, the
+ * diagonal present), float64 K_vals[nnz]; M_diag[n] (diagonal mass) or NULL
+ * for M = I. mem_space says where the four arrays live. The library copies
+ * them into its own formats (CSR + SELL-32 slices, float32 / bfloat16
+ * copies). Synchronous. */
+int pint_operator_assemble(pint_ctx ctx, pint_op* op, int64_t n,
+                           const int32_t* rowptr, const int32_t* colind,
+                           const double* K_vals, const double* M_diag,
+                           int mem_space, void* stream);
+/* Same pattern, new values (e.g. a new Jacobian, Algorithm 1). Either
+ * pointer may be NULL to keep the old values. */
+int pint_operator_update_values(pint_op op, const double* K_vals,
+                                const double* M_diag, int mem_space,
+                                void* stream);
+int pint_operator_destroy(pint_op op);
+int64_t pint_operator_nnz(pint_op op);
+
+/* Cell-centred FV operator of -div(D grad u) + div(v u) on [0,1]^d with
+ * nx*ny*nz cells (nz = 1: 2-D; h = 1/nx), natural x-fastest numbering,
+ * homogeneous Dirichlet ghost faces, first-order upwind convection, M = I.
+ * D[n] is the per-cell diffusion coefficient (mem_space). Assembled on the
+ * device. Synchronous. */
+int pint_fv_convdiff(pint_ctx ctx, pint_op* op, int nx, int ny, int nz,
+                     const double* D, double vx, double vy, double vz,
+                     int mem_space, void* stream);
+
+/* --------------------------------------------------------------- coupling */
+/* Set the s x s time-stepping matrices A1, A2 (host, row-major) of
+ * Eq. general-system-time-steps. The splitting of Eq. matrix-splitting uses
+ * alpha = A1[0][0] and beta = A2[0][0]; the inner operator is
+ * J = alpha M + beta K. 1 <= s <= PINT_MAX_S. */
+int pint_set_coupling(pint_op op, int s, const double* A1, const double* A2);
+
+/* Build A1, A2 for `steps` consecutive steps of the m-stage stiffly accurate
+ * DIRK tableau A (m x m, row-major host) with step tau,
+ * Eq. time-stepping-matrices-multiple-parallel-time-steps; with
+ * eliminate_first != 0 the explicit first stage (a_11 = 0) is removed as in
+ * Sec. 2.1 and e[i] = a_{i+2,1} (m-1 values) is returned for the B0 terms
+ * e_i (b^n - K y^n). A1, A2 must hold (steps*m')^2 doubles, m' = m or m-1;
+ * *s_out = steps*m'. */
+int pint_coupling_from_dirk(const double* A, int m, int steps, double tau,
+                            int eliminate_first, double* A1, double* A2,
+                            double* e, int* s_out);
+
+/* R = M Y A1^T + (K Y - B) A2^T - B0, all float64 N x s row-major (device).
+ * One pass over K for all s columns; the s x s right-multiplies are applied
+ * per row in registers (Sec. 3, BOP kernel, fused with the coupling). */
+int pint_apply_coupled(pint_op op, const double* Y, const double* B,
+                       const double* B0, double* R, void* stream);
+
+/* Linear slab solve (Eq. matrix-fixed-point-equation as defect correction,
+ * block GMRES(m) inner solve on J = alpha M + beta K with right Jacobi or
+ * ILU(0) preconditioning). Y: in = initial guess, out = solution. Stops when
+ * every column satisfies ||R_k|| <= tol ||F_k|| (absolute tol if F_k = 0).
+ * Synchronous. Returns PINT_ERR_NOT_CONVERGED (stats filled) at max_outer,
+ * PINT_ERR_BREAKDOWN on a non-finite residual. */
+int pint_solve_block(pint_op op, const double* B, const double* B0, double* Y,
+                     const pint_opts* opts, pint_stats* stats, void* stream);
+
+/* shift((Y_1,...,Y_s)) = (Y_2,...,Y_s,Y_s) in place (Sec. 2.2, Eq. shift). */
+int pint_shift(double* Y, int64_t n, int s, void* stream);
+
+/* ------------------------------------------------ nonlinear problems (a11) */
+enum { PINT_PROBLEM_DIFFREACT = 1, PINT_PROBLEM_RICHARDS = 2 };
+/* Nonlinear FV problem M(y)' + f(t,y) = 0 on an nx*ny*nz grid.
+ *  DIFFREACT: u_t = div((1+u^2) grad u) + u(1-u) + src(t), M = I, zero-flux
+ *             boundary, moving-circle source of Sec. 4.2; params unused.
+ *  RICHARDS:  d/dt theta(psi) - div(K_S kr(psi) grad(psi + z)) = 0 with the
+ *             van Genuchten-Mualem relations (Eq. RelationshipsThetaK);
+ *             params = {alpha, n, theta_r, theta_s, dt_D}; field = K_S[n]
+ *             (device); top patch (x,y < 1/2) Dirichlet ramp -2 -> 0.2 over
+ *             dt_D, other faces no-flow.
+ * The problem builds its own operator (stencil pattern) reachable through
+ * pint_problem_operator. */
+int pint_problem_create(pint_ctx ctx, pint_problem* prob, int kind, int nx,
+                        int ny, int nz, const double* params,
+                        const double* field, void* stream);
+int pint_problem_destroy(pint_problem prob);
+pint_op pint_problem_operator(pint_problem prob);
+/* mass_out = M(y), f_out = f(t, y) for one column y[n] (either output may
+ * be NULL). */
+int pint_problem_eval(pint_problem prob, double t, const double* y,
+                      double* mass_out, double* f_out, void* stream);
+/* R = M(Y) A1^T + F(T, Y) A2^T - B0 with the coupling of the problem's
+ * operator, times[s] (host) the stage times (Eq. matrix-equation-pipelining
+ * residual, sign read as "+F A2^T"). */
+int pint_problem_residual(pint_problem prob, const double* times,
+                          const double* Y, const double* B0, double* R,
+                          void* stream);
+/* One simplified-Newton iteration of Algorithm 1 on the current window:
+ * R = R(Y); if ||R_0|| <= tol * max(||B0_0||, tiny) set *converged = 1 and
+ * return; else J = alpha M'(Y_0) + beta Df(t_0, Y_0), solve J V = R with
+ * block GMRES (inner_tol), Y <- Y - V, *converged = 0. Synchronous. */
+int pint_newton_step(pint_problem prob, const double* times, double* Y,
+                     const double* B0, const pint_opts* opts, int* converged,
+                     pint_stats* stats, void* stream);
+/* Algorithm 1 ("Block Krylov Time Stepping with Pipelining"): windows of s
+ * consecutive stages of the stiffly accurate DIRK tableau (A, c) (m stages,
+ * host arrays) starting from Y = (y0, ..., y0), shifted by one stage whenever
+ * column 0 has converged, for `nstages` global stages. stages_out is N x
+ * nstages ROW-MAJOR (device): column g = converged stage g. Synchronous. */
+int pint_pipeline_run(pint_problem prob, const double* A, const double* c,
+                      int m, double tau, int s, const double* y0,
+                      int nstages, double* stages_out, const pint_opts* opts,
+                      pint_stats* stats, void* stream);
+
+/* ------------------------------------------- building blocks (test access)
+ * The kernels of the inner solve, exposed for parity tests. `precision`
+ * selects float64 (PINT_FP64: double arrays) or float32 (PINT_FP32: float
+ * arrays); H, R and norms are always float64. V holds nb blocks of N x s
+ * row-major each, block b at V + b*n*s. */
+/* Z = J X with J = alpha M + beta K of the current coupling (float64). */
+int pint_inner_apply(pint_op op, const double* X, double* Z, void* stream);
+/* Z = P^{-1} X for the preconditioner of `precond` (float64), set up from
+ * J on first use. */
+int pint_precond_apply(pint_op op, int precond, const double* X, double* Z,
+                       void* stream);
+/* H[(b*s+i)*s + k] = sum_r V_b[r][i] W[r][k]  ((nb*s) x s, float64, device). */
+int pint_block_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb,
+                    const void* V, const void* W, double* H, void* stream);
+/* W[r][k] -= sum_{b,i} V_b[r][i] H[(b*s+i)*s + k]. */
+int pint_block_update(pint_ctx ctx, int precision, int64_t n, int s, int nb,
+                      const void* V, const double* H, void* W, void* stream);
+/* CholQR2: W <- Q, R (s x s, device, row-major upper) with W_in = Q R;
+ * deflated columns of Q are zero. */
+int pint_cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W,
+                 double* R, void* stream);
+/* norms[k] = ||X_k||_2 (host array of s doubles). Synchronous. */
+int pint_colnorms(pint_ctx ctx, int precision, int64_t n, int s,
+                  const void* X, double* norms, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PINT_H */

@@ -1,0 +1,793 @@
+// Block Krylov inner solve and the outer defect correction.
+//
+// The matrix equation (alpha M + beta K) Y = RHS of Eq. matrix-fixed-point-
+// equation is solved for all s columns at once by block GMRES(m) with right
+// preconditioning (the paper uses DUNE-ISTL block Krylov solvers, Sec. 4; it is
+// silent on orthogonalisation). Per Arnoldi step:
+//   W = J P^{-1} V_j                      (k_spmm, ilu kernels)
+//   H = [V]^T W, W -= [V] H   twice       (k_gram + k_gram_reduce, k_update)
+//   W = V_{j+1} R  by CholQR2             (k_gram, k_chol, k_rowmul)
+//   Householder update of the block Hessenberg least-squares problem and the
+//   per-column residual estimates         (k_hess_step, one CTA, float64)
+// The outer loop is the fixed point of Eq. matrix-fixed-point-equation as
+// defect correction: R = R(Y) (k_coupled, float64), V = J^{-1} R, Y -= V.
+#include "internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+namespace pint {
+
+constexpr int kGramTile = 16;      // rows staged in shared memory per pass
+constexpr int kSmallLd = 17;       // reflector pitch (s + 1 <= 17)
+
+// ------------------------------------------------------------- Gram (a5)
+// partial[blk][p][k] = sum over this CTA's rows r of V_b[r][i] * W[r][k],
+// p = b*s + i. Threads: PT p-lanes x TR row groups; NPT p-values per thread.
+template <typename VT, int S, bool EXACT, int NPT>
+__global__ void __launch_bounds__(256)
+k_gram(int64_t n, int s, int nb, const VT* __restrict__ V, int64_t bstride,
+       const VT* __restrict__ W, int64_t rows_per_cta, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  VT* T = reinterpret_cast<VT*>(smem_raw);
+  const int P = nb * s;
+  const int pitch = P + s;
+  int PT = 32;
+  while (PT < P && PT < 256) PT <<= 1;
+  const int TR = 256 / PT;
+  const int pg = threadIdx.x % PT, rg = threadIdx.x / PT;
+  VT acc[NPT][S];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j)
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc[j][k] = VT(0);
+
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
+  for (int64_t tile = r0; tile < r1; tile += kGramTile) {
+    const int nrows = (int)((r1 - tile) < kGramTile ? (r1 - tile) : kGramTile);
+    const int seg = nrows * s;
+    for (int b = 0; b <= nb; ++b) {
+      const VT* src = (b < nb ? V + (int64_t)b * bstride : W) + tile * s;
+      for (int e = threadIdx.x; e < seg; e += 256) {
+        const int rr = e / s, i = e - rr * s;
+        T[rr * pitch + b * s + i] = src[e];
+      }
+    }
+    __syncthreads();
+    for (int rr = rg; rr < nrows; rr += TR) {
+      VT w[S];
+#pragma unroll
+      for (int k = 0; k < S; ++k) w[k] = (EXACT || k < s) ? T[rr * pitch + P + k] : VT(0);
+#pragma unroll
+      for (int j = 0; j < NPT; ++j) {
+        const int p = pg + j * PT;
+        if (p < P) {
+          const VT v = T[rr * pitch + p];
+#pragma unroll
+          for (int k = 0; k < S; ++k) acc[j][k] = fma(v, w[k], acc[j][k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // cross row-group reduction in float64
+  double* red = reinterpret_cast<double*>(smem_raw);
+  const int E = P * s;
+  double* out = partial + (int64_t)blockIdx.x * E;
+  if (TR == 1) {
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+      const int p = pg + j * PT;
+      if (p < P)
+#pragma unroll
+        for (int k = 0; k < S; ++k)
+          if (EXACT || k < s) out[p * s + k] = (double)acc[j][k];
+    }
+    return;
+  }
+  // NPT == 1 whenever TR > 1 (P <= 128)
+  for (int rgi = 0; rgi < TR; ++rgi) {
+    if (rg == rgi && pg < P) {
+#pragma unroll
+      for (int k = 0; k < S; ++k)
+        if (EXACT || k < s)
+          red[pg * s + k] = (rgi == 0 ? 0.0 : red[pg * s + k]) + (double)acc[0][k];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < E; e += 256) out[e] = red[e];
+}
+
+// H[e] = sum_blk partial[blk][e]  (fixed order: deterministic)
+__global__ void k_gram_reduce(int nblk, int E, const double* __restrict__ partial,
+                              double* __restrict__ H) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += partial[(int64_t)b * E + e];
+  H[e] = v;
+}
+
+static void ensure_partial(pint_ctx ctx, size_t bytes) {
+  if (ctx->partial_bytes >= bytes) return;
+  if (ctx->d_partial) dfree(ctx, ctx->d_partial, ctx->partial_bytes);
+  ctx->d_partial = static_cast<double*>(dalloc(ctx, bytes));
+  ctx->partial_bytes = bytes;
+}
+
+template <typename VT>
+static void gram_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t bstride,
+                   const VT* W, double* H, cudaStream_t st) {
+  const int P = nb * s;
+  PINT_REQUIRE(P <= 1024, PINT_ERR_INVALID, "Gram block too wide (nb*s > 1024)");
+  int PT = 32;
+  while (PT < P && PT < 256) PT <<= 1;
+  const int npt = (P + PT - 1) / PT;
+  const int64_t want = std::max<int64_t>(1, std::min<int64_t>(4LL * ctx->num_sms, (n + 63) / 64));
+  int64_t rpc = (n + want - 1) / want;
+  rpc = std::max<int64_t>(kGramTile, ((rpc + kGramTile - 1) / kGramTile) * kGramTile);
+  const int nblk = (int)((n + rpc - 1) / rpc);
+  const int E = P * s;
+  ensure_partial(ctx, sizeof(double) * (size_t)nblk * E);
+  const size_t tile_bytes = sizeof(VT) * kGramTile * (P + s);
+  const size_t red_bytes = sizeof(double) * E;
+  const size_t smem = std::max(tile_bytes, (PT < 256 ? red_bytes : (size_t)0));
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool EX = decltype(E_)::value;
+    auto launch = [&](auto kern) {
+      PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<nblk, 256, smem, st>>>(n, s, nb, V, bstride, W, rpc, ctx->d_partial);
+    };
+    if (npt == 1) launch(k_gram<VT, S, EX, 1>);
+    else if (npt == 2) launch(k_gram<VT, S, EX, 2>);
+    else launch(k_gram<VT, S, EX, 4>);
+  });
+  check_launch("k_gram");
+  k_gram_reduce<<<(E + 255) / 256, 256, 0, st>>>(nblk, E, ctx->d_partial, H);
+  check_launch("k_gram_reduce");
+  ctx->launches += 2;
+}
+
+void launch_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb, const void* V,
+                 int64_t bstride, const void* W, double* H, cudaStream_t st) {
+  if (precision == PINT_FP64)
+    gram_t<double>(ctx, n, s, nb, (const double*)V, bstride, (const double*)W, H, st);
+  else
+    gram_t<float>(ctx, n, s, nb, (const float*)V, bstride, (const float*)W, H, st);
+}
+
+// ------------------------------------------------------- block update (a6)
+// MODE 0: W -= V H ; 1: W = V H ; 2: W += V H. H ((nb*s) x s, float64) is
+// staged in shared memory in the vector precision with pitch S.
+template <typename VT, int S, bool EXACT, int MODE>
+__global__ void __launch_bounds__(256)
+k_update(int64_t n, int s, int nb, const VT* __restrict__ V, int64_t bstride,
+         const double* __restrict__ H, VT* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  VT* Hs = reinterpret_cast<VT*>(smem_raw);
+  const int P = nb * s;
+  for (int e = threadIdx.x; e < P * S; e += blockDim.x) {
+    const int p = e / S, k = e - p * S;
+    Hs[e] = (k < s) ? (VT)H[p * s + k] : VT(0);
+  }
+  __syncthreads();
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    VT acc[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc[k] = VT(0);
+    for (int b = 0; b < nb; ++b) {
+      VT v[S];
+      load_row<S, EXACT>(V + (int64_t)b * bstride + r * s, s, v);
+      const VT* hb = Hs + b * s * S;
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        if (!EXACT && i >= s) break;
+#pragma unroll
+        for (int k = 0; k < S; ++k) acc[k] = fma(v[i], hb[i * S + k], acc[k]);
+      }
+    }
+    VT* wr = W + r * s;
+    if constexpr (MODE == 1) {
+      store_row<S, EXACT>(wr, s, acc);
+    } else {
+      VT w[S];
+      load_row<S, EXACT>(wr, s, w);
+#pragma unroll
+      for (int k = 0; k < S; ++k) w[k] = (MODE == 0) ? w[k] - acc[k] : w[k] + acc[k];
+      store_row<S, EXACT>(wr, s, w);
+    }
+  }
+}
+
+template <typename VT>
+static void update_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t bstride,
+                     const double* H, VT* W, int mode, cudaStream_t st) {
+  const int P = nb * s;
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool EX = decltype(E_)::value;
+    const size_t smem = sizeof(VT) * (size_t)P * S;
+    const unsigned g = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(4LL * ctx->num_sms, (n + 255) / 256));
+    auto launch = [&](auto kern) {
+      PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<g, 256, smem, st>>>(n, s, nb, V, bstride, H, W);
+    };
+    if (mode == 0) launch(k_update<VT, S, EX, 0>);
+    else if (mode == 1) launch(k_update<VT, S, EX, 1>);
+    else launch(k_update<VT, S, EX, 2>);
+  });
+  check_launch("k_update");
+  ctx->launches += 1;
+}
+
+void launch_update(pint_ctx ctx, int precision, int64_t n, int s, int nb, const void* V,
+                   int64_t bstride, const double* H, void* W, int mode, cudaStream_t st) {
+  if (precision == PINT_FP64)
+    update_t<double>(ctx, n, s, nb, (const double*)V, bstride, H, (double*)W, mode, st);
+  else
+    update_t<float>(ctx, n, s, nb, (const float*)V, bstride, H, (float*)W, mode, st);
+}
+
+// ------------------------------------------------------------ CholQR (a7)
+// Upper Cholesky G = R^T R in natural order with deflation (pivot <=
+// defl * G_kk or G_kk <= 0 -> zero row of R); Rinv with Q = W Rinv, zero
+// columns for deflated k. One CTA of 256 threads, s <= 16.
+__global__ void k_chol(int s, const double* __restrict__ G, double defl, double* __restrict__ R,
+                       double* __restrict__ Rinv, int* __restrict__ defl_count) {
+  __shared__ double Gs[kMaxS][kMaxS + 1];
+  __shared__ double Rs[kMaxS][kMaxS + 1];
+  __shared__ double g0[kMaxS];
+  __shared__ int dead[kMaxS];
+  const int t = threadIdx.x, i = t / kMaxS, j = t % kMaxS;
+  if (i < s && j < s) {
+    Gs[i][j] = G[i * s + j];
+    Rs[i][j] = 0.0;
+  }
+  if (t < s) g0[t] = G[t * s + t];
+  __syncthreads();
+  for (int k = 0; k < s; ++k) {
+    __shared__ double piv;
+    if (t == 0) {
+      const double d = Gs[k][k];
+      const bool isdead = !(g0[k] > 0.0) || !(d > defl * g0[k]);
+      dead[k] = isdead ? 1 : 0;
+      piv = isdead ? 0.0 : sqrt(d);
+      if (isdead && defl_count) atomicAdd(defl_count, 1);
+    }
+    __syncthreads();
+    if (t < s && t >= k) Rs[k][t] = dead[k] ? 0.0 : (t == k ? piv : Gs[k][t] / piv);
+    __syncthreads();
+    if (i < s && j < s && i > k && j > k) Gs[i][j] -= Rs[k][i] * Rs[k][j];
+    __syncthreads();
+  }
+  if (i < s && j < s) R[i * s + j] = Rs[i][j];
+  // row t of Rinv: Rinv[t][k] = ((t==k) - sum_{c<k} Rinv[t][c] R[c][k]) / R[k][k]
+  if (t < s) {
+    double row[kMaxS];
+    for (int k = 0; k < s; ++k) {
+      double v = 0.0;
+      if (!dead[k]) {
+        v = (t == k) ? 1.0 : 0.0;
+        for (int c = 0; c < k; ++c) v -= row[c] * Rs[c][k];
+        v /= Rs[k][k];
+      }
+      row[k] = v;
+    }
+    for (int k = 0; k < s; ++k) Rinv[t * s + k] = row[k];
+  }
+}
+
+// W[r] <- W[r] * Ri (s x s), in place: each thread owns a row.
+template <typename VT, int S, bool EXACT>
+__global__ void __launch_bounds__(256)
+k_rowmul(int64_t n, int s, VT* __restrict__ W, const double* __restrict__ Ri) {
+  __shared__ VT Rs[S * S];
+  for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+    const int i = e / S, k = e % S;
+    Rs[e] = (i < s && k < s) ? (VT)Ri[i * s + k] : VT(0);
+  }
+  __syncthreads();
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    VT w[S], o[S];
+    load_row<S, EXACT>(W + r * s, s, w);
+#pragma unroll
+    for (int k = 0; k < S; ++k) o[k] = VT(0);
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int k = i; k < S; ++k) o[k] = fma(w[i], Rs[i * S + k], o[k]);
+    store_row<S, EXACT>(W + r * s, s, o);
+  }
+}
+
+// C = A B for s x s row-major matrices (one CTA).
+__global__ void k_small_mm(int s, const double* __restrict__ A, const double* __restrict__ B,
+                           double* __restrict__ C) {
+  const int t = threadIdx.x, i = t / kMaxS, j = t % kMaxS;
+  if (i >= s || j >= s) return;
+  double v = 0.0;
+  for (int k = 0; k < s; ++k) v += A[i * s + k] * B[k * s + j];
+  C[i * s + j] = v;
+}
+
+struct CholScratch {
+  double* G;
+  double* R1;
+  double* R2;
+  double* Rinv;
+};
+
+static CholScratch chol_scratch(pint_ctx ctx) {
+  double* b = ctx->d_small + kSmallChol;
+  return {b, b + 256, b + 512, b + 768};
+}
+
+template <typename VT>
+static void cholqr_pass(pint_ctx ctx, int64_t n, int s, VT* W, double* R, double defl,
+                        int* defl_count, cudaStream_t st) {
+  CholScratch cs = chol_scratch(ctx);
+  gram_t<VT>(ctx, n, s, 1, W, 0, W, cs.G, st);
+  k_chol<<<1, 256, 0, st>>>(s, cs.G, defl, R, cs.Rinv, defl_count);
+  check_launch("k_chol");
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool EX = decltype(E_)::value;
+    const unsigned g = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(8LL * ctx->num_sms, (n + 255) / 256));
+    k_rowmul<VT, S, EX><<<g, 256, 0, st>>>(n, s, W, cs.Rinv);
+  });
+  check_launch("k_rowmul");
+  ctx->launches += 2;
+}
+
+void cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W, double* R,
+             int* defl_count, cudaStream_t st) {
+  CholScratch cs = chol_scratch(ctx);
+  const double defl = precision == PINT_FP64 ? 1e-14 : 1e-8;
+  if (precision == PINT_FP64) {
+    cholqr_pass<double>(ctx, n, s, (double*)W, cs.R1, defl, defl_count, st);
+    cholqr_pass<double>(ctx, n, s, (double*)W, cs.R2, defl, defl_count, st);
+  } else {
+    cholqr_pass<float>(ctx, n, s, (float*)W, cs.R1, defl, defl_count, st);
+    cholqr_pass<float>(ctx, n, s, (float*)W, cs.R2, defl, defl_count, st);
+  }
+  k_small_mm<<<1, 256, 0, st>>>(s, cs.R2, cs.R1, R);
+  check_launch("k_small_mm");
+  ctx->launches += 1;
+}
+
+// ---------------------------------------------- block Hessenberg (a8)
+// Column block j: [H1 + H2 ; Rn] ((j+2)s x s) -> apply the js earlier
+// reflectors, make s new reflectors of length s+1, rotate Gr, write the
+// per-column residual estimates and flag = {all converged, non-finite}.
+// One CTA of 512 threads; warp l owns column l.
+__global__ void __launch_bounds__(512)
+k_hess_step(int j, int s, int ldh, const double* __restrict__ H1, const double* __restrict__ H2,
+            const double* __restrict__ Rn, double* __restrict__ Hb, double* __restrict__ refl,
+            double* __restrict__ Gr, const double* __restrict__ target, double* __restrict__ est,
+            int* __restrict__ flag) {
+  extern __shared__ double col[];
+  __shared__ double vcur[32];
+  const int L = (j + 2) * s;
+  const int top = (j + 1) * s;
+  for (int idx = threadIdx.x; idx < s * L; idx += blockDim.x) {
+    const int l = idx / L, row = idx - l * L;
+    col[idx] = row < top ? H1[row * s + l] + H2[row * s + l] : Rn[(row - top) * s + l];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane <= s;
+  if (warp < s) {
+    double* cl = col + warp * L;
+    for (int c = 0; c < j * s; ++c) {
+      const double v = act ? refl[c * kSmallLd + lane] : 0.0;
+      const double x = act ? cl[c + lane] : 0.0;
+      const double d = warp_sum(v * x);
+      if (act) cl[c + lane] = x - 2.0 * v * d;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int l = 0; l < s; ++l) {
+    const int c = j * s + l;
+    if (warp == l) {
+      double* cl = col + l * L;
+      const double x = act ? cl[c + lane] : 0.0;
+      const double nrm = sqrt(warp_sum(x * x));
+      const double x0 = __shfl_sync(0xffffffffu, x, 0);
+      const double beta = x0 >= 0.0 ? -nrm : nrm;
+      double v = x - (lane == 0 ? beta : 0.0);
+      const double vn = sqrt(warp_sum(v * v));
+      v = (vn > 0.0 && act) ? v / vn : 0.0;
+      vcur[lane] = v;
+      if (act) refl[c * kSmallLd + lane] = v;
+      if (act) cl[c + lane] = (lane == 0) ? (nrm > 0.0 ? beta : 0.0) : 0.0;
+    }
+    __syncthreads();
+    if (warp < s) {
+      const double v = vcur[lane];
+      if (warp > l) {
+        double* cl = col + warp * L;
+        const double x = act ? cl[c + lane] : 0.0;
+        const double d = warp_sum(v * x);
+        if (act) cl[c + lane] = x - 2.0 * v * d;
+      }
+      const double g = act ? Gr[(c + lane) * s + warp] : 0.0;
+      const double d = warp_sum(v * g);
+      if (act) Gr[(c + lane) * s + warp] = g - 2.0 * v * d;
+    }
+    __syncthreads();
+  }
+  if (warp < s) {
+    const double g = lane < s ? Gr[(top + lane) * s + warp] : 0.0;
+    const double e = sqrt(warp_sum(g * g));
+    if (lane == 0) est[warp] = e;
+  }
+  for (int idx = threadIdx.x; idx < s * L; idx += blockDim.x) {
+    const int l = idx / L, row = idx - l * L;
+    Hb[(int64_t)(j * s + l) * ldh + row] = col[idx];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int conv = 1, bad = 0;
+    for (int k = 0; k < s; ++k) {
+      const double e = est[k];
+      if (!isfinite(e)) bad = 1;
+      if (!(e <= target[k])) conv = 0;
+    }
+    flag[0] = conv;
+    flag[1] = bad;
+  }
+}
+
+// Gr = [S ; 0] for a new cycle ((m+1)s x s)
+__global__ void k_gr_init(int rows, int s, const double* __restrict__ S, double* __restrict__ Gr) {
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < rows * s; e += blockDim.x * gridDim.x)
+    Gr[e] = e < s * s ? S[e] : 0.0;
+}
+
+// Back substitution Rt Y = Gr[0:kd] with the upper triangle stored in Hb
+// (column-major, leading dimension ldh); tiny pivots give zero rows of Y.
+__global__ void __launch_bounds__(512)
+k_backsolve(int kd, int s, int ldh, const double* __restrict__ Hb, const double* __restrict__ Gr,
+            double* __restrict__ Y) {
+  extern __shared__ double Gs[];
+  __shared__ double ybuf[kMaxS];
+  __shared__ double scale;
+  for (int e = threadIdx.x; e < kd * s; e += blockDim.x) Gs[e] = Gr[e];
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < kd; ++i) m = fmax(m, fabs(Hb[(int64_t)i * ldh + i]));
+    scale = m;
+  }
+  __syncthreads();
+  for (int i = kd - 1; i >= 0; --i) {
+    const double rii = Hb[(int64_t)i * ldh + i];
+    if (threadIdx.x < s) {
+      const double y = fabs(rii) <= 1e-300 + 1e-14 * scale ? 0.0 : Gs[i * s + threadIdx.x] / rii;
+      ybuf[threadIdx.x] = y;
+      Y[i * s + threadIdx.x] = y;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < i * s; e += blockDim.x) {
+      const int r = e / s, k = e - r * s;
+      Gs[e] -= Hb[(int64_t)i * ldh + r] * ybuf[k];
+    }
+    __syncthreads();
+  }
+}
+
+// X += V (elementwise, n*s)
+template <typename VT>
+__global__ void k_axpy(int64_t ne, const VT* __restrict__ V, VT* __restrict__ X) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ne) X[i] += V[i];
+}
+
+// ------------------------------------------------------- work buffers
+struct KrylovWork {
+  int64_t n = 0;
+  int s = 0, m = 0, prec = -1;
+  size_t es = 0;
+  void* V = nullptr;     // (m+1) blocks of n*s
+  void* Zt = nullptr;    // n*s temp
+  void* Xk = nullptr;    // n*s Krylov solution
+  void* Rs = nullptr;    // n*s scaled inner right-hand side
+  double* R64 = nullptr; // n*s outer residual
+  double* Hg1 = nullptr;
+  double* Hg2 = nullptr;
+  double* Rn = nullptr;
+  double* S = nullptr;
+  double* Hb = nullptr;
+  double* refl = nullptr;
+  double* Gr = nullptr;
+  double* Yls = nullptr;
+  double* target = nullptr;
+  double* est = nullptr;
+  double* rnorm = nullptr;
+  double* fnorm = nullptr;
+  int* flag = nullptr;
+  int* defl = nullptr;
+  size_t bytes = 0;
+  std::vector<std::pair<void*, size_t>> allocs;
+};
+
+static void* walloc(pint_ctx ctx, KrylovWork* w, size_t bytes) {
+  void* p = dalloc(ctx, bytes);
+  w->allocs.push_back({p, bytes});
+  return p;
+}
+
+void free_work(pint_op op) {
+  if (!op->work) return;
+  for (auto& a : op->work->allocs) dfree(op->ctx, a.first, a.second);
+  delete op->work;
+  op->work = nullptr;
+}
+
+static KrylovWork* ensure_work(pint_op op, int prec, int m) {
+  const int s = op->s;
+  KrylovWork* w = op->work;
+  if (w && w->n == op->n && w->s == s && w->m >= m && w->prec == prec) return w;
+  free_work(op);
+  w = new KrylovWork();
+  op->work = w;
+  w->n = op->n;
+  w->s = s;
+  w->m = m;
+  w->prec = prec;
+  w->es = prec == PINT_FP64 ? 8 : 4;
+  pint_ctx ctx = op->ctx;
+  const size_t ns = (size_t)op->n * s;
+  try {
+    w->V = walloc(ctx, w, w->es * ns * (m + 1));
+    w->Zt = walloc(ctx, w, w->es * ns);
+    w->Xk = walloc(ctx, w, w->es * ns);
+    w->Rs = walloc(ctx, w, w->es * ns);
+    w->R64 = (double*)walloc(ctx, w, 8 * ns);
+    const size_t rows = (size_t)(m + 1) * s;
+    w->Hg1 = (double*)walloc(ctx, w, 8 * rows * s);
+    w->Hg2 = (double*)walloc(ctx, w, 8 * rows * s);
+    w->Rn = (double*)walloc(ctx, w, 8 * s * s);
+    w->S = (double*)walloc(ctx, w, 8 * s * s);
+    w->Hb = (double*)walloc(ctx, w, 8 * rows * (size_t)m * s);
+    w->refl = (double*)walloc(ctx, w, 8 * (size_t)m * s * kSmallLd);
+    w->Gr = (double*)walloc(ctx, w, 8 * rows * s);
+    w->Yls = (double*)walloc(ctx, w, 8 * rows * s);
+    w->target = (double*)walloc(ctx, w, 8 * kMaxS);
+    w->est = (double*)walloc(ctx, w, 8 * kMaxS);
+    w->rnorm = (double*)walloc(ctx, w, 8 * kMaxS);
+    w->fnorm = (double*)walloc(ctx, w, 8 * kMaxS);
+    w->flag = (int*)walloc(ctx, w, 64);
+    w->defl = (int*)walloc(ctx, w, 64);
+    // Gram partials for the widest block ((m+1) s) at the largest grid
+    ensure_partial(ctx, sizeof(double) * 4 * (size_t)ctx->num_sms * rows * s);
+  } catch (...) {
+    free_work(op);
+    throw;
+  }
+  return w;
+}
+
+// --------------------------------------------------------- inner solve
+// Block GMRES(m) on J Xk = Rs (unit columns) in precision VT. With Jacobi the
+// matrix is the column-scaled J D^{-1} and Xk is the scaled unknown; with
+// ILU(0) the preconditioner is applied to every basis block and to the final
+// combination. Returns Arnoldi steps taken.
+static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStream_t st) {
+  pint_ctx ctx = op->ctx;
+  const int64_t n = op->n;
+  const int s = op->s, m = o->restart, prec = o->precision;
+  const int vprec = prec == PINT_FP64 ? PINT_FP64 : PINT_FP32;
+  const bool jac = o->precond == PINT_PC_JACOBI;
+  const bool ilu = o->precond == PINT_PC_ILU0;
+  const int64_t bs = n * s;
+  const size_t es = w->es;
+  auto Vb = [&](int b) { return (void*)((char*)w->V + (size_t)b * bs * es); };
+  const int ldh = (m + 1) * s;
+  // targets: inner_tol (columns are unit or zero)
+  {
+    double t[kMaxS];
+    for (int k = 0; k < s; ++k) t[k] = o->inner_tol;
+    PINT_CUDA(cudaMemcpyAsync(w->target, t, 8 * s, cudaMemcpyHostToDevice, st));
+  }
+  PINT_CUDA(cudaMemsetAsync(w->Xk, 0, es * bs, st));
+  PINT_CUDA(cudaMemsetAsync(w->defl, 0, 64, st));
+  PINT_CUDA(cudaMemcpyAsync(Vb(0), w->Rs, es * bs, cudaMemcpyDeviceToDevice, st));
+  InnerResult res{0, 0, false, 0};
+  const size_t hess_smem = 8 * (size_t)s * (m + 1) * s;
+  const size_t back_smem = 8 * (size_t)m * s * s;
+  PINT_CUDA(cudaFuncSetAttribute(k_hess_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)hess_smem));
+  PINT_CUDA(cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)back_smem));
+  while (res.its < o->max_inner) {
+    res.cycles += 1;
+    cholqr2(ctx, vprec, n, s, Vb(0), w->S, w->defl, st);
+    k_gr_init<<<8, 256, 0, st>>>(ldh, s, w->S, w->Gr);
+    check_launch("k_gr_init");
+    ctx->launches += 1;
+    int j = 0;
+    bool conv = false;
+    for (j = 0; j < m; ++j) {
+      if (ilu) {
+        ilu_apply(op, prec, Vb(j), w->Zt, st);
+        launch_inner_spmm(op, prec, false, w->Zt, Vb(j + 1), nullptr, st);
+      } else {
+        launch_inner_spmm(op, prec, jac, Vb(j), Vb(j + 1), nullptr, st);
+      }
+      launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg1, st);
+      launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg1, Vb(j + 1), 0, st);
+      launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg2, st);
+      launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg2, Vb(j + 1), 0, st);
+      cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, st);
+      k_hess_step<<<1, 512, 8 * (size_t)s * (j + 2) * s, st>>>(
+          j, s, ldh, w->Hg1, w->Hg2, w->Rn, w->Hb, w->refl, w->Gr, w->target, w->est, w->flag);
+      check_launch("k_hess_step");
+      ctx->launches += 1;
+      res.its += 1;
+      PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      PINT_CUDA(cudaStreamSynchronize(st));
+      if (ilu) ilu_check(op);
+      PINT_REQUIRE(ctx->h_flag[1] == 0, PINT_ERR_BREAKDOWN,
+                   "non-finite residual estimate in block GMRES");
+      conv = ctx->h_flag[0] != 0;
+      if (conv || res.its >= o->max_inner) {
+        j += 1;
+        break;
+      }
+    }
+    const int kd = j * s;
+    k_backsolve<<<1, 512, 8 * (size_t)kd * s, st>>>(kd, s, ldh, w->Hb, w->Gr, w->Yls);
+    check_launch("k_backsolve");
+    ctx->launches += 1;
+    if (ilu) {
+      launch_update(ctx, vprec, n, s, j, w->V, bs, w->Yls, w->Zt, 1, st);
+      void* tmp = Vb(std::min(j, m));   // block j is free after the cycle
+      ilu_apply(op, prec, w->Zt, tmp, st);
+      if (vprec == PINT_FP64)
+        k_axpy<double><<<grid_for(bs, 256), 256, 0, st>>>(bs, (const double*)tmp, (double*)w->Xk);
+      else
+        k_axpy<float><<<grid_for(bs, 256), 256, 0, st>>>(bs, (const float*)tmp, (float*)w->Xk);
+      check_launch("k_axpy");
+      ctx->launches += 1;
+    } else {
+      launch_update(ctx, vprec, n, s, j, w->V, bs, w->Yls, w->Xk, 2, st);
+    }
+    if (conv) {
+      res.converged = true;
+      break;
+    }
+    if (res.its >= o->max_inner) break;
+    // restart: V_0 = Rs - J Xk
+    launch_inner_spmm(op, prec, jac, w->Xk, Vb(0), w->Rs, st);
+  }
+  PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->defl, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PINT_CUDA(cudaStreamSynchronize(st));
+  res.deflations = ctx->h_flag[0];
+  return res;
+}
+
+InnerResult inner_solve(pint_op op, const pint_opts* o, const double* R, const double* rnorm_dev,
+                        double* /*unused*/, cudaStream_t st) {
+  KrylovWork* w = ensure_work(op, o->precision == PINT_FP64 ? PINT_FP64 : PINT_FP32, o->restart);
+  const int64_t n = op->n;
+  const int s = op->s;
+  if (w->prec == PINT_FP64) {
+    launch_scale_copy64(n, s, R, (double*)w->Rs, rnorm_dev, st, op->ctx);   // Rs = R / ||R_k||
+  } else {
+    launch_scale_cast(n, s, R, (float*)w->Rs, rnorm_dev, st, op->ctx);
+  }
+  return gmres(op, o, w, st);
+}
+
+void work_views(pint_op op, int prec, int m, double** R64, double** rnorm, void** Xk,
+                int* wprec) {
+  KrylovWork* w = ensure_work(op, prec, m);
+  *R64 = w->R64;
+  *rnorm = w->rnorm;
+  *Xk = w->Xk;
+  *wprec = w->prec;
+}
+
+// ------------------------------------------------------- outer driver
+static double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
+                     const pint_opts* o, pint_stats* stats, cudaStream_t st) {
+  pint_ctx ctx = op->ctx;
+  const double t0 = now_ms();
+  const long l0 = ctx->launches;
+  PINT_REQUIRE(op->s >= 1, PINT_ERR_INVALID, "coupling not set (pint_set_coupling)");
+  PINT_REQUIRE(o->restart >= 1 && o->restart <= PINT_MAX_RESTART, PINT_ERR_INVALID,
+               "restart out of range");
+  PINT_REQUIRE((int64_t)(o->restart + 1) * op->s <= 1024, PINT_ERR_INVALID,
+               "(restart + 1) * s must not exceed 1024");
+  PINT_REQUIRE(o->precision >= PINT_FP64 && o->precision <= PINT_BF16, PINT_ERR_INVALID,
+               "precision");
+  PINT_REQUIRE(o->precond >= PINT_PC_NONE && o->precond <= PINT_PC_ILU0, PINT_ERR_INVALID,
+               "precond");
+  const int64_t n = op->n;
+  const int s = op->s;
+  if (!op->j_valid) build_inner(op, st);
+  double setup_ms = 0.0;
+  if (o->precond == PINT_PC_ILU0) {
+    const double ts = now_ms();
+    ilu_setup(op, st);
+    setup_ms = now_ms() - ts;
+  }
+  KrylovWork* w = ensure_work(op, o->precision == PINT_FP64 ? PINT_FP64 : PINT_FP32, o->restart);
+  // ||F_k|| with F = B A2^T + B0: residual of Y = 0 is -F
+  PINT_CUDA(cudaMemsetAsync(w->Zt, 0, w->es * (size_t)n * s, st));
+  double* zeroY = nullptr;
+  if (w->es == 8) {
+    zeroY = (double*)w->Zt;
+  } else {
+    zeroY = (double*)w->V;   // first 8*n*s bytes of the basis are free here
+    PINT_CUDA(cudaMemsetAsync(zeroY, 0, 8 * (size_t)n * s, st));
+  }
+  launch_coupled(op, zeroY, B, B0, w->R64, st);
+  launch_colnorm(ctx, PINT_FP64, n, s, w->R64, w->fnorm, st);
+  double fn[kMaxS], rn[kMaxS];
+  PINT_CUDA(cudaMemcpyAsync(ctx->h_small, w->fnorm, 8 * s, cudaMemcpyDeviceToHost, st));
+  PINT_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < s; ++k) fn[k] = ctx->h_small[k];
+  int status = PINT_ERR_NOT_CONVERGED;
+  int outer = 0, inner = 0, cycles = 0, defl = 0;
+  for (outer = 0; outer <= o->max_outer; ++outer) {
+    launch_coupled(op, Y, B, B0, w->R64, st);
+    launch_colnorm(ctx, PINT_FP64, n, s, w->R64, w->rnorm, st);
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_small, w->rnorm, 8 * s, cudaMemcpyDeviceToHost, st));
+    PINT_CUDA(cudaStreamSynchronize(st));
+    bool done = true, bad = false;
+    for (int k = 0; k < s; ++k) {
+      rn[k] = ctx->h_small[k];
+      if (!std::isfinite(rn[k])) bad = true;
+      const double thr = fn[k] > 0.0 ? o->tol * fn[k] : o->tol;
+      if (!(rn[k] <= thr)) done = false;
+    }
+    if (stats)
+      for (int k = 0; k < s; ++k) stats->col_relres[k] = fn[k] > 0.0 ? rn[k] / fn[k] : rn[k];
+    if (bad) {
+      status = PINT_ERR_BREAKDOWN;
+      break;
+    }
+    if (done) {
+      status = PINT_OK;
+      break;
+    }
+    if (outer == o->max_outer) break;
+    InnerResult ir = inner_solve(op, o, w->R64, w->rnorm, nullptr, st);
+    inner += ir.its;
+    cycles += ir.cycles;
+    defl += ir.deflations;
+    const int vprec = w->prec;
+    launch_outer_update(vprec, n, s, Y, w->Xk, w->rnorm,
+                        o->precond == PINT_PC_JACOBI ? op->Jinvdiag : nullptr, st, ctx);
+  }
+  PINT_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->status = status;
+    stats->outer_its = outer;
+    stats->inner_its = inner;
+    stats->restarts = cycles;
+    stats->deflations = defl;
+    stats->setup_ms = setup_ms;
+    stats->solve_ms = now_ms() - t0;
+    stats->kernel_launches = (int)(ctx->launches - l0);
+  }
+  if (status == PINT_ERR_BREAKDOWN)
+    throw Error{PINT_ERR_BREAKDOWN, "non-finite outer residual"};
+  return status;
+}
+
+}  // namespace pint

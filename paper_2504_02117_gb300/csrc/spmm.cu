@@ -1,0 +1,421 @@
+// Sparse block kernels: SELL-32 build, the fused coupled residual (Sec. 2.2
+// residual / Eq. matrix-fixed-point-equation), the inner operator apply
+// J X = (alpha M + beta K) X (Sec. 3, BOP kernel), column norms, casts and
+// the outer update. One thread owns one row and its s accumulators (the s
+// "SIMD lanes" of Sec. 3 become registers); a warp owns one SELL slice, so
+// matrix values and column indices are read once per s columns, coalesced.
+#include "internal.h"
+
+#include <algorithm>
+
+namespace pint {
+
+// ---------------------------------------------------------------- SELL build
+void sell_build(pint_op op) {
+  const int64_t n = op->n;
+  const int64_t ns = (n + kSellC - 1) / kSellC;
+  std::vector<int64_t> sptr(ns + 1, 0);
+  for (int64_t q = 0; q < ns; ++q) {
+    int w = 0;
+    for (int64_t r = q * kSellC; r < std::min<int64_t>(n, (q + 1) * kSellC); ++r)
+      w = std::max(w, op->h_rowptr[r + 1] - op->h_rowptr[r]);
+    sptr[q + 1] = sptr[q] + (int64_t)w * kSellC;
+  }
+  const int64_t ne = sptr[ns];
+  std::vector<int> col(ne);
+  std::vector<int64_t> map(op->nnz);
+  for (int64_t q = 0; q < ns; ++q) {
+    const int w = (int)((sptr[q + 1] - sptr[q]) / kSellC);
+    for (int l = 0; l < kSellC; ++l) {
+      const int64_t r = q * kSellC + l;
+      for (int t = 0; t < w; ++t) {
+        const int64_t pos = sptr[q] + (int64_t)t * kSellC + l;
+        if (r < n && op->h_rowptr[r] + t < op->h_rowptr[r + 1]) {
+          const int64_t p = op->h_rowptr[r] + t;
+          col[pos] = op->h_colind[p];
+          map[p] = pos;
+        } else {
+          col[pos] = (int)std::min<int64_t>(r, n - 1);   // padding: own row, value 0
+        }
+      }
+    }
+  }
+  SellPattern& S = op->sell;
+  S.n = n;
+  S.nslices = ns;
+  S.nelem = ne;
+  S.slice_ptr = dalloc_n<int64_t>(op->ctx, ns + 1);
+  S.col = dalloc_n<int>(op->ctx, std::max<int64_t>(ne, 1));
+  S.csr_to_sell = dalloc_n<int64_t>(op->ctx, std::max<int64_t>(op->nnz, 1));
+  PINT_CUDA(cudaMemcpy(S.slice_ptr, sptr.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice));
+  PINT_CUDA(cudaMemcpy(S.col, col.data(), sizeof(int) * ne, cudaMemcpyHostToDevice));
+  PINT_CUDA(cudaMemcpy(S.csr_to_sell, map.data(), sizeof(int64_t) * op->nnz, cudaMemcpyHostToDevice));
+}
+
+template <typename OT>
+__global__ void k_sell_scatter(int64_t nnz, const int* __restrict__ rowptr_unused,
+                               const int64_t* __restrict__ map, const double* __restrict__ src,
+                               const int* __restrict__ colind, const double* __restrict__ colscale,
+                               OT* __restrict__ dst) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  double v = src[p];
+  if (colscale) v *= colscale[colind[p]];
+  if constexpr (std::is_same<OT, double>::value) dst[map[p]] = v;
+  else if constexpr (std::is_same<OT, float>::value) dst[map[p]] = __double2float_rn(v);
+  else dst[map[p]] = __double2bfloat16(v);
+}
+
+void sell_scatter(pint_op op, const double* csr_vals, double* sell_vals, cudaStream_t st) {
+  PINT_CUDA(cudaMemsetAsync(sell_vals, 0, sizeof(double) * op->sell.nelem, st));
+  k_sell_scatter<double><<<grid_for(op->nnz, 256), 256, 0, st>>>(
+      op->nnz, nullptr, op->sell.csr_to_sell, csr_vals, op->colind, nullptr, sell_vals);
+  check_launch("k_sell_scatter");
+  op->ctx->launches += 1;
+}
+
+// ------------------------------------------------ inner operator J values
+__global__ void k_build_inner(int64_t n, const int* __restrict__ rowptr,
+                              const int* __restrict__ diagpos, const double* __restrict__ K,
+                              const double* __restrict__ M, double alpha, double beta,
+                              double* __restrict__ J, double* __restrict__ Jd,
+                              double* __restrict__ Jinv) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) J[p] = beta * K[p];
+  const int d = diagpos[r];
+  J[d] += alpha * (M ? M[r] : 1.0);
+  Jd[r] = J[d];
+  Jinv[r] = 1.0 / J[d];
+}
+
+void build_inner(pint_op op, cudaStream_t st) {
+  if (!op->Jval) {
+    op->Jval = dalloc_n<double>(op->ctx, op->nnz);
+    op->Jdiag = dalloc_n<double>(op->ctx, op->n);
+    op->Jinvdiag = dalloc_n<double>(op->ctx, op->n);
+  }
+  k_build_inner<<<grid_for(op->n, 256), 256, 0, st>>>(op->n, op->rowptr, op->diagpos, op->Kval,
+                                                      op->Mdiag, op->alpha, op->beta, op->Jval,
+                                                      op->Jdiag, op->Jinvdiag);
+  check_launch("k_build_inner");
+  op->ctx->launches += 1;
+  op->j_valid = true;
+}
+
+void* inner_sell(pint_op op, int precision, bool jacobi, cudaStream_t st) {
+  void*& slot = op->sellJ[precision][jacobi ? 1 : 0];
+  if (slot) return slot;
+  const size_t es = precision == PINT_FP64 ? 8 : precision == PINT_FP32 ? 4 : 2;
+  slot = dalloc(op->ctx, es * op->sell.nelem);
+  PINT_CUDA(cudaMemsetAsync(slot, 0, es * op->sell.nelem, st));
+  const double* cs = jacobi ? op->Jinvdiag : nullptr;
+  const unsigned g = grid_for(op->nnz, 256);
+  if (precision == PINT_FP64)
+    k_sell_scatter<double><<<g, 256, 0, st>>>(op->nnz, nullptr, op->sell.csr_to_sell, op->Jval,
+                                              op->colind, cs, static_cast<double*>(slot));
+  else if (precision == PINT_FP32)
+    k_sell_scatter<float><<<g, 256, 0, st>>>(op->nnz, nullptr, op->sell.csr_to_sell, op->Jval,
+                                             op->colind, cs, static_cast<float*>(slot));
+  else
+    k_sell_scatter<__nv_bfloat16><<<g, 256, 0, st>>>(op->nnz, nullptr, op->sell.csr_to_sell,
+                                                     op->Jval, op->colind, cs,
+                                                     static_cast<__nv_bfloat16*>(slot));
+  check_launch("k_sell_scatter(J)");
+  op->ctx->launches += 1;
+  return slot;
+}
+
+// --------------------------------------------------- fused coupled residual
+// R_r = d_r (Y_r A1^T) + ((K Y)_r - B_r) A2^T - B0_r  for every row r, with the
+// s x s products unrolled against the kernel-parameter copies of A1, A2
+// (zero coefficients skipped by warp-uniform branches).
+template <int S, bool EXACT>
+__global__ void __launch_bounds__(256)
+k_coupled(int64_t n, int s, const int64_t* __restrict__ sptr, const int* __restrict__ col,
+          const double* __restrict__ val, const double* __restrict__ Md,
+          const double* __restrict__ Y, const double* __restrict__ B,
+          const double* __restrict__ B0, double* __restrict__ R,
+          const __grid_constant__ Coupling cp) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const int64_t q = row >> 5;
+  const int lane = (int)(row & 31);
+  const int64_t b0 = sptr[q];
+  const int w = (int)((sptr[q + 1] - b0) >> 5);
+  double ky[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) ky[k] = 0.0;
+  const double* vp = val + b0 + lane;
+  const int* cpp = col + b0 + lane;
+  for (int t = 0; t < w; ++t) {
+    const double v = __ldg(vp + (int64_t)t * 32);
+    const int c = __ldg(cpp + (int64_t)t * 32);
+    double x[S];
+    load_row<S, EXACT>(Y + (int64_t)c * s, s, x);
+#pragma unroll
+    for (int k = 0; k < S; ++k) ky[k] = fma(v, x[k], ky[k]);
+  }
+  double y[S], bb[S], out[S];
+  load_row<S, EXACT>(Y + row * s, s, y);
+  if (B) {
+    load_row<S, EXACT>(B + row * s, s, bb);
+#pragma unroll
+    for (int k = 0; k < S; ++k) ky[k] -= bb[k];
+  }
+  if (B0) {
+    load_row<S, EXACT>(B0 + row * s, s, out);
+#pragma unroll
+    for (int k = 0; k < S; ++k) out[k] = -out[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < S; ++k) out[k] = 0.0;
+  }
+  const double d = Md ? __ldg(Md + row) : 1.0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    if (!EXACT && i >= s) break;
+    double m1 = 0.0, m2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      if (!EXACT && k >= s) break;
+      const double a1 = cp.A1[i * kMaxS + k];
+      const double a2 = cp.A2[i * kMaxS + k];
+      if (a1 != 0.0) m1 = fma(a1, y[k], m1);
+      if (a2 != 0.0) m2 = fma(a2, ky[k], m2);
+    }
+    out[i] += fma(d, m1, m2);
+  }
+  store_row<S, EXACT>(R + row * s, s, out);
+}
+
+void launch_coupled(pint_op op, const double* Y, const double* B, const double* B0, double* R,
+                    cudaStream_t st) {
+  Coupling cp;
+  std::copy(op->A1, op->A1 + kMaxS * kMaxS, cp.A1);
+  std::copy(op->A2, op->A2 + kMaxS * kMaxS, cp.A2);
+  const int s = op->s;
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool E = decltype(E_)::value;
+    k_coupled<S, E><<<grid_for(op->n, 256), 256, 0, st>>>(op->n, s, op->sell.slice_ptr,
+                                                          op->sell.col, op->sellK, op->Mdiag, Y,
+                                                          B, B0, R, cp);
+  });
+  check_launch("k_coupled");
+  op->ctx->launches += 1;
+}
+
+// ------------------------------------------------------- inner SpMM (a4)
+// MODE 0: Z = J X ; MODE 1: Z = Rin - J X
+template <typename MT, typename VT, int S, bool EXACT, int MODE>
+__global__ void __launch_bounds__(256)
+k_spmm(int64_t n, int s, const int64_t* __restrict__ sptr, const int* __restrict__ col,
+       const MT* __restrict__ val, const VT* __restrict__ X, VT* __restrict__ Z,
+       const VT* __restrict__ Rin) {
+  using A = VT;
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const int64_t q = row >> 5;
+  const int lane = (int)(row & 31);
+  const int64_t b0 = sptr[q];
+  const int w = (int)((sptr[q + 1] - b0) >> 5);
+  A acc[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) acc[k] = A(0);
+  const MT* vp = val + b0 + lane;
+  const int* cpp = col + b0 + lane;
+  for (int t = 0; t < w; ++t) {
+    const A v = to_acc(vp[(int64_t)t * 32], A(0));
+    const int c = __ldg(cpp + (int64_t)t * 32);
+    A x[S];
+    load_row<S, EXACT>(X + (int64_t)c * s, s, x);
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc[k] = fma(v, x[k], acc[k]);
+  }
+  if constexpr (MODE == 1) {
+    A r[S];
+    load_row<S, EXACT>(Rin + row * s, s, r);
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc[k] = r[k] - acc[k];
+  }
+  store_row<S, EXACT>(Z + row * s, s, acc);
+}
+
+void launch_inner_spmm(pint_op op, int precision, bool jacobi, const void* X, void* Z,
+                       const void* Rin, cudaStream_t st) {
+  void* val = inner_sell(op, precision, jacobi, st);
+  const int s = op->s;
+  const unsigned g = grid_for(op->n, 256);
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool E = decltype(E_)::value;
+    auto& P = op->sell;
+    if (precision == PINT_FP64) {
+      if (Rin)
+        k_spmm<double, double, S, E, 1><<<g, 256, 0, st>>>(
+            op->n, s, P.slice_ptr, P.col, (const double*)val, (const double*)X, (double*)Z,
+            (const double*)Rin);
+      else
+        k_spmm<double, double, S, E, 0><<<g, 256, 0, st>>>(
+            op->n, s, P.slice_ptr, P.col, (const double*)val, (const double*)X, (double*)Z,
+            nullptr);
+    } else if (precision == PINT_FP32) {
+      if (Rin)
+        k_spmm<float, float, S, E, 1><<<g, 256, 0, st>>>(
+            op->n, s, P.slice_ptr, P.col, (const float*)val, (const float*)X, (float*)Z,
+            (const float*)Rin);
+      else
+        k_spmm<float, float, S, E, 0><<<g, 256, 0, st>>>(
+            op->n, s, P.slice_ptr, P.col, (const float*)val, (const float*)X, (float*)Z, nullptr);
+    } else {
+      if (Rin)
+        k_spmm<__nv_bfloat16, float, S, E, 1><<<g, 256, 0, st>>>(
+            op->n, s, P.slice_ptr, P.col, (const __nv_bfloat16*)val, (const float*)X, (float*)Z,
+            (const float*)Rin);
+      else
+        k_spmm<__nv_bfloat16, float, S, E, 0><<<g, 256, 0, st>>>(
+            op->n, s, P.slice_ptr, P.col, (const __nv_bfloat16*)val, (const float*)X, (float*)Z,
+            nullptr);
+    }
+  });
+  check_launch("k_spmm");
+  op->ctx->launches += 1;
+}
+
+// ---------------------------------------------------------- column norms
+constexpr int kNormBlocks = 512;
+
+template <typename VT, int S, bool EXACT>
+__global__ void __launch_bounds__(256)
+k_colsq(int64_t n, int s, const VT* __restrict__ X, double* __restrict__ partial) {
+  double acc[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) acc[k] = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    VT x[S];
+    load_row<S, EXACT>(X + r * s, s, x);
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc[k] = fma((double)x[k], (double)x[k], acc[k]);
+  }
+  __shared__ double red[8][S];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    double v = warp_sum(acc[k]);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < S) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+    partial[blockIdx.x * kMaxS + threadIdx.x] = v;
+  }
+}
+
+__global__ void k_colsq_final(int nblk, int s, const double* __restrict__ partial,
+                              double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= s) return;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += partial[b * kMaxS + k];
+  out[k] = sqrt(v);
+}
+
+void launch_colnorm(pint_ctx ctx, int precision, int64_t n, int s, const void* X, double* out,
+                    cudaStream_t st) {
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kNormBlocks, (n + 255) / 256));
+  double* partial = ctx->d_small + kSmallNormPartial;
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool E = decltype(E_)::value;
+    if (precision == PINT_FP64)
+      k_colsq<double, S, E><<<nb, 256, 0, st>>>(n, s, (const double*)X, partial);
+    else
+      k_colsq<float, S, E><<<nb, 256, 0, st>>>(n, s, (const float*)X, partial);
+  });
+  k_colsq_final<<<1, 32, 0, st>>>(nb, s, partial, out);
+  check_launch("k_colsq");
+  ctx->launches += 2;
+}
+
+// ---------------------------------------------------- outer update (a10)
+// Y[r][k] -= colscale[k] * rowscale[r] * V[r][k]
+template <typename VT>
+__global__ void k_outer_update(int64_t n, int s, double* __restrict__ Y, const VT* __restrict__ V,
+                               const double* __restrict__ colscale,
+                               const double* __restrict__ rowscale) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * s) return;
+  const int64_t r = i / s;
+  const int k = (int)(i - r * s);
+  double v = (double)V[i] * colscale[k];
+  if (rowscale) v *= rowscale[r];
+  Y[i] -= v;
+}
+
+void launch_outer_update(int precision, int64_t n, int s, double* Y, const void* V,
+                         const double* colscale, const double* rowscale, cudaStream_t st,
+                         pint_ctx ctx) {
+  const unsigned g = grid_for(n * s, 256);
+  if (precision == PINT_FP64)
+    k_outer_update<double><<<g, 256, 0, st>>>(n, s, Y, (const double*)V, colscale, rowscale);
+  else
+    k_outer_update<float><<<g, 256, 0, st>>>(n, s, Y, (const float*)V, colscale, rowscale);
+  check_launch("k_outer_update");
+  ctx->launches += 1;
+}
+
+// dst = src / colscale (per column); dst float64 or float32 (round to nearest)
+template <typename OT>
+__global__ void k_scale_cast(int64_t n, int s, const double* __restrict__ src, OT* __restrict__ dst,
+                             const double* __restrict__ colnorm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * s) return;
+  const int k = (int)(i % s);
+  const double c = colnorm ? colnorm[k] : 1.0;
+  const double v = c > 0.0 ? src[i] / c : 0.0;
+  if constexpr (std::is_same<OT, double>::value) dst[i] = v;
+  else dst[i] = __double2float_rn(v);
+}
+
+void launch_scale_cast(int64_t n, int s, const double* src, float* dst, const double* colnorm,
+                       cudaStream_t st, pint_ctx ctx) {
+  k_scale_cast<float><<<grid_for(n * s, 256), 256, 0, st>>>(n, s, src, dst, colnorm);
+  check_launch("k_scale_cast");
+  ctx->launches += 1;
+}
+
+void launch_scale_copy64(int64_t n, int s, const double* src, double* dst, const double* colnorm,
+                         cudaStream_t st, pint_ctx ctx) {
+  k_scale_cast<double><<<grid_for(n * s, 256), 256, 0, st>>>(n, s, src, dst, colnorm);
+  check_launch("k_scale_copy64");
+  ctx->launches += 1;
+}
+
+void launch_copy_cast(int precision, int64_t n, int s, const double* src, void* dst,
+                      cudaStream_t st, pint_ctx ctx) {
+  if (precision == PINT_FP64)
+    k_scale_cast<double><<<grid_for(n * s, 256), 256, 0, st>>>(n, s, src, (double*)dst, nullptr);
+  else
+    k_scale_cast<float><<<grid_for(n * s, 256), 256, 0, st>>>(n, s, src, (float*)dst, nullptr);
+  check_launch("k_copy_cast");
+  ctx->launches += 1;
+}
+
+// ---------------------------------------------------------------- shift
+__global__ void k_shift(int64_t n, int s, double* __restrict__ Y) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double* y = Y + r * s;
+  for (int k = 0; k + 1 < s; ++k) y[k] = y[k + 1];
+}
+
+void launch_shift(double* Y, int64_t n, int s, cudaStream_t st, pint_ctx ctx) {
+  k_shift<<<grid_for(n, 256), 256, 0, st>>>(n, s, Y);
+  check_launch("k_shift");
+  if (ctx) ctx->launches += 1;
+}
+
+}  // namespace pint

@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports every symbol include/pint.h declares
+(no compute calls: runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pint.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pint_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = _declared()
+    for must in ("pint_create", "pint_operator_assemble", "pint_set_coupling",
+                 "pint_apply_coupled", "pint_solve_block", "pint_newton_step", "pint_shift",
+                 "pint_pipeline_run", "pint_coupling_from_dirk"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2504_02117_gb300.build import build
+    lib_path = build()
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header():
+    import paper_2504_02117_gb300 as P
+    missing = [n for n in _declared() if not hasattr(P, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls_without_gpu():
+    """Calls that touch no device: defaults, the DIRK coupling builder (theta
+    example of Sec. 2.1 after elimination) and argument validation."""
+    import numpy as np
+    import paper_2504_02117_gb300 as P
+    o = P.pint_opts_default()
+    assert o.restart == 30 and o.tol == 1e-10
+    th, tau = 0.3, 0.25
+    A = np.array([[0.0, 0.0], [1 - th, th]])
+    A1, A2, e = P.pint_coupling_from_dirk(A, 4, tau, eliminate_first=True)
+    np.testing.assert_allclose(A1, (np.eye(4) - np.eye(4, k=-1)) / tau)
+    np.testing.assert_allclose(A2, th * np.eye(4) + (1 - th) * np.eye(4, k=-1))
+    np.testing.assert_allclose(e, [1 - th])
+    with pytest.raises(P.PintError):
+        P.pint_coupling_from_dirk(np.array([[1.0, 0.0], [0.5, 0.5]]), 2, tau, eliminate_first=True)
+    with pytest.raises(P.PintError):
+        P.pint_coupling_from_dirk(np.eye(3), 6, tau)        # 18 > 16 columns
+    assert P.lib.pint_shift(None, 10, 2, None) == P.PINT_ERR_INVALID
+
+
+def test_dirk_builder_matches_oracle():
+    import numpy as np
+    import paper_2504_02117_gb300 as P
+    from oracle import coupling
+    for tab in (coupling.implicit_euler(), coupling.sdirk2()):
+        for steps in (1, 3):
+            A1, A2, _ = P.pint_coupling_from_dirk(tab[0], steps, 0.1)
+            R1, R2, _ = coupling.multistep_matrices(tab[0], steps, 0.1)
+            np.testing.assert_array_equal(A1, R1)
+            np.testing.assert_array_equal(A2, R2)

@@ -1,0 +1,200 @@
+"""GPU parity of the building-block kernels against the oracle (float64
+definition) through the C ABI. Sizes span several SELL slices / CTAs and a
+ragged tail (N not a multiple of 32)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import coupling, fv, krylov, slab
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(13, 11, 7), (64, 64, 1), (5, 3, 1)]
+SS = [1, 2, 3, 4, 5, 8, 13, 16]
+
+
+def _dev(a, dtype=None):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), device="cuda",
+                        dtype=dtype or torch.float64)
+
+
+def _problem(dims, seed=0, v=(1.0, -0.5, 0.25)):
+    n = int(np.prod(dims))
+    D = np.exp(synth.normal(seed, n)).reshape(dims[::-1])
+    K = fv.convdiff_matrix(dims, D, v if dims[2] > 1 else (v[0], v[1], 0.0))
+    return D, K, n
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("s", SS)
+def test_apply_coupled_matches_oracle(P, ctx, dims, s):
+    import torch
+    D, K, n = _problem(dims, 1)
+    v = (1.0, -0.5, 0.25) if dims[2] > 1 else (1.0, -0.5, 0.0)
+    op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), v)
+    try:
+        rng = np.random.default_rng(s)
+        A1 = rng.standard_normal((s, s))
+        A2 = rng.standard_normal((s, s))
+        A1[0, 0] = 3.0
+        A1[np.abs(A1) < 0.3] = 0.0          # exercise the zero-skipping branches
+        P.pint_set_coupling(ctx, op, A1, A2)
+        Y, B, B0 = (synth.uniform(10 + i, n * s).reshape(n, s) for i in range(3))
+        R = torch.empty(n, s, device="cuda", dtype=torch.float64)
+        P.pint_apply_coupled(ctx, op, _dev(Y), _dev(B), _dev(B0), R)
+        ref = slab.coupled_residual(K, np.ones(n), A1, A2, Y, B, B0)
+        scale = np.abs(K).max() * np.abs(A2).sum(axis=1).max() * 10
+        np.testing.assert_allclose(R.cpu().numpy(), ref, rtol=0, atol=1e-13 * scale)
+        P.pint_apply_coupled(ctx, op, _dev(Y), None, None, R)
+        ref = slab.coupled_residual(K, np.ones(n), A1, A2, Y)
+        np.testing.assert_allclose(R.cpu().numpy(), ref, rtol=0, atol=1e-13 * scale)
+    finally:
+        P.pint_operator_destroy(op)
+
+
+def test_operator_assemble_csr_with_mass(P, ctx):
+    """User CSR (host and device) with a diagonal mass matrix."""
+    import torch
+    D, K, n = _problem((9, 7, 5), 2)
+    rng = np.random.default_rng(0)
+    M = 0.5 + rng.random(n)
+    s = 4
+    A, _, _ = coupling.implicit_euler()
+    A1, A2, _ = coupling.multistep_matrices(A, s, 0.01)
+    Y = rng.standard_normal((n, s))
+    ref = slab.coupled_residual(K, M, A1, A2, Y)
+    for dev in (False, True):
+        args = [K.indptr.astype(np.int32), K.indices.astype(np.int32), K.data, M]
+        if dev:
+            args = [torch.tensor(a, device="cuda") for a in args]
+        op = P.pint_operator_assemble(ctx, n, *args)
+        P.pint_set_coupling(ctx, op, A1, A2)
+        R = torch.empty(n, s, device="cuda", dtype=torch.float64)
+        P.pint_apply_coupled(ctx, op, _dev(Y), None, None, R)
+        np.testing.assert_allclose(R.cpu().numpy(), ref, rtol=1e-14, atol=1e-9)
+        assert P.pint_operator_nnz(op) == K.nnz
+        P.pint_operator_destroy(op)
+
+
+def test_operator_assemble_rejects_bad_csr(P, ctx):
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([1, 0], dtype=np.int32)       # no diagonal entries
+    with pytest.raises(P.PintError):
+        P.pint_operator_assemble(ctx, 2, rp, ci, np.ones(2))
+
+
+@pytest.mark.parametrize("s", [1, 3, 8, 16])
+def test_inner_apply_and_jacobi(P, ctx, s):
+    import torch
+    dims = (13, 11, 7)
+    D, K, n = _problem(dims, 3)
+    op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), (1.0, -0.5, 0.25))
+    try:
+        A, _, _ = coupling.sdirk2()
+        tau = 0.02
+        A1 = np.eye(s) / tau
+        A2 = np.eye(s) * A[0, 0]
+        P.pint_set_coupling(ctx, op, A1, A2)
+        X = synth.uniform(5, n * s).reshape(n, s)
+        Z = torch.empty(n, s, device="cuda", dtype=torch.float64)
+        P.pint_inner_apply(ctx, op, _dev(X), Z)
+        J = sp.identity(n) / tau + A[0, 0] * K
+        np.testing.assert_allclose(Z.cpu().numpy(), J @ X, rtol=1e-13, atol=1e-10)
+        P.pint_precond_apply(ctx, op, P.PINT_PC_JACOBI, _dev(X), Z)
+        np.testing.assert_allclose(Z.cpu().numpy(), krylov.jacobi(J.tocsr())(X), rtol=1e-15)
+    finally:
+        P.pint_operator_destroy(op)
+
+
+@pytest.mark.parametrize("dims", [(13, 11, 7), (40, 33, 1)])
+@pytest.mark.parametrize("s", [1, 3, 8, 16])
+def test_ilu0_apply_matches_oracle(P, ctx, dims, s):
+    import torch
+    D, K, n = _problem(dims, 4)
+    v = (1.0, -0.5, 0.25) if dims[2] > 1 else (1.0, -0.5, 0.0)
+    op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), v)
+    try:
+        tau = 1e-3
+        P.pint_set_coupling(ctx, op, np.eye(s) / tau, np.eye(s))
+        J = sp.csr_matrix(sp.identity(n) / tau + K)
+        J.sort_indices()
+        X = synth.uniform(6, n * s).reshape(n, s)
+        Z = torch.empty(n, s, device="cuda", dtype=torch.float64)
+        P.pint_precond_apply(ctx, op, P.PINT_PC_ILU0, _dev(X), Z)
+        ref = krylov.ilu0_apply(*krylov.ilu0(J))(X)
+        np.testing.assert_allclose(Z.cpu().numpy(), ref, rtol=1e-11, atol=1e-14)
+    finally:
+        P.pint_operator_destroy(op)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("s,nb", [(1, 1), (1, 31), (3, 7), (4, 31), (8, 12), (16, 1), (16, 31)])
+def test_gram_update_colnorms(P, ctx, prec, s, nb):
+    import torch
+    n = 4099
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    code = P.PINT_FP64 if prec == "fp64" else P.PINT_FP32
+    V = synth.uniform(7, nb * n * s).reshape(nb, n, s)
+    W = synth.uniform(8, n * s).reshape(n, s)
+    if prec == "fp32":
+        V = V.astype(np.float32).astype(np.float64)
+        W = W.astype(np.float32).astype(np.float64)
+    Vd, Wd = _dev(V, dt), _dev(W, dt)
+    H = torch.empty(nb * s, s, device="cuda", dtype=torch.float64)
+    P.pint_block_gram(ctx, code, n, s, nb, Vd, Wd, H)
+    Vm = np.concatenate([V[b] for b in range(nb)], axis=1)      # n x (nb s)
+    ref = Vm.T @ W
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    np.testing.assert_allclose(H.cpu().numpy(), ref, rtol=0, atol=tol * np.sqrt(n))
+    Hh = synth.uniform(9, nb * s * s).reshape(nb * s, s) * 0.1
+    P.pint_block_update(ctx, code, n, s, nb, Vd, _dev(Hh), Wd)
+    ref = W - Vm @ Hh
+    tol = 1e-13 if prec == "fp64" else 1e-5
+    np.testing.assert_allclose(Wd.double().cpu().numpy(), ref, rtol=0, atol=tol * nb * s)
+    nrm = P.pint_colnorms(ctx, code, n, s, Wd)
+    np.testing.assert_allclose(nrm, np.linalg.norm(Wd.double().cpu().numpy(), axis=0),
+                               rtol=1e-12 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("s", [1, 2, 5, 8, 16])
+def test_cholqr2_matches_oracle(P, ctx, s):
+    import torch
+    n = 2053
+    W = synth.uniform(3, n * s).reshape(n, s) @ np.diag(np.logspace(0, 3, s))
+    Wd = _dev(W)
+    R = torch.empty(s, s, device="cuda", dtype=torch.float64)
+    P.pint_cholqr2(ctx, P.PINT_FP64, n, s, Wd, R)
+    Q = Wd.cpu().numpy()
+    Qr, Rr = krylov.cholqr2(W)
+    np.testing.assert_allclose(R.cpu().numpy(), Rr, rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(Q, Qr, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(s), atol=1e-13)
+
+
+def test_cholqr2_deflation_no_nan(P, ctx):
+    import torch
+    n, s = 1000, 4
+    W = synth.uniform(4, n * s).reshape(n, s)
+    W[:, 2] = W[:, 0]
+    W[:, 3] = 0.0
+    Wd = _dev(W)
+    R = torch.empty(s, s, device="cuda", dtype=torch.float64)
+    P.pint_cholqr2(ctx, P.PINT_FP64, n, s, Wd, R)
+    Q = Wd.cpu().numpy()
+    assert np.all(np.isfinite(Q)) and np.all(np.isfinite(R.cpu().numpy()))
+    np.testing.assert_allclose(Q[:, 2:], 0.0)
+    np.testing.assert_allclose(Q @ R.cpu().numpy(), W, atol=1e-12)
+
+
+@pytest.mark.parametrize("s", [2, 5, 16])
+def test_shift(P, s):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n = 77
+    Y = np.arange(n * s, dtype=np.float64).reshape(n, s)
+    Yd = _dev(Y)
+    P.pint_shift(Yd, n, s)
+    np.testing.assert_array_equal(Yd.cpu().numpy(), coupling.shift(Y))
