@@ -77,6 +77,9 @@ typedef struct pint_problem_s* pint_problem;
 typedef struct {
   double tol;        /* outer: ||R_k||_2 <= tol ||F_k||_2, F = B A2^T + B0   */
   double inner_tol;  /* inner block GMRES: per-column relative reduction    */
+  double max_step;   /* Newton calls only: if > 0, column k of the update V
+                        is scaled by min(1, max_step / max_r |V_rk|) (a step
+                        bound; the paper gives no globalisation). 0 = off    */
   int restart;       /* GMRES restart length m, 1..PINT_MAX_RESTART (30)    */
   int max_outer;     /* outer (defect-correction / Newton) iteration limit  */
   int max_inner;     /* block Arnoldi steps per inner solve                 */
@@ -202,9 +205,11 @@ int pint_problem_residual(pint_problem prob, const double* times,
                           const double* Y, const double* B0, double* R,
                           void* stream);
 /* One simplified-Newton iteration of Algorithm 1 on the current window:
- * R = R(Y); if ||R_0|| <= tol * max(||B0_0||, tiny) set *converged = 1 and
+ * R = R(Y); if ||R_0|| <= tol * ||B0_0|| (tol alone if B0_0 = 0) set
+ * *converged = 1 and
  * return; else J = alpha M'(Y_0) + beta Df(t_0, Y_0), solve J V = R with
- * block GMRES (inner_tol), Y <- Y - V, *converged = 0. Synchronous. */
+ * block GMRES (inner_tol), Y <- Y - V (each column's step bounded by
+ * opts.max_step when it is > 0), *converged = 0. Synchronous. */
 int pint_newton_step(pint_problem prob, const double* times, double* Y,
                      const double* B0, const pint_opts* opts, int* converged,
                      pint_stats* stats, void* stream);
@@ -217,6 +222,37 @@ int pint_pipeline_run(pint_problem prob, const double* A, const double* c,
                       int m, double tau, int s, const double* y0,
                       int nstages, double* stages_out, const pint_opts* opts,
                       pint_stats* stats, void* stream);
+
+/* --------------------------------------------------------------- profiler
+ * Kernel families, for per-family CUDA-event timing. When the profiler is on,
+ * each family's launches are bracketed by events on the launching stream;
+ * every launch also books the family's algorithmic bytes and flops (the
+ * CSR-form figures: matrix values + int32 column indices + rowptr, each
+ * block vector read once and written once). */
+enum {
+  PINT_K_COUPLED = 0, /* fused coupled residual (linear and nonlinear)        */
+  PINT_K_SPMM,        /* inner operator apply J X                             */
+  PINT_K_GRAM,        /* block Gram products [V]^T W                          */
+  PINT_K_UPDATE,      /* block AXPY with a small matrix                       */
+  PINT_K_CHOLQR,      /* CholQR2 (its Gram, Cholesky, scaling)                */
+  PINT_K_HESS,        /* block Hessenberg least squares                       */
+  PINT_K_ILU,         /* ILU(0) factorisation and sweeps                      */
+  PINT_K_NORM,        /* column norms                                         */
+  PINT_K_VEC,         /* outer update, casts, axpy, shift, B0 terms           */
+  PINT_K_NL,          /* nonlinear pointwise, Jacobian and single-column eval */
+  PINT_K_COUNT
+};
+/* Turn event timing on (1) or off (0). Launch, byte and flop counts are
+ * always kept. */
+int pint_profile_enable(pint_ctx ctx, int on);
+/* Synchronizes the device, folds finished event pairs into the totals and
+ * returns family `k`'s totals since the last reset (any pointer may be
+ * NULL). */
+int pint_profile_read(pint_ctx ctx, int k, double* ms, double* bytes,
+                      double* flops, long long* launches);
+int pint_profile_reset(pint_ctx ctx);
+/* Kernels this context has launched since it was created. */
+long long pint_kernel_launches(pint_ctx ctx);
 
 /* ------------------------------------------- building blocks (test access)
  * The kernels of the inner solve, exposed for parity tests. `precision`

@@ -14,7 +14,8 @@ Semi-discrete form M(y)' + f(t, y) = 0 with f(t,y) = K[y] y - b(t)
   for each window the residual
       R(Y) = M(Y) A1^T + F(T, Y) A2^T - B0        (sign read as "+ F A2^T")
   of Eq. matrix-equation-pipelining is driven to ||R_0|| <= eps ||F_0|| in
-  column 0 by simplified Newton steps with the first column's Jacobian
+  column 0 (F_0 = B0_0) by simplified Newton steps with the first column's
+  Jacobian
       J = (1/tau) M'(Y_0) + a_kk Df(t_0, Y_0),
   each solving J V = R for all s columns with block GMRES; then the window is
   shifted (Eq. shift) by one stage.
@@ -140,9 +141,16 @@ def window_residual(prob, A1, A2, times, Y, B0):
 
 
 def pipelined_block_newton(prob, A, c, tau, y0, nstages, s, tol=1e-8, inner_tol=1e-5,
-                           precond="ilu0", restart=30, max_newton=50, inner_maxit=1000):
+                           precond="ilu0", restart=30, max_newton=50, inner_maxit=1000,
+                           max_step=None):
     """Algorithm 1 over `nstages` global stages with a window of s stages.
-    Returns (stages N x nstages, stats dict)."""
+    Returns (stages N x nstages, stats dict).
+
+    max_step (reading, the paper gives no globalisation): when set, column k
+    of each Newton update V is scaled by min(1, max_step / max_r |V_rk|). The
+    trailing columns of a window take chord steps with the first column's
+    Jacobian; for Richards' equation they can otherwise leave the physical
+    range of heads and poison later windows."""
     y0 = np.asarray(y0, dtype=np.float64)
     N = len(y0)
     Y = np.repeat(y0[:, None], s, axis=1)
@@ -165,6 +173,9 @@ def pipelined_block_newton(prob, A, c, tau, y0, nstages, s, tol=1e-8, inner_tol=
             V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R, inner_tol, restart,
                                          inner_maxit)
             inner_its += info["iters"]
+            if max_step:
+                vmax = np.max(np.abs(V), axis=0)
+                V = V * np.minimum(1.0, max_step / np.maximum(vmax, 1e-300))
             Y = Y - V
         newton_its.append(it)
         stages[g0] = Y[:, 0].copy()

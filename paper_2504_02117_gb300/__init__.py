@@ -26,6 +26,8 @@ PINT_MEM_HOST, PINT_MEM_DEVICE = 0, 1
 PINT_PC_NONE, PINT_PC_JACOBI, PINT_PC_ILU0 = 0, 1, 2
 PINT_FP64, PINT_FP32, PINT_BF16 = 0, 1, 2
 PINT_PROBLEM_DIFFREACT, PINT_PROBLEM_RICHARDS = 1, 2
+KERNEL_FAMILIES = ["coupled", "spmm", "gram", "update", "cholqr", "hess", "ilu", "norm", "vec",
+                   "nl"]
 
 _STATUS = {0: "PINT_OK", 1: "PINT_ERR_INVALID", 2: "PINT_ERR_NOMEM", 3: "PINT_ERR_CUDA",
            4: "PINT_ERR_NOT_CONVERGED", 5: "PINT_ERR_BREAKDOWN", 6: "PINT_ERR_TIMEOUT"}
@@ -38,7 +40,8 @@ class PintError(RuntimeError):
 
 
 class pint_opts(C.Structure):
-    _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("restart", C.c_int),
+    _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("max_step", C.c_double),
+                ("restart", C.c_int),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("reserved", C.c_int * 3)]
 
@@ -87,6 +90,11 @@ _SIGS = {
                               C.POINTER(pint_stats), _vp]),
     "pint_pipeline_run": (_i, [_vp, _vp, _vp, _i, _d, _i, _vp, _i, _vp, C.POINTER(pint_opts),
                                C.POINTER(pint_stats), _vp]),
+    "pint_profile_enable": (_i, [_vp, _i]),
+    "pint_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d),
+                               C.POINTER(C.c_longlong)]),
+    "pint_profile_reset": (_i, [_vp]),
+    "pint_kernel_launches": (C.c_longlong, [_vp]),
     "pint_inner_apply": (_i, [_vp, _vp, _vp, _vp]),
     "pint_precond_apply": (_i, [_vp, _i, _vp, _vp, _vp]),
     "pint_block_gram": (_i, [_vp, _i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
@@ -305,3 +313,22 @@ def pint_colnorms(ctx, precision, n, s, X, stream=None):
     out = np.zeros(s)
     _check(lib.pint_colnorms(ctx, precision, n, s, _ptr(X), _ptr(out), _stream(stream)), ctx)
     return out
+
+
+def pint_profile_enable(ctx, on=True):
+    _check(lib.pint_profile_enable(ctx, int(bool(on))), ctx)
+
+
+def pint_profile_read(ctx, k):
+    """Totals of kernel family k: dict(ms, bytes, flops, launches)."""
+    ms, by, fl, la = C.c_double(), C.c_double(), C.c_double(), C.c_longlong()
+    _check(lib.pint_profile_read(ctx, k, C.byref(ms), C.byref(by), C.byref(fl), C.byref(la)), ctx)
+    return {"ms": ms.value, "bytes": by.value, "flops": fl.value, "launches": la.value}
+
+
+def pint_profile_reset(ctx):
+    _check(lib.pint_profile_reset(ctx), ctx)
+
+
+def pint_kernel_launches(ctx):
+    return lib.pint_kernel_launches(ctx)

@@ -231,6 +231,12 @@ int pint_create(pint_ctx* out, int device, size_t budget) {
 int pint_destroy(pint_ctx ctx) {
   if (!ctx) return PINT_ERR_INVALID;
   cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& r : ctx->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   dfree(ctx, ctx->d_small, sizeof(double) * kSmallDoubles);
   dfree(ctx, ctx->d_flag, 64 * sizeof(int));
   dfree(ctx, ctx->d_partial, ctx->partial_bytes);
@@ -492,5 +498,60 @@ int pint_colnorms(pint_ctx ctx, int precision, int64_t n, int s, const void* X, 
     return PINT_OK;
   });
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------- profiler
+namespace pint {
+static void prof_collect(pint_ctx ctx) {
+  if (ctx->prof_pending.empty()) return;
+  PINT_CUDA(cudaDeviceSynchronize());
+  for (auto& r : ctx->prof_pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->prof_ms[r.fam] += ms;
+    ctx->ev_pool.push_back(r.a);
+    ctx->ev_pool.push_back(r.b);
+  }
+  ctx->prof_pending.clear();
+}
+}  // namespace pint
+
+extern "C" {
+
+int pint_profile_enable(pint_ctx ctx, int on) {
+  if (!ctx) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    ctx->prof_on = on != 0;
+    return PINT_OK;
+  });
+}
+
+int pint_profile_read(pint_ctx ctx, int k, double* ms, double* bytes, double* flops,
+                      long long* launches) {
+  if (!ctx) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    PINT_REQUIRE(k >= 0 && k < PF_COUNT, PINT_ERR_INVALID, "kernel family");
+    prof_collect(ctx);
+    if (ms) *ms = ctx->prof_ms[k];
+    if (bytes) *bytes = ctx->prof_bytes[k];
+    if (flops) *flops = ctx->prof_flops[k];
+    if (launches) *launches = ctx->prof_launches[k];
+    return PINT_OK;
+  });
+}
+
+int pint_profile_reset(pint_ctx ctx) {
+  if (!ctx) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    prof_collect(ctx);
+    for (int k = 0; k < PF_COUNT; ++k) {
+      ctx->prof_ms[k] = ctx->prof_bytes[k] = ctx->prof_flops[k] = 0.0;
+      ctx->prof_launches[k] = 0;
+    }
+    return PINT_OK;
+  });
+}
+
+long long pint_kernel_launches(pint_ctx ctx) { return ctx ? ctx->launches : -1; }
 
 }  // extern "C"

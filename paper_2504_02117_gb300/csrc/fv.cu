@@ -429,6 +429,9 @@ static void nl_residual(pint_problem p, const double* times, const double* Y, co
     TH = p->scratch;
     KR = p->scratch + n * s;
   }
+  ProfScope ps(p->ctx, PF_COUPLED,
+               8.0 * n * s * (2 + (B0 ? 1 : 0) + (p->kind == PINT_PROBLEM_RICHARDS ? 4 : 0)),
+               30.0 * n * s, st);
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool E = decltype(E_)::value;
@@ -445,6 +448,7 @@ static void nl_residual(pint_problem p, const double* times, const double* Y, co
 static void nl_eval(pint_problem p, double t, const double* y, double* m, double* f,
                     cudaStream_t st) {
   NlParams P = params_of(p, &t, 1);
+  ProfScope ps(p->ctx, PF_NL, 24.0 * p->n, 30.0 * p->n, st);
   k_nl_eval<<<grid_for(p->n, 128), 128, 0, st>>>(grid_of(p), p->n, P, y, m, f);
   check_launch("k_nl_eval");
   p->ctx->launches += 1;
@@ -459,6 +463,7 @@ static void nl_jacobian(pint_problem p, double t, const double* Y, int ys, cudaS
     op->Jinvdiag = dalloc_n<double>(op->ctx, op->n);
   }
   NlParams P = params_of(p, &t, 1);
+  ProfScope ps(p->ctx, PF_NL, 8.0 * op->nnz + 24.0 * p->n, 60.0 * p->n, st);
   k_nl_jacobian<<<grid_for(p->n, 128), 128, 0, st>>>(grid_of(p), p->n, P, Y, ys, op->alpha,
                                                      op->beta, op->rowptr, op->Jval, op->Jdiag,
                                                      op->Jinvdiag);
@@ -518,8 +523,14 @@ static void newton_step(pint_problem p, const double* times, double* Y, const do
     stats->restarts += ir.cycles;
     stats->deflations += ir.deflations;
   }
-  launch_outer_update(wprec, n, s, Y, Xk, rnorm,
-                      o->precond == PINT_PC_JACOBI ? op->Jinvdiag : nullptr, st, ctx);
+  const double* rs = o->precond == PINT_PC_JACOBI ? op->Jinvdiag : nullptr;
+  const double* cs = rnorm;
+  if (o->max_step > 0.0) {
+    double* bounded = ctx->d_small + kSmallScratch + 128;
+    launch_step_bound(wprec, n, s, Xk, rs, rnorm, o->max_step, bounded, st, ctx);
+    cs = bounded;
+  }
+  launch_outer_update(wprec, n, s, Y, Xk, cs, rs, st, ctx);
 }
 
 // Window of s consecutive stages starting at global stage g0 (0-based) of the

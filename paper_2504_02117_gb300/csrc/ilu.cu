@@ -303,6 +303,7 @@ void ilu_setup(pint_op op, cudaStream_t st) {
   Sched& sc = schedule(op, true, 32);
   const unsigned ep = next_epoch(op, S->epoch_f, S->flag_f, st);
   PINT_CUDA(cudaMemsetAsync(S->ticket, 0, sizeof(int), st));
+  ProfScope ps(op->ctx, PF_ILU, op->nnz * 28.0 + 12.0 * op->n, 2.0 * op->nnz * 3, st);
   k_ilu_factor<<<sweep_grid(op, sc.nchunk), 256, 0, st>>>(op->rowptr, op->colind, op->diagpos,
                                                           S->F64, sc.order, sc.chunk, sc.nchunk,
                                                           S->flag_f, ep, S->ticket, S->err);
@@ -327,6 +328,10 @@ static void apply_t(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st
   const unsigned ef = next_epoch(op, S->epoch_f, S->flag_f, st);
   const unsigned eb = next_epoch(op, S->epoch_b, S->flag_b, st);
   PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
+  ProfScope ps(op->ctx, PF_ILU,
+               op->nnz * (sizeof(VT) + 4.0) + 4.0 * (op->n + 1) + 8.0 * op->n + 8.0 * op->n +
+                   4.0 * sizeof(VT) * op->n * s,
+               2.0 * op->nnz * s, st);
   k_ilu_sweep<VT, true><<<sweep_grid(op, f.nchunk), 256, 0, st>>>(
       s, spl, op->rowptr, op->colind, op->diagpos, F, f.order, f.chunk, f.nchunk, X, Z, S->flag_f,
       ef, S->ticket, S->err);

@@ -156,6 +156,28 @@ struct SellPattern {
 
 }  // namespace pint
 
+namespace pint {
+// Kernel families for the optional CUDA-event profiler (pint_profile_*).
+enum ProfFamily {
+  PF_COUPLED = 0,  // fused coupled residual (k_coupled, k_nl_residual)
+  PF_SPMM,         // inner operator apply (k_spmm)
+  PF_GRAM,         // block Gram products (k_gram + reduce)
+  PF_UPDATE,       // block AXPY with a small matrix (k_update)
+  PF_CHOLQR,       // CholQR pieces (k_chol, k_rowmul, small mm)
+  PF_HESS,         // Hessenberg least squares (k_hess_step, k_backsolve, init)
+  PF_ILU,          // ILU(0) factor and sweeps
+  PF_NORM,         // column norms
+  PF_VEC,          // outer update, casts, axpy, shift, B0 terms
+  PF_NL,           // nonlinear pointwise / Jacobian / eval kernels
+  PF_COUNT
+};
+struct ProfRec {
+  int fam;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+}  // namespace pint
+
 // ------------------------------------------------------------ opaque types
 struct pint_ctx_s {
   int device = 0;
@@ -172,6 +194,14 @@ struct pint_ctx_s {
   double* d_small = nullptr;     // 65536 doubles of small dense state
   int* d_flag = nullptr;         // 64 ints
   long launches = 0;
+  // profiler
+  bool prof_on = false;
+  std::vector<pint::ProfRec> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[pint::PF_COUNT] = {};
+  double prof_bytes[pint::PF_COUNT] = {};
+  double prof_flops[pint::PF_COUNT] = {};
+  long prof_launches[pint::PF_COUNT] = {};
 };
 
 namespace pint {
@@ -211,6 +241,45 @@ struct pint_op_s {
 
 namespace pint {
 
+// Records (when the context's profiler is on) a CUDA event pair around the
+// launches made in its scope and books algorithmic bytes / flops to `fam`.
+struct ProfScope {
+  pint_ctx c;
+  int fam;
+  double bytes, flops;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfScope(pint_ctx c_, int fam_, double bytes_, double flops_, cudaStream_t st_)
+      : c(c_), fam(fam_), bytes(bytes_), flops(flops_), st(st_) {
+    if (c) {
+      c->prof_launches[fam] += 1;
+      c->prof_bytes[fam] += bytes;
+      c->prof_flops[fam] += flops;
+    }
+    if (c && c->prof_on) {
+      a = take_event();
+      cudaEventRecord(a, st);
+    }
+  }
+  ~ProfScope() {
+    if (c && c->prof_on && a) {
+      cudaEvent_t b = take_event();
+      cudaEventRecord(b, st);
+      c->prof_pending.push_back({fam, a, b, bytes, flops});
+    }
+  }
+  cudaEvent_t take_event() {
+    if (!c->ev_pool.empty()) {
+      cudaEvent_t e = c->ev_pool.back();
+      c->ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
 // ----------------------------------------------------------- allocation
 void* dalloc(pint_ctx ctx, size_t bytes);
 void dfree(pint_ctx ctx, void* p, size_t bytes);
@@ -241,6 +310,10 @@ void launch_scale_copy64(int64_t n, int s, const double* src, double* dst,
 void launch_copy_cast(int precision, int64_t n, int s, const double* src, void* dst,
                       cudaStream_t st, pint_ctx ctx);
 void launch_shift(double* Y, int64_t n, int s, cudaStream_t st, pint_ctx ctx);
+// out[k] = rnorm[k] * min(1, delta / max_r |rnorm[k] rowscale[r] X[r][k]|)
+void launch_step_bound(int precision, int64_t n, int s, const void* X, const double* rowscale,
+                       const double* rnorm, double delta, double* out, cudaStream_t st,
+                       pint_ctx ctx);
 
 // ----------------------------------------------------------- krylov.cu
 void launch_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb, const void* V,

@@ -119,8 +119,9 @@ static void ensure_partial(pint_ctx ctx, size_t bytes) {
 
 template <typename VT>
 static void gram_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t bstride,
-                   const VT* W, double* H, cudaStream_t st) {
+                   const VT* W, double* H, cudaStream_t st, int fam = PF_GRAM) {
   const int P = nb * s;
+  ProfScope ps(ctx, fam, sizeof(VT) * (double)(nb + 1) * n * s, 2.0 * n * nb * s * s, st);
   PINT_REQUIRE(P <= 1024, PINT_ERR_INVALID, "Gram block too wide (nb*s > 1024)");
   int PT = 32;
   while (PT < P && PT < 256) PT <<= 1;
@@ -207,6 +208,8 @@ template <typename VT>
 static void update_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t bstride,
                      const double* H, VT* W, int mode, cudaStream_t st) {
   const int P = nb * s;
+  ProfScope ps(ctx, PF_UPDATE, sizeof(VT) * (double)n * s * (nb + (mode == 1 ? 1 : 2)),
+               2.0 * n * nb * s * s, st);
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool EX = decltype(E_)::value;
@@ -332,7 +335,8 @@ template <typename VT>
 static void cholqr_pass(pint_ctx ctx, int64_t n, int s, VT* W, double* R, double defl,
                         int* defl_count, cudaStream_t st) {
   CholScratch cs = chol_scratch(ctx);
-  gram_t<VT>(ctx, n, s, 1, W, 0, W, cs.G, st);
+  gram_t<VT>(ctx, n, s, 1, W, 0, W, cs.G, st, PF_CHOLQR);
+  ProfScope ps(ctx, PF_CHOLQR, 2.0 * sizeof(VT) * n * s, 1.0 * n * s * s, st);
   k_chol<<<1, 256, 0, st>>>(s, cs.G, defl, R, cs.Rinv, defl_count);
   check_launch("k_chol");
   with_s(s, [&](auto S_, auto E_) {
@@ -357,6 +361,7 @@ void cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W, double* R,
     cholqr_pass<float>(ctx, n, s, (float*)W, cs.R1, defl, defl_count, st);
     cholqr_pass<float>(ctx, n, s, (float*)W, cs.R2, defl, defl_count, st);
   }
+  ProfScope ps(ctx, PF_CHOLQR, 0.0, 2.0 * s * s * s, st);
   k_small_mm<<<1, 256, 0, st>>>(s, cs.R2, cs.R1, R);
   check_launch("k_small_mm");
   ctx->launches += 1;
@@ -610,7 +615,10 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
   while (res.its < o->max_inner) {
     res.cycles += 1;
     cholqr2(ctx, vprec, n, s, Vb(0), w->S, w->defl, st);
-    k_gr_init<<<8, 256, 0, st>>>(ldh, s, w->S, w->Gr);
+    {
+      ProfScope ps(ctx, PF_HESS, 0.0, 0.0, st);
+      k_gr_init<<<8, 256, 0, st>>>(ldh, s, w->S, w->Gr);
+    }
     check_launch("k_gr_init");
     ctx->launches += 1;
     int j = 0;
@@ -627,6 +635,7 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
       launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg2, st);
       launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg2, Vb(j + 1), 0, st);
       cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, st);
+      ProfScope psh(ctx, PF_HESS, 0.0, 4.0 * (j + 1) * s * s * (s + 1), st);
       k_hess_step<<<1, 512, 8 * (size_t)s * (j + 2) * s, st>>>(
           j, s, ldh, w->Hg1, w->Hg2, w->Rn, w->Hb, w->refl, w->Gr, w->target, w->est, w->flag);
       check_launch("k_hess_step");
@@ -644,13 +653,17 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
       }
     }
     const int kd = j * s;
-    k_backsolve<<<1, 512, 8 * (size_t)kd * s, st>>>(kd, s, ldh, w->Hb, w->Gr, w->Yls);
-    check_launch("k_backsolve");
-    ctx->launches += 1;
+    {
+      ProfScope ps(ctx, PF_HESS, 0.0, 1.0 * kd * kd * s, st);
+      k_backsolve<<<1, 512, 8 * (size_t)kd * s, st>>>(kd, s, ldh, w->Hb, w->Gr, w->Yls);
+      check_launch("k_backsolve");
+      ctx->launches += 1;
+    }
     if (ilu) {
       launch_update(ctx, vprec, n, s, j, w->V, bs, w->Yls, w->Zt, 1, st);
       void* tmp = Vb(std::min(j, m));   // block j is free after the cycle
       ilu_apply(op, prec, w->Zt, tmp, st);
+      ProfScope ps(ctx, PF_VEC, 3.0 * es * bs, 1.0 * bs, st);
       if (vprec == PINT_FP64)
         k_axpy<double><<<grid_for(bs, 256), 256, 0, st>>>(bs, (const double*)tmp, (double*)w->Xk);
       else

@@ -195,6 +195,14 @@ void launch_coupled(pint_op op, const double* Y, const double* B, const double* 
   std::copy(op->A1, op->A1 + kMaxS * kMaxS, cp.A1);
   std::copy(op->A2, op->A2 + kMaxS * kMaxS, cp.A2);
   const int s = op->s;
+  int nza = 0;
+  for (int i = 0; i < s; ++i)
+    for (int k = 0; k < s; ++k) nza += (op->A1[i * kMaxS + k] != 0.0) + (op->A2[i * kMaxS + k] != 0.0);
+  const double N = (double)op->n;
+  ProfScope ps(op->ctx, PF_COUPLED,
+               op->nnz * 12.0 + 4.0 * (N + 1) + (op->Mdiag ? 8.0 * N : 0.0) +
+                   8.0 * N * s * (2 + (B ? 1 : 0) + (B0 ? 1 : 0)),
+               2.0 * op->nnz * s + 2.0 * N * nza, st);
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool E = decltype(E_)::value;
@@ -247,6 +255,11 @@ void launch_inner_spmm(pint_op op, int precision, bool jacobi, const void* X, vo
   void* val = inner_sell(op, precision, jacobi, st);
   const int s = op->s;
   const unsigned g = grid_for(op->n, 256);
+  const double vs = precision == PINT_FP64 ? 8.0 : precision == PINT_FP32 ? 4.0 : 2.0;
+  const double xs = precision == PINT_FP64 ? 8.0 : 4.0;
+  ProfScope ps(op->ctx, PF_SPMM,
+               op->nnz * (vs + 4.0) + 4.0 * (op->n + 1) + xs * op->n * s * (Rin ? 3 : 2),
+               2.0 * op->nnz * s, st);
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool E = decltype(E_)::value;
@@ -327,6 +340,7 @@ void launch_colnorm(pint_ctx ctx, int precision, int64_t n, int s, const void* X
                     cudaStream_t st) {
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kNormBlocks, (n + 255) / 256));
   double* partial = ctx->d_small + kSmallNormPartial;
+  ProfScope ps(ctx, PF_NORM, (precision == PINT_FP64 ? 8.0 : 4.0) * n * s, 2.0 * n * s, st);
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool E = decltype(E_)::value;
@@ -359,6 +373,8 @@ void launch_outer_update(int precision, int64_t n, int s, double* Y, const void*
                          const double* colscale, const double* rowscale, cudaStream_t st,
                          pint_ctx ctx) {
   const unsigned g = grid_for(n * s, 256);
+  ProfScope ps(ctx, PF_VEC, (16.0 + (precision == PINT_FP64 ? 8.0 : 4.0)) * n * s +
+                                (rowscale ? 8.0 * n : 0.0), 3.0 * n * s, st);
   if (precision == PINT_FP64)
     k_outer_update<double><<<g, 256, 0, st>>>(n, s, Y, (const double*)V, colscale, rowscale);
   else
@@ -382,6 +398,7 @@ __global__ void k_scale_cast(int64_t n, int s, const double* __restrict__ src, O
 
 void launch_scale_cast(int64_t n, int s, const double* src, float* dst, const double* colnorm,
                        cudaStream_t st, pint_ctx ctx) {
+  ProfScope ps(ctx, PF_VEC, 12.0 * n * s, 1.0 * n * s, st);
   k_scale_cast<float><<<grid_for(n * s, 256), 256, 0, st>>>(n, s, src, dst, colnorm);
   check_launch("k_scale_cast");
   ctx->launches += 1;
@@ -389,6 +406,7 @@ void launch_scale_cast(int64_t n, int s, const double* src, float* dst, const do
 
 void launch_scale_copy64(int64_t n, int s, const double* src, double* dst, const double* colnorm,
                          cudaStream_t st, pint_ctx ctx) {
+  ProfScope ps(ctx, PF_VEC, 16.0 * n * s, 1.0 * n * s, st);
   k_scale_cast<double><<<grid_for(n * s, 256), 256, 0, st>>>(n, s, src, dst, colnorm);
   check_launch("k_scale_copy64");
   ctx->launches += 1;
@@ -413,9 +431,61 @@ __global__ void k_shift(int64_t n, int s, double* __restrict__ Y) {
 }
 
 void launch_shift(double* Y, int64_t n, int s, cudaStream_t st, pint_ctx ctx) {
+  ProfScope ps(ctx, PF_VEC, 16.0 * n * s, 0.0, st);
   k_shift<<<grid_for(n, 256), 256, 0, st>>>(n, s, Y);
   check_launch("k_shift");
   if (ctx) ctx->launches += 1;
 }
 
+}  // namespace pint
+
+namespace pint {
+// ------------------------------------------------ Newton step bound
+// out[k] = rnorm[k] * min(1, delta / max_r |rnorm[k] * rowscale[r] * X[r][k]|)
+// The column maxima use atomicMax on the bit patterns of non-negative
+// doubles (their integer order equals their numeric order): deterministic.
+template <typename VT>
+__global__ void k_colmax(int64_t n, int s, const VT* __restrict__ X,
+                         const double* __restrict__ rowscale,
+                         unsigned long long* __restrict__ bits) {
+  double m[kMaxS];
+  for (int k = 0; k < s; ++k) m[k] = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double rs = rowscale ? fabs(rowscale[r]) : 1.0;
+    for (int k = 0; k < s; ++k) m[k] = fmax(m[k], rs * fabs((double)X[r * s + k]));
+  }
+  for (int k = 0; k < s; ++k) {
+    double v = m[k];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(bits + k, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+__global__ void k_step_scale(int s, const double* __restrict__ rnorm,
+                             const unsigned long long* __restrict__ bits, double delta,
+                             double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= s) return;
+  const double step = rnorm[k] * __longlong_as_double((long long)bits[k]);
+  out[k] = rnorm[k] * (step > delta ? delta / step : 1.0);
+}
+
+void launch_step_bound(int precision, int64_t n, int s, const void* X, const double* rowscale,
+                       const double* rnorm, double delta, double* out, cudaStream_t st,
+                       pint_ctx ctx) {
+  unsigned long long* bits =
+      reinterpret_cast<unsigned long long*>(ctx->d_small + kSmallScratch + 64);
+  PINT_CUDA(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * kMaxS, st));
+  ProfScope ps(ctx, PF_VEC, (precision == PINT_FP64 ? 8.0 : 4.0) * n * s, 2.0 * n * s, st);
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms * 4LL,
+                                                                      (n + 255) / 256));
+  if (precision == PINT_FP64)
+    k_colmax<double><<<g, 256, 0, st>>>(n, s, (const double*)X, rowscale, bits);
+  else
+    k_colmax<float><<<g, 256, 0, st>>>(n, s, (const float*)X, rowscale, bits);
+  k_step_scale<<<1, 32, 0, st>>>(s, rnorm, bits, delta, out);
+  check_launch("k_colmax");
+  ctx->launches += 2;
+}
 }  // namespace pint

@@ -14,8 +14,8 @@ def pytest_configure(config):
 
 def pytest_sessionstart(session):
     # libpint.so is built in-tree (nvcc cross-compiles without a GPU)
-    from paper_2504_02117_gb300.build import build
-    build()
+    import __graft_entry__
+    __graft_entry__._build_module().build()
 
 
 @pytest.fixture(scope="session")

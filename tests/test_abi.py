@@ -24,8 +24,8 @@ def test_header_declares_the_boundary_calls():
 
 
 def test_library_exports_every_declared_symbol():
-    from paper_2504_02117_gb300.build import build
-    lib_path = build()
+    import __graft_entry__
+    lib_path = __graft_entry__._build_module().build()
     lib = ctypes.CDLL(lib_path)
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing

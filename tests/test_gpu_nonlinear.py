@@ -144,6 +144,7 @@ def test_pipeline_richards_equals_sequential(P, ctx):
         o.inner_tol = 1e-6
         o.precond = P.PINT_PC_ILU0
         o.max_outer = 60
+        o.max_step = 1.0                 # step bound of 1 m of head per Newton update
         P.pint_pipeline_run(ctx, prob, A, c, tau, s, _dev(y0), G, out, o)
         Yseq, _ = newton.sequential_dirk_newton(oprob, A, c, tau, y0, G)
         err = np.linalg.norm(out.cpu().numpy() - Yseq, axis=0) / np.linalg.norm(Yseq, axis=0)

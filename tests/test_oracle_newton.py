@@ -102,6 +102,24 @@ def test_pipelined_diffreact_equals_sequential():
     np.testing.assert_allclose(Ypl, Yseq, rtol=1e-10, atol=1e-11)
 
 
+def test_pipelined_richards_step_bound_8cube():
+    """On 8^3 cells the trailing window columns' chord steps diverge without a
+    step bound (the oracle reaches |psi| ~ 1e18); with max_step = 1 every
+    window converges and the result equals sequential Newton stepping."""
+    import synth
+    dims = (8, 8, 8)
+    Ks = np.exp(2.0 * synth.correlated_field(4, dims[::-1], 2.0))
+    vg = fv.VanGenuchten(1.0, 2.0, 0.05, 0.4)
+    z, _ = fv.richards_cells(dims)
+    prob = newton.RichardsProblem(dims, Ks, vg, 1 / 16)
+    A, _, c = coupling.implicit_euler()
+    Yseq, _ = newton.sequential_dirk_newton(prob, A, c, 1 / 96, -z, 6)
+    Ypl, st = newton.pipelined_block_newton(prob, A, c, 1 / 96, -z, 6, 4, tol=1e-12,
+                                            inner_tol=1e-6, max_newton=40, max_step=1.0)
+    assert max(st["newton"]) < 40
+    np.testing.assert_allclose(Ypl, Yseq, rtol=1e-9, atol=1e-10)
+
+
 def test_pipelined_richards_equals_sequential():
     dims = (4, 4, 4)
     rng = np.random.default_rng(4)
