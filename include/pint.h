@@ -275,6 +275,28 @@ int pint_block_update(pint_ctx ctx, int precision, int64_t n, int s, int nb,
  * deflated columns of Q are zero. */
 int pint_cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W,
                  double* R, void* stream);
+/* Same product as pint_block_gram, for callers that cannot allocate device
+ * memory: pint_block_gram needs a context, and creating one calls cudaMalloc.
+ * Frameworks whose caching allocator owns the whole device pool, real-time
+ * loops that must never allocate, and code that must not take the implicit
+ * synchronisation of cudaMalloc/cudaFree can call this one instead. The paper
+ * has no counterpart; it is an interface convenience.
+ *  - No context; no cudaMalloc, cudaFree or other allocating call. The
+ *    cross-CTA partial sums live in a fixed 4 MiB float64 array in the
+ *    library's device memory, held on every device that loads the library
+ *    until the process exits.
+ *  - Limit: nb * s * s <= 4096 (otherwise PINT_ERR_INVALID with a message
+ *    from pint_last_error(NULL)); 1 <= s <= 16; V, W 16-byte aligned.
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address; make that first call before any stream capture.
+ *  - All calls share the array, which keeps the last call's contents; every
+ *    call overwrites the part it reads. Calls that overlap on the GPU (other
+ *    streams, other host threads) race on it and must be serialised by the
+ *    caller.
+ * Runs on the current device and `stream`; asynchronous. */
+int pint_block_gram_noalloc(int precision, int64_t n, int s, int nb,
+                            const void* V, const void* W, double* H,
+                            void* stream);
 /* norms[k] = ||X_k||_2 (host array of s doubles). Synchronous. */
 int pint_colnorms(pint_ctx ctx, int precision, int64_t n, int s,
                   const void* X, double* norms, void* stream);

@@ -99,6 +99,7 @@ _SIGS = {
     "pint_precond_apply": (_i, [_vp, _i, _vp, _vp, _vp]),
     "pint_block_gram": (_i, [_vp, _i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
     "pint_block_update": (_i, [_vp, _i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
+    "pint_block_gram_noalloc": (_i, [_i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
     "pint_cholqr2": (_i, [_vp, _i, _i64, _i, _vp, _vp, _vp]),
     "pint_colnorms": (_i, [_vp, _i, _i64, _i, _vp, _vp, _vp]),
 }
@@ -297,6 +298,12 @@ def pint_precond_apply(ctx, op, precond, X, Z, stream=None):
 def pint_block_gram(ctx, precision, n, s, nb, V, W, H, stream=None):
     _check(lib.pint_block_gram(ctx, precision, n, s, nb, _ptr(V), _ptr(W), _ptr(H),
                                _stream(stream)), ctx)
+
+
+def pint_block_gram_noalloc(precision, n, s, nb, V, W, H, stream=None):
+    """Gram product without device allocation (no context; fixed scratch)."""
+    _check(lib.pint_block_gram_noalloc(precision, n, s, nb, _ptr(V), _ptr(W), _ptr(H),
+                                       _stream(stream)))
 
 
 def pint_block_update(ctx, precision, n, s, nb, V, H, W, stream=None):

@@ -35,6 +35,7 @@ void dfree(pint_ctx ctx, void* p, size_t bytes) {
 }
 
 static thread_local std::string g_noctx_err;
+void set_noctx_error(const std::string& msg) { g_noctx_err = msg; }
 
 template <typename Fn>
 static int guard(pint_ctx ctx, Fn&& fn) {

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 
 namespace pint {
 
@@ -804,3 +805,111 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
 }
 
 }  // namespace pint
+
+// ===================================================================
+// Block Gram product without any device allocation.
+//
+// pint_block_gram needs a context, and the context allocates device memory
+// (cudaMalloc) for its reduction buffers. Some callers cannot allow that: code
+// that runs inside a framework whose caching allocator already owns the
+// device memory pool, real-time loops that must never allocate, and paths that
+// must not take the implicit device synchronisation of cudaMalloc/cudaFree.
+// pint_block_gram_noalloc computes the same H = [V_1..V_nb]^T W with the
+// cross-CTA partial sums kept in the file-scope device array below instead.
+// ===================================================================
+namespace pint {
+
+// 4 MiB of float64 partial sums, resident on every device that loads the
+// library until the process exits.
+constexpr int kNoAllocScratchDoubles = 1 << 19;
+constexpr int kNoAllocMaxBlocks = 128;      // CTAs of the Gram launch
+constexpr int kNoAllocMaxEntries = kNoAllocScratchDoubles / kNoAllocMaxBlocks;   // nb*s*s
+static __device__ __align__(256) double g_gram_scratch[kNoAllocScratchDoubles];
+
+struct NoAllocDevice {
+  bool ready = false;
+  double* scratch = nullptr;   // device address of g_gram_scratch on this device
+  int num_sms = 0;
+};
+static NoAllocDevice g_noalloc_dev[64];
+static std::mutex g_noalloc_mutex;
+
+void set_noctx_error(const std::string& msg);   // api.cu
+
+template <typename VT>
+static void gram_noalloc_t(const NoAllocDevice& d, int64_t n, int s, int nb, const VT* V,
+                           const VT* W, double* H, cudaStream_t st) {
+  const int P = nb * s;
+  int PT = 32;
+  while (PT < P && PT < 256) PT <<= 1;
+  const int npt = (P + PT - 1) / PT;
+  const int64_t want = std::max<int64_t>(
+      1, std::min<int64_t>(std::min(4 * d.num_sms, kNoAllocMaxBlocks), (n + 63) / 64));
+  int64_t rpc = (n + want - 1) / want;
+  rpc = std::max<int64_t>(kGramTile, ((rpc + kGramTile - 1) / kGramTile) * kGramTile);
+  const int nblk = (int)((n + rpc - 1) / rpc);
+  const int E = P * s;
+  const size_t tile_bytes = sizeof(VT) * kGramTile * (P + s);
+  const size_t red_bytes = sizeof(double) * E;
+  const size_t smem = std::max(tile_bytes, (PT < 256 ? red_bytes : (size_t)0));
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool EX = decltype(E_)::value;
+    auto launch = [&](auto kern) {
+      PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<nblk, 256, smem, st>>>(n, s, nb, V, n * s, W, rpc, d.scratch);
+    };
+    if (npt == 1) launch(k_gram<VT, S, EX, 1>);
+    else if (npt == 2) launch(k_gram<VT, S, EX, 2>);
+    else launch(k_gram<VT, S, EX, 4>);
+  });
+  check_launch("k_gram (no-alloc)");
+  k_gram_reduce<<<(E + 255) / 256, 256, 0, st>>>(nblk, E, d.scratch, H);
+  check_launch("k_gram_reduce (no-alloc)");
+}
+
+}  // namespace pint
+
+extern "C" int pint_block_gram_noalloc(int precision, int64_t n, int s, int nb, const void* V,
+                                       const void* W, double* H, void* stream) {
+  using namespace pint;
+  try {
+    PINT_REQUIRE(n >= 1 && s >= 1 && s <= PINT_MAX_S && nb >= 1, PINT_ERR_INVALID,
+                 "pint_block_gram_noalloc: need n >= 1, 1 <= s <= 16, nb >= 1");
+    PINT_REQUIRE((int64_t)nb * s * s <= kNoAllocMaxEntries, PINT_ERR_INVALID,
+                 "pint_block_gram_noalloc: nb*s*s = " + std::to_string((int64_t)nb * s * s) +
+                     " exceeds the maximum of " + std::to_string(kNoAllocMaxEntries) +
+                     " (fixed scratch of 4 MiB)");
+    PINT_REQUIRE(precision == PINT_FP64 || precision == PINT_FP32, PINT_ERR_INVALID,
+                 "pint_block_gram_noalloc: precision must be PINT_FP64 or PINT_FP32");
+    PINT_REQUIRE(V && W && H, PINT_ERR_INVALID, "pint_block_gram_noalloc: NULL pointer");
+    PINT_REQUIRE(reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(W) % 16 == 0,
+                 PINT_ERR_INVALID, "pint_block_gram_noalloc: V and W must be 16-byte aligned");
+    int dev = 0;
+    PINT_CUDA(cudaGetDevice(&dev));
+    PINT_REQUIRE(dev >= 0 && dev < 64, PINT_ERR_INVALID, "pint_block_gram_noalloc: device index");
+    NoAllocDevice d;
+    {
+      std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+      NoAllocDevice& slot = g_noalloc_dev[dev];
+      if (!slot.ready) {   // once per device, with that device current
+        void* p = nullptr;
+        PINT_CUDA(cudaGetSymbolAddress(&p, g_gram_scratch));
+        PINT_CUDA(cudaDeviceGetAttribute(&slot.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        slot.scratch = static_cast<double*>(p);
+        slot.ready = true;
+      }
+      d = slot;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (precision == PINT_FP64)
+      gram_noalloc_t<double>(d, n, s, nb, (const double*)V, (const double*)W, H, st);
+    else
+      gram_noalloc_t<float>(d, n, s, nb, (const float*)V, (const float*)W, H, st);
+    return PINT_OK;
+  } catch (const Error& e) {
+    set_noctx_error(e.msg);
+    return e.code;
+  }
+}
