@@ -617,6 +617,9 @@ int pint_fv_convdiff(pint_ctx ctx, pint_op* out, int nx, int ny, int nz, const d
     std::vector<int> rp, ci;
     grid_pattern(nx, ny, nz, rp, ci);
     pint_op op = op_create(ctx, n, rp.data(), ci.data(), st);
+    op->grid_nx = nx;
+    op->grid_ny = ny;
+    op->grid_nz = nz;
     try {
       const double* dD = D;
       double* tmp = nullptr;
@@ -678,6 +681,9 @@ int pint_problem_create(pint_ctx ctx, pint_problem* out, int kind, int nx, int n
       std::vector<int> rp, ci;
       grid_pattern(nx, ny, nz, rp, ci);
       p->op = op_create(ctx, n, rp.data(), ci.data(), st);
+      p->op->grid_nx = nx;
+      p->op->grid_ny = ny;
+      p->op->grid_nz = nz;
       p->op->owner = p;
       p->vec = dalloc_n<double>(ctx, n);
       p->B0 = dalloc_n<double>(ctx, n * kMaxS);

@@ -45,6 +45,15 @@ struct IluState {
   int* d_order_f = nullptr;
   int* d_order_b = nullptr;
   std::map<int, Sched> sched_f, sched_b;   // by rows per chunk
+  // tiled sweeps for natural-order 5/7-point stencils
+  bool tiled = false;
+  int TX = 0, TY = 0, TZ = 0, NTX = 0, NTY = 0, NTZ = 0, ntiles = 0, nlev = 0;
+  int* tile_order = nullptr;      // tiles by ascending tile level
+  int* loc_list = nullptr;        // local rows of a full tile by local level
+  int* loc_lvlptr = nullptr;
+  unsigned* tflag_f = nullptr;
+  unsigned* tflag_b = nullptr;
+  unsigned tepoch_f = 0, tepoch_b = 0;
 };
 
 // -------------------------------------------------------------- helpers
@@ -179,6 +188,155 @@ k_ilu_sweep(int s, int sp_log2, const int* __restrict__ rowptr, const int* __res
   }
 }
 
+// ---------------------------------------------------- tiled stencil sweep
+// For the natural-order 7-point (5-point in 2-D) stencil, row (i,j,k) reads
+// only (i-1,j,k), (i,j-1,k), (i,j,k-1) forward and the +1 neighbours backward.
+// A CTA owns a TX x TY x TZ tile: it prefetches the tile's coefficients and
+// right-hand sides, waits (bounded) for the flags of the three upstream
+// tiles, loads their faces into shared memory and sweeps its local levels
+// li+lj+lk with __syncthreads only, then publishes one flag for the tile.
+// Tiles are taken from an atomic ticket in tile-level order, so a CTA only
+// waits for tiles with lower tickets, taken by running CTAs. The arithmetic
+// per row and column is the same as the CSR sweep (same operands, same order).
+struct TileGeom {
+  int nx, ny, nz, TX, TY, TZ, NTX, NTY, ntiles, nlev;
+};
+
+template <typename VT, bool FWD>
+__global__ void __launch_bounds__(256)
+k_ilu_tile(TileGeom g, int s, const int* __restrict__ rowptr, const int* __restrict__ diagpos,
+           const VT* __restrict__ F, const VT* X, VT* Z, const int* __restrict__ tile_order,
+           const int* __restrict__ loc_list, const int* __restrict__ loc_lvlptr,
+           unsigned* tflags, unsigned epoch, int* ticket, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TR = g.TX * g.TY * g.TZ;
+  VT* Ys = reinterpret_cast<VT*>(smem_raw);                 // TR x s
+  VT* Hx = Ys + (size_t)TR * s;                              // TY*TZ x s
+  VT* Hy = Hx + (size_t)g.TY * g.TZ * s;                     // TX*TZ x s
+  VT* Hz = Hy + (size_t)g.TX * g.TZ * s;                     // TX*TY x s
+  VT* C = Hz + (size_t)g.TX * g.TY * s;                      // TR x 4 coefficients
+  __shared__ int tile_sh;
+  const unsigned long long deadline = globaltimer() + kWaitBudgetNs;
+  const int64_t sxy = (int64_t)g.nx * g.ny;
+  bool ok = true;
+  while (true) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(ticket, 1);
+      tile_sh = t < g.ntiles ? tile_order[FWD ? t : g.ntiles - 1 - t] : -1;
+    }
+    __syncthreads();
+    const int tile = tile_sh;
+    __syncthreads();
+    if (tile < 0) return;
+    const int I = tile % g.NTX, J = (tile / g.NTX) % g.NTY, K = tile / (g.NTX * g.NTY);
+    const int x0 = I * g.TX, y0 = J * g.TY, z0 = K * g.TZ;
+    const int ex = min(g.TX, g.nx - x0), ey = min(g.TY, g.ny - y0), ez = min(g.TZ, g.nz - z0);
+    // prefetch coefficients and right-hand sides
+    for (int l = threadIdx.x; l < TR; l += blockDim.x) {
+      const int li = l % g.TX, lj = (l / g.TX) % g.TY, lk = l / (g.TX * g.TY);
+      if (li >= ex || lj >= ey || lk >= ez) continue;
+      const int gi = x0 + li, gj = y0 + lj, gk = z0 + lk;
+      const int64_t r = gi + (int64_t)g.nx * gj + sxy * gk;
+      const int d = diagpos[r];
+      VT c0 = VT(0), c1 = VT(0), c2 = VT(0);
+      if (FWD) {
+        int p = rowptr[r];
+        if (gk > 0) c0 = F[p++];      // -z
+        if (gj > 0) c1 = F[p++];      // -y
+        if (gi > 0) c2 = F[p++];      // -x
+      } else {
+        int p = d + 1;
+        if (gi + 1 < g.nx) c0 = F[p++];   // +x
+        if (gj + 1 < g.ny) c1 = F[p++];   // +y
+        if (gk + 1 < g.nz) c2 = F[p++];   // +z
+      }
+      C[4 * l + 0] = c0;
+      C[4 * l + 1] = c1;
+      C[4 * l + 2] = c2;
+      C[4 * l + 3] = F[d];
+      for (int c = 0; c < s; ++c)
+        Ys[(size_t)l * s + c] = FWD ? X[r * s + c] : __ldcg(Z + r * s + c);
+    }
+    // upstream tiles: FWD -x,-y,-z ; BWD +x,+y,+z
+    if (threadIdx.x < 3 && ok) {
+      int nt = -1;
+      if (FWD) {
+        if (threadIdx.x == 0 && I > 0) nt = tile - 1;
+        if (threadIdx.x == 1 && J > 0) nt = tile - g.NTX;
+        if (threadIdx.x == 2 && K > 0) nt = tile - g.NTX * g.NTY;
+      } else {
+        if (threadIdx.x == 0 && x0 + ex < g.nx) nt = tile + 1;
+        if (threadIdx.x == 1 && y0 + ey < g.ny) nt = tile + g.NTX;
+        if (threadIdx.x == 2 && z0 + ez < g.nz) nt = tile + g.NTX * g.NTY;
+      }
+      if (nt >= 0) ok = wait_ready(tflags + nt, epoch, err, deadline);
+    }
+    __syncthreads();
+    // faces of the upstream tiles (zero where the grid ends)
+    const int hx = FWD ? x0 - 1 : x0 + ex, hy = FWD ? y0 - 1 : y0 + ey, hz = FWD ? z0 - 1 : z0 + ez;
+    for (int e = threadIdx.x; e < g.TY * g.TZ * s; e += blockDim.x) {
+      const int c = e % s, q = e / s, lj = q % g.TY, lk = q / g.TY;
+      VT v = VT(0);
+      if (hx >= 0 && hx < g.nx && lj < ey && lk < ez)
+        v = __ldcg(Z + (hx + (int64_t)g.nx * (y0 + lj) + sxy * (z0 + lk)) * s + c);
+      Hx[e] = v;
+    }
+    for (int e = threadIdx.x; e < g.TX * g.TZ * s; e += blockDim.x) {
+      const int c = e % s, q = e / s, li = q % g.TX, lk = q / g.TX;
+      VT v = VT(0);
+      if (hy >= 0 && hy < g.ny && li < ex && lk < ez)
+        v = __ldcg(Z + (x0 + li + (int64_t)g.nx * hy + sxy * (z0 + lk)) * s + c);
+      Hy[e] = v;
+    }
+    for (int e = threadIdx.x; e < g.TX * g.TY * s; e += blockDim.x) {
+      const int c = e % s, q = e / s, li = q % g.TX, lj = q / g.TX;
+      VT v = VT(0);
+      if (hz >= 0 && hz < g.nz && li < ex && lj < ey)
+        v = __ldcg(Z + (x0 + li + (int64_t)g.nx * (y0 + lj) + sxy * hz) * s + c);
+      Hz[e] = v;
+    }
+    __syncthreads();
+    // local wavefront
+    for (int it = 0; it < g.nlev; ++it) {
+      const int lv = FWD ? it : g.nlev - 1 - it;
+      const int b = loc_lvlptr[lv], cnt = loc_lvlptr[lv + 1] - b;
+      for (int e = threadIdx.x; e < cnt * s; e += blockDim.x) {
+        const int l = loc_list[b + e / s], c = e % s;
+        const int li = l % g.TX, lj = (l / g.TX) % g.TY, lk = l / (g.TX * g.TY);
+        if (li >= ex || lj >= ey || lk >= ez) continue;
+        VT acc = Ys[(size_t)l * s + c];
+        if (FWD) {
+          const VT vz = lk > 0 ? Ys[(size_t)(l - g.TX * g.TY) * s + c] : Hz[(li + g.TX * lj) * s + c];
+          const VT vy = lj > 0 ? Ys[(size_t)(l - g.TX) * s + c] : Hy[(li + g.TX * lk) * s + c];
+          const VT vx = li > 0 ? Ys[(size_t)(l - 1) * s + c] : Hx[(lj + g.TY * lk) * s + c];
+          acc -= C[4 * l + 0] * vz;
+          acc -= C[4 * l + 1] * vy;
+          acc -= C[4 * l + 2] * vx;
+        } else {
+          const VT vx = li + 1 < ex ? Ys[(size_t)(l + 1) * s + c] : Hx[(lj + g.TY * lk) * s + c];
+          const VT vy = lj + 1 < ey ? Ys[(size_t)(l + g.TX) * s + c] : Hy[(li + g.TX * lk) * s + c];
+          const VT vz = lk + 1 < ez ? Ys[(size_t)(l + g.TX * g.TY) * s + c] : Hz[(li + g.TX * lj) * s + c];
+          acc -= C[4 * l + 0] * vx;
+          acc -= C[4 * l + 1] * vy;
+          acc -= C[4 * l + 2] * vz;
+          acc /= C[4 * l + 3];
+        }
+        Ys[(size_t)l * s + c] = acc;
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < TR * s; e += blockDim.x) {
+      const int l = e / s, c = e % s;
+      const int li = l % g.TX, lj = (l / g.TX) % g.TY, lk = l / (g.TX * g.TY);
+      if (li >= ex || lj >= ey || lk >= ez) continue;
+      Z[(x0 + li + (int64_t)g.nx * (y0 + lj) + sxy * (z0 + lk)) * s + c] = Ys[e];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(tflags + tile, epoch);
+  }
+}
+
 // ------------------------------------------------------------ host side
 static void levels(const pint_op op, bool forward, std::vector<int>& order,
                    std::vector<int>& lvlptr) {
@@ -259,6 +417,38 @@ static void ensure_state(pint_op op) {
   PINT_CUDA(cudaMemset(S->flag_f, 0, sizeof(unsigned) * op->n));
   PINT_CUDA(cudaMemset(S->flag_b, 0, sizeof(unsigned) * op->n));
   PINT_CUDA(cudaMemset(S->err, 0, 2 * sizeof(int)));
+  if (op->grid_nx > 0) {
+    const int nx = op->grid_nx, ny = op->grid_ny, nz = op->grid_nz;
+    S->TX = nz > 1 ? 8 : (ny > 1 ? 16 : 64);
+    S->TY = nz > 1 ? 8 : (ny > 1 ? 16 : 1);
+    S->TZ = nz > 1 ? 8 : 1;
+    S->NTX = (nx + S->TX - 1) / S->TX;
+    S->NTY = (ny + S->TY - 1) / S->TY;
+    S->NTZ = (nz + S->TZ - 1) / S->TZ;
+    S->ntiles = S->NTX * S->NTY * S->NTZ;
+    S->nlev = S->TX + S->TY + S->TZ - 2;
+    std::vector<int> order(S->ntiles), loc(S->TX * S->TY * S->TZ), ptr(S->nlev + 1, 0);
+    for (int t = 0; t < S->ntiles; ++t) order[t] = t;
+    auto tlev = [&](int t) { return t % S->NTX + (t / S->NTX) % S->NTY + t / (S->NTX * S->NTY); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tlev(a) < tlev(b); });
+    const int TR = (int)loc.size();
+    auto llev = [&](int l) { return l % S->TX + (l / S->TX) % S->TY + l / (S->TX * S->TY); };
+    for (int l = 0; l < TR; ++l) ptr[llev(l) + 1]++;
+    for (int v = 0; v < S->nlev; ++v) ptr[v + 1] += ptr[v];
+    std::vector<int> pos(ptr.begin(), ptr.end() - 1);
+    for (int l = 0; l < TR; ++l) loc[pos[llev(l)]++] = l;
+    S->tile_order = dalloc_n<int>(ctx, S->ntiles);
+    S->loc_list = dalloc_n<int>(ctx, TR);
+    S->loc_lvlptr = dalloc_n<int>(ctx, S->nlev + 1);
+    S->tflag_f = dalloc_n<unsigned>(ctx, S->ntiles);
+    S->tflag_b = dalloc_n<unsigned>(ctx, S->ntiles);
+    PINT_CUDA(cudaMemcpy(S->tile_order, order.data(), sizeof(int) * S->ntiles, cudaMemcpyHostToDevice));
+    PINT_CUDA(cudaMemcpy(S->loc_list, loc.data(), sizeof(int) * TR, cudaMemcpyHostToDevice));
+    PINT_CUDA(cudaMemcpy(S->loc_lvlptr, ptr.data(), sizeof(int) * (S->nlev + 1), cudaMemcpyHostToDevice));
+    PINT_CUDA(cudaMemset(S->tflag_f, 0, sizeof(unsigned) * S->ntiles));
+    PINT_CUDA(cudaMemset(S->tflag_b, 0, sizeof(unsigned) * S->ntiles));
+    S->tiled = true;
+  }
 }
 
 static unsigned sweep_grid(pint_op op, int nchunk) {
@@ -280,6 +470,13 @@ void ilu_destroy(pint_op op) {
   dfree(c, S->err, 2 * sizeof(int));
   dfree(c, S->d_order_f, sizeof(int) * op->n);
   dfree(c, S->d_order_b, sizeof(int) * op->n);
+  if (S->tiled) {
+    dfree(c, S->tile_order, sizeof(int) * S->ntiles);
+    dfree(c, S->loc_list, sizeof(int) * S->TX * S->TY * S->TZ);
+    dfree(c, S->loc_lvlptr, sizeof(int) * (S->nlev + 1));
+    dfree(c, S->tflag_f, sizeof(unsigned) * S->ntiles);
+    dfree(c, S->tflag_b, sizeof(unsigned) * S->ntiles);
+  }
   delete S;
   op->ilu = nullptr;
 }
@@ -317,8 +514,44 @@ void ilu_setup(pint_op op, cudaStream_t st) {
 }
 
 template <typename VT>
+static void apply_tiled(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st) {
+  IluState* S = op->ilu;
+  const int s = op->s;
+  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, S->TX, S->TY, S->TZ, S->NTX, S->NTY,
+             S->ntiles, S->nlev};
+  const int TR = S->TX * S->TY * S->TZ;
+  const size_t smem = sizeof(VT) * ((size_t)TR * s +
+                                    (size_t)(S->TY * S->TZ + S->TX * S->TZ + S->TX * S->TY) * s +
+                                    4 * (size_t)TR);
+  auto launch = [&](auto kern, const VT* x, unsigned* flags, unsigned ep, int* ticket) {
+    PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+    const int grid = std::max(1, std::min(S->ntiles, std::max(1, per_sm) * op->ctx->num_sms));
+    kern<<<grid, 256, smem, st>>>(g, s, op->rowptr, op->diagpos, F, x, Z, S->tile_order,
+                                  S->loc_list, S->loc_lvlptr, flags, ep, ticket, S->err);
+  };
+  const unsigned ef = next_epoch(op, S->tepoch_f, S->tflag_f, st);
+  const unsigned eb = next_epoch(op, S->tepoch_b, S->tflag_b, st);
+  PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
+  ProfScope ps(op->ctx, PF_ILU,
+               op->nnz * (sizeof(VT) + 4.0) + 4.0 * (op->n + 1) + 4.0 * op->n +
+                   4.0 * sizeof(VT) * op->n * s,
+               2.0 * op->nnz * s, st);
+  launch(k_ilu_tile<VT, true>, X, S->tflag_f, ef, S->ticket);
+  check_launch("k_ilu_tile<fwd>");
+  launch(k_ilu_tile<VT, false>, Z, S->tflag_b, eb, S->ticket + 1);
+  check_launch("k_ilu_tile<bwd>");
+  op->ctx->launches += 2;
+}
+
+template <typename VT>
 static void apply_t(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st) {
   IluState* S = op->ilu;
+  if (S->tiled) {
+    apply_tiled<VT>(op, F, X, Z, st);
+    return;
+  }
   const int s = op->s;
   int spl = 0;
   while ((1 << spl) < s) ++spl;
@@ -327,11 +560,11 @@ static void apply_t(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st
   Sched& b = schedule(op, false, rpw);
   const unsigned ef = next_epoch(op, S->epoch_f, S->flag_f, st);
   const unsigned eb = next_epoch(op, S->epoch_b, S->flag_b, st);
-  PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
   ProfScope ps(op->ctx, PF_ILU,
                op->nnz * (sizeof(VT) + 4.0) + 4.0 * (op->n + 1) + 8.0 * op->n + 8.0 * op->n +
                    4.0 * sizeof(VT) * op->n * s,
                2.0 * op->nnz * s, st);
+  PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
   k_ilu_sweep<VT, true><<<sweep_grid(op, f.nchunk), 256, 0, st>>>(
       s, spl, op->rowptr, op->colind, op->diagpos, F, f.order, f.chunk, f.nchunk, X, Z, S->flag_f,
       ef, S->ticket, S->err);

@@ -220,6 +220,9 @@ struct pint_op_s {
   int* diagpos = nullptr;        // device, CSR position of the diagonal
   std::vector<int> h_rowptr, h_colind;
   pint::SellPattern sell;
+  // structured-grid shape when the pattern is the natural-order 5/7-point
+  // stencil built by the FV constructors (0 otherwise)
+  int grid_nx = 0, grid_ny = 0, grid_nz = 0;
   double* sellK = nullptr;       // K values in SELL (float64)
   // coupling
   int s = 0;
@@ -316,13 +319,15 @@ void launch_step_bound(int precision, int64_t n, int s, const void* X, const dou
                        pint_ctx ctx);
 
 // ----------------------------------------------------------- krylov.cu
+// n_pad > 0: rows [n, n_pad) of V and W are zero and n_pad % 64 == 0, which
+// enables the bulk-copy (TMA) pipeline; 0: plain loads.
 void launch_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb, const void* V,
-                 int64_t bstride, const void* W, double* H, cudaStream_t st);
+                 int64_t bstride, const void* W, double* H, cudaStream_t st, int64_t n_pad = 0);
 // mode 0: W -= V H ; 1: W = V H ; 2: W += V H
 void launch_update(pint_ctx ctx, int precision, int64_t n, int s, int nb, const void* V,
                    int64_t bstride, const double* H, void* W, int mode, cudaStream_t st);
 void cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W, double* R,
-             int* defl_count_dev, cudaStream_t st);
+             int* defl_count_dev, cudaStream_t st, int64_t n_pad = 0);
 int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
                      const pint_opts* o, pint_stats* stats, cudaStream_t st);
 // Inner solve J V = R (R float64, scaled per column inside), result V float64.

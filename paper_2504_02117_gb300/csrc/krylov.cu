@@ -101,6 +101,158 @@ k_gram(int64_t n, int s, int nb, const VT* __restrict__ V, int64_t bstride,
   for (int e = threadIdx.x; e < E; e += 256) out[e] = red[e];
 }
 
+// ---------------------------------------------------- Gram, TMA pipeline
+// Same product over a zero-padded row range [0, n_pad): each CTA streams
+// tiles of TR rows of the nb+1 blocks (V_0..V_{nb-1}, W) into shared memory
+// with 1-D bulk copies (cp.async.bulk, completion on an mbarrier) through a
+// ring of kStages stages, so that every SM keeps >100 KB of loads in flight
+// while the threads multiply the previous tiles. Waits on the mbarriers are
+// bounded (globaltimer); a timeout raises *err and the CTA drains without
+// waiting further.
+constexpr int kStages = 4;
+constexpr unsigned long long kMbarBudgetNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+      "l"(src), "r"(bytes), "r"(b)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(a), "r"(parity) : "memory");
+  return done != 0;
+}
+
+template <typename VT, int S, bool EXACT, int NPT>
+__global__ void __launch_bounds__(256)
+k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstride,
+            const VT* __restrict__ W, int64_t rows_per_cta, int TR, double* __restrict__ partial,
+            int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ int aborted;
+  const int P = nb * s;
+  const unsigned blk_bytes = (unsigned)(TR * s * sizeof(VT));
+  const unsigned stage_bytes = blk_bytes * (nb + 1);
+  int PT = 32;
+  while (PT < P && PT < 256) PT <<= 1;
+  const int TRG = 256 / PT;
+  const int pg = threadIdx.x % PT, rg = threadIdx.x / PT;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = (r0 + rows_per_cta < n_pad) ? r0 + rows_per_cta : n_pad;
+  const int ntiles = r1 > r0 ? (int)((r1 - r0) / TR) : 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+    aborted = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int stage, int tile) {
+    unsigned char* dst = smem_raw + (size_t)stage * stage_bytes;
+    mbar_expect_tx(&bars[stage], stage_bytes);
+    const int64_t row = r0 + (int64_t)tile * TR;
+    for (int b = 0; b <= nb; ++b) {
+      const VT* src = (b < nb ? V + (int64_t)b * bstride : W) + row * s;
+      bulk_g2s(dst + (size_t)b * blk_bytes, src, blk_bytes, &bars[stage]);
+    }
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < kStages && t < ntiles; ++t) issue(t, t);
+  // per-thread offsets of its p values inside a stage (block-major [b][rr][i])
+  int off[NPT];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int p = pg + j * PT;
+    off[j] = p < P ? (p / s) * TR * s + (p % s) : -1;
+  }
+  VT acc[NPT][S];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j)
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc[j][k] = VT(0);
+  const unsigned long long deadline = gtimer() + kMbarBudgetNs;
+  for (int t = 0; t < ntiles; ++t) {
+    const int stage = t % kStages;
+    const unsigned parity = (unsigned)((t / kStages) & 1);
+    if (!*(volatile int*)&aborted) {
+      while (!mbar_try_wait(&bars[stage], parity)) {
+        if (*(volatile int*)&aborted) break;
+        if (gtimer() > deadline) {
+          aborted = 1;
+          atomicExch(err, 3);
+          break;
+        }
+      }
+    }
+    const VT* T = reinterpret_cast<const VT*>(smem_raw + (size_t)stage * stage_bytes);
+    const VT* Wt = T + (size_t)nb * TR * s;
+    for (int rr = rg; rr < TR; rr += TRG) {
+      VT w[S];
+#pragma unroll
+      for (int k = 0; k < S; ++k) w[k] = (EXACT || k < s) ? Wt[rr * s + k] : VT(0);
+#pragma unroll
+      for (int j = 0; j < NPT; ++j) {
+        if (off[j] >= 0) {
+          const VT v = T[off[j] + rr * s];
+#pragma unroll
+          for (int k = 0; k < S; ++k) acc[j][k] = fma(v, w[k], acc[j][k]);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && t + kStages < ntiles && !aborted) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(stage, t + kStages);
+    }
+  }
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(smem_raw);
+  const int E = P * s;
+  double* out = partial + (int64_t)blockIdx.x * E;
+  if (TRG == 1) {
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+      const int p = pg + j * PT;
+      if (p < P)
+#pragma unroll
+        for (int k = 0; k < S; ++k)
+          if (EXACT || k < s) out[p * s + k] = (double)acc[j][k];
+    }
+    return;
+  }
+  for (int rgi = 0; rgi < TRG; ++rgi) {
+    if (rg == rgi && pg < P) {
+#pragma unroll
+      for (int k = 0; k < S; ++k)
+        if (EXACT || k < s)
+          red[pg * s + k] = (rgi == 0 ? 0.0 : red[pg * s + k]) + (double)acc[0][k];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < E; e += 256) out[e] = red[e];
+}
+
 // H[e] = sum_blk partial[blk][e]  (fixed order: deterministic)
 __global__ void k_gram_reduce(int nblk, int E, const double* __restrict__ partial,
                               double* __restrict__ H) {
@@ -119,10 +271,54 @@ static void ensure_partial(pint_ctx ctx, size_t bytes) {
 }
 
 template <typename VT>
+static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V, int64_t bstride,
+                        const VT* W, double* H, cudaStream_t st) {
+  const int P = nb * s;
+  const size_t es = sizeof(VT);
+  if (n_pad % 64 != 0 || (bstride * es) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(V) % 16 != 0 || reinterpret_cast<uintptr_t>(W) % 16 != 0)
+    return false;
+  // tile rows: largest power of two <= 64 with a stage of at most 48 KB
+  int TR = 64;
+  while (TR > 4 && (size_t)(nb + 1) * TR * s * es > 48 * 1024) TR >>= 1;
+  if ((size_t)(nb + 1) * TR * s * es > 48 * 1024) return false;
+  int PT = 32;
+  while (PT < P && PT < 256) PT <<= 1;
+  const int npt = (P + PT - 1) / PT;
+  const int64_t want = std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, n_pad / 64));
+  int64_t rpc = (n_pad + want - 1) / want;
+  rpc = ((rpc + 63) / 64) * 64;
+  const int nblk = (int)((n_pad + rpc - 1) / rpc);
+  const int E = P * s;
+  ensure_partial(ctx, sizeof(double) * (size_t)nblk * E);
+  const size_t stage_bytes = (size_t)(nb + 1) * TR * s * es;
+  const size_t smem = std::max(kStages * stage_bytes, (PT < 256 ? sizeof(double) * E : (size_t)0));
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool EX = decltype(E_)::value;
+    auto launch = [&](auto kern) {
+      PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<nblk, 256, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, ctx->d_partial,
+                                    ctx->d_flag);
+    };
+    if (npt == 1) launch(k_gram_bulk<VT, S, EX, 1>);
+    else if (npt == 2) launch(k_gram_bulk<VT, S, EX, 2>);
+    else launch(k_gram_bulk<VT, S, EX, 4>);
+  });
+  check_launch("k_gram_bulk");
+  k_gram_reduce<<<(E + 255) / 256, 256, 0, st>>>(nblk, E, ctx->d_partial, H);
+  check_launch("k_gram_reduce");
+  ctx->launches += 2;
+  return true;
+}
+
+template <typename VT>
 static void gram_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t bstride,
-                   const VT* W, double* H, cudaStream_t st, int fam = PF_GRAM) {
+                   const VT* W, double* H, cudaStream_t st, int fam = PF_GRAM,
+                   int64_t n_pad = 0) {
   const int P = nb * s;
   ProfScope ps(ctx, fam, sizeof(VT) * (double)(nb + 1) * n * s, 2.0 * n * nb * s * s, st);
+  if (n_pad > 0 && gram_bulk_t<VT>(ctx, n_pad, s, nb, V, bstride, W, H, st)) return;
   PINT_REQUIRE(P <= 1024, PINT_ERR_INVALID, "Gram block too wide (nb*s > 1024)");
   int PT = 32;
   while (PT < P && PT < 256) PT <<= 1;
@@ -154,11 +350,13 @@ static void gram_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t 
 }
 
 void launch_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb, const void* V,
-                 int64_t bstride, const void* W, double* H, cudaStream_t st) {
+                 int64_t bstride, const void* W, double* H, cudaStream_t st, int64_t n_pad) {
   if (precision == PINT_FP64)
-    gram_t<double>(ctx, n, s, nb, (const double*)V, bstride, (const double*)W, H, st);
+    gram_t<double>(ctx, n, s, nb, (const double*)V, bstride, (const double*)W, H, st, PF_GRAM,
+                   n_pad);
   else
-    gram_t<float>(ctx, n, s, nb, (const float*)V, bstride, (const float*)W, H, st);
+    gram_t<float>(ctx, n, s, nb, (const float*)V, bstride, (const float*)W, H, st, PF_GRAM,
+                  n_pad);
 }
 
 // ------------------------------------------------------- block update (a6)
@@ -334,9 +532,9 @@ static CholScratch chol_scratch(pint_ctx ctx) {
 
 template <typename VT>
 static void cholqr_pass(pint_ctx ctx, int64_t n, int s, VT* W, double* R, double defl,
-                        int* defl_count, cudaStream_t st) {
+                        int* defl_count, cudaStream_t st, int64_t n_pad) {
   CholScratch cs = chol_scratch(ctx);
-  gram_t<VT>(ctx, n, s, 1, W, 0, W, cs.G, st, PF_CHOLQR);
+  gram_t<VT>(ctx, n, s, 1, W, 0, W, cs.G, st, PF_CHOLQR, n_pad);
   ProfScope ps(ctx, PF_CHOLQR, 2.0 * sizeof(VT) * n * s, 1.0 * n * s * s, st);
   k_chol<<<1, 256, 0, st>>>(s, cs.G, defl, R, cs.Rinv, defl_count);
   check_launch("k_chol");
@@ -352,15 +550,15 @@ static void cholqr_pass(pint_ctx ctx, int64_t n, int s, VT* W, double* R, double
 }
 
 void cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W, double* R,
-             int* defl_count, cudaStream_t st) {
+             int* defl_count, cudaStream_t st, int64_t n_pad) {
   CholScratch cs = chol_scratch(ctx);
   const double defl = precision == PINT_FP64 ? 1e-14 : 1e-8;
   if (precision == PINT_FP64) {
-    cholqr_pass<double>(ctx, n, s, (double*)W, cs.R1, defl, defl_count, st);
-    cholqr_pass<double>(ctx, n, s, (double*)W, cs.R2, defl, defl_count, st);
+    cholqr_pass<double>(ctx, n, s, (double*)W, cs.R1, defl, defl_count, st, n_pad);
+    cholqr_pass<double>(ctx, n, s, (double*)W, cs.R2, defl, defl_count, st, n_pad);
   } else {
-    cholqr_pass<float>(ctx, n, s, (float*)W, cs.R1, defl, defl_count, st);
-    cholqr_pass<float>(ctx, n, s, (float*)W, cs.R2, defl, defl_count, st);
+    cholqr_pass<float>(ctx, n, s, (float*)W, cs.R1, defl, defl_count, st, n_pad);
+    cholqr_pass<float>(ctx, n, s, (float*)W, cs.R2, defl, defl_count, st, n_pad);
   }
   ProfScope ps(ctx, PF_CHOLQR, 0.0, 2.0 * s * s * s, st);
   k_small_mm<<<1, 256, 0, st>>>(s, cs.R2, cs.R1, R);
@@ -520,6 +718,8 @@ struct KrylovWork {
   double* fnorm = nullptr;
   int* flag = nullptr;
   int* defl = nullptr;
+  int64_t n_pad = 0;     // rows per basis block (multiple of 64)
+  int64_t bs = 0;        // basis block stride in elements (n_pad * s)
   size_t bytes = 0;
   std::vector<std::pair<void*, size_t>> allocs;
 };
@@ -551,8 +751,14 @@ static KrylovWork* ensure_work(pint_op op, int prec, int m) {
   w->es = prec == PINT_FP64 ? 8 : 4;
   pint_ctx ctx = op->ctx;
   const size_t ns = (size_t)op->n * s;
+  // basis blocks hold n_pad = 64 * ceil(n / 64) rows; the extra rows stay
+  // zero (nothing writes them), which lets the Gram products stream whole
+  // 16-byte-aligned tiles with bulk copies
+  w->n_pad = ((op->n + 63) / 64) * 64;
+  w->bs = w->n_pad * s;
   try {
-    w->V = walloc(ctx, w, w->es * ns * (m + 1));
+    w->V = walloc(ctx, w, w->es * (size_t)w->bs * (m + 1));
+    PINT_CUDA(cudaMemset(w->V, 0, w->es * (size_t)w->bs * (m + 1)));
     w->Zt = walloc(ctx, w, w->es * ns);
     w->Xk = walloc(ctx, w, w->es * ns);
     w->Rs = walloc(ctx, w, w->es * ns);
@@ -593,7 +799,9 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
   const int vprec = prec == PINT_FP64 ? PINT_FP64 : PINT_FP32;
   const bool jac = o->precond == PINT_PC_JACOBI;
   const bool ilu = o->precond == PINT_PC_ILU0;
-  const int64_t bs = n * s;
+  const int64_t bs = w->bs;        // padded block stride of the basis
+  const int64_t ns = n * s;        // elements of an unpadded block vector
+  const int64_t np = w->n_pad;
   const size_t es = w->es;
   auto Vb = [&](int b) { return (void*)((char*)w->V + (size_t)b * bs * es); };
   const int ldh = (m + 1) * s;
@@ -603,9 +811,9 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
     for (int k = 0; k < s; ++k) t[k] = o->inner_tol;
     PINT_CUDA(cudaMemcpyAsync(w->target, t, 8 * s, cudaMemcpyHostToDevice, st));
   }
-  PINT_CUDA(cudaMemsetAsync(w->Xk, 0, es * bs, st));
+  PINT_CUDA(cudaMemsetAsync(w->Xk, 0, es * ns, st));
   PINT_CUDA(cudaMemsetAsync(w->defl, 0, 64, st));
-  PINT_CUDA(cudaMemcpyAsync(Vb(0), w->Rs, es * bs, cudaMemcpyDeviceToDevice, st));
+  PINT_CUDA(cudaMemcpyAsync(Vb(0), w->Rs, es * ns, cudaMemcpyDeviceToDevice, st));
   InnerResult res{0, 0, false, 0};
   const size_t hess_smem = 8 * (size_t)s * (m + 1) * s;
   const size_t back_smem = 8 * (size_t)m * s * s;
@@ -615,7 +823,7 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
                                  (int)back_smem));
   while (res.its < o->max_inner) {
     res.cycles += 1;
-    cholqr2(ctx, vprec, n, s, Vb(0), w->S, w->defl, st);
+    cholqr2(ctx, vprec, n, s, Vb(0), w->S, w->defl, st, np);
     {
       ProfScope ps(ctx, PF_HESS, 0.0, 0.0, st);
       k_gr_init<<<8, 256, 0, st>>>(ldh, s, w->S, w->Gr);
@@ -631,11 +839,11 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
       } else {
         launch_inner_spmm(op, prec, jac, Vb(j), Vb(j + 1), nullptr, st);
       }
-      launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg1, st);
+      launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg1, st, np);
       launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg1, Vb(j + 1), 0, st);
-      launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg2, st);
+      launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg2, st, np);
       launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg2, Vb(j + 1), 0, st);
-      cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, st);
+      cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, st, np);
       ProfScope psh(ctx, PF_HESS, 0.0, 4.0 * (j + 1) * s * s * (s + 1), st);
       k_hess_step<<<1, 512, 8 * (size_t)s * (j + 2) * s, st>>>(
           j, s, ldh, w->Hg1, w->Hg2, w->Rn, w->Hb, w->refl, w->Gr, w->target, w->est, w->flag);
@@ -643,7 +851,10 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
       ctx->launches += 1;
       res.its += 1;
       PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 2, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
       PINT_CUDA(cudaStreamSynchronize(st));
+      PINT_REQUIRE(ctx->h_flag[2] == 0, PINT_ERR_TIMEOUT,
+                   "bulk-copy wait in the Gram kernel exceeded its time budget");
       if (ilu) ilu_check(op);
       PINT_REQUIRE(ctx->h_flag[1] == 0, PINT_ERR_BREAKDOWN,
                    "non-finite residual estimate in block GMRES");
@@ -664,11 +875,11 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
       launch_update(ctx, vprec, n, s, j, w->V, bs, w->Yls, w->Zt, 1, st);
       void* tmp = Vb(std::min(j, m));   // block j is free after the cycle
       ilu_apply(op, prec, w->Zt, tmp, st);
-      ProfScope ps(ctx, PF_VEC, 3.0 * es * bs, 1.0 * bs, st);
+      ProfScope ps(ctx, PF_VEC, 3.0 * es * ns, 1.0 * ns, st);
       if (vprec == PINT_FP64)
-        k_axpy<double><<<grid_for(bs, 256), 256, 0, st>>>(bs, (const double*)tmp, (double*)w->Xk);
+        k_axpy<double><<<grid_for(ns, 256), 256, 0, st>>>(ns, (const double*)tmp, (double*)w->Xk);
       else
-        k_axpy<float><<<grid_for(bs, 256), 256, 0, st>>>(bs, (const float*)tmp, (float*)w->Xk);
+        k_axpy<float><<<grid_for(ns, 256), 256, 0, st>>>(ns, (const float*)tmp, (float*)w->Xk);
       check_launch("k_axpy");
       ctx->launches += 1;
     } else {
