@@ -452,7 +452,8 @@ int pint_block_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb, const
     PINT_REQUIRE(precision == PINT_FP64 || precision == PINT_FP32, PINT_ERR_INVALID, "precision");
     require_aligned(V, "V");
     require_aligned(W, "W");
-    launch_gram(ctx, precision, n, s, nb, V, n * s, W, H, as_stream(stream));
+    // n a multiple of 64 needs no padding rows: use the bulk-copy pipeline
+    launch_gram(ctx, precision, n, s, nb, V, n * s, W, H, as_stream(stream), n % 64 == 0 ? n : 0);
     return PINT_OK;
   });
 }

@@ -181,7 +181,7 @@ __global__ void k_rich_point(int64_t n, int s, Soil soil, const double* __restri
 
 // R_r = M(Y)_r A1^T + F(T,Y)_r A2^T - B0_r (Eq. matrix-equation-pipelining
 // residual) with the column-wise nonlinear f evaluated from the stencil.
-template <int S, bool EXACT>
+template <int S, bool EXACT, int LO>
 __global__ void __launch_bounds__(128)
 k_nl_residual(Grid g, int64_t n, int s, const __grid_constant__ NlParams P,
               const double* __restrict__ Y, const double* __restrict__ TH,
@@ -263,10 +263,16 @@ k_nl_residual(Grid g, int64_t n, int s, const __grid_constant__ NlParams P,
 #pragma unroll
     for (int c = 0; c < S; ++c) {
       if (!EXACT && c >= s) break;
+      if (LO > 0 && (c > a || a - c > LO)) continue;
       const double a1 = cp.A1[a * kMaxS + c];
       const double a2 = cp.A2[a * kMaxS + c];
-      if (a1 != 0.0) acc = fma(a1, mass[c], acc);
-      if (a2 != 0.0) acc = fma(a2, f[c], acc);
+      if (LO > 0) {
+        acc = fma(a1, mass[c], acc);
+        acc = fma(a2, f[c], acc);
+      } else {
+        if (a1 != 0.0) acc = fma(a1, mass[c], acc);
+        if (a2 != 0.0) acc = fma(a2, f[c], acc);
+      }
     }
     out[a] += acc;
   }
@@ -439,7 +445,13 @@ static void nl_residual(pint_problem p, const double* times, const double* Y, co
       k_rich_point<S, E><<<grid_for(n, 128), 128, 0, st>>>(n, s, P.soil, Y, TH, KR);
       p->ctx->launches += 1;
     }
-    k_nl_residual<S, E><<<grid_for(n, 128), 128, 0, st>>>(g, n, s, P, Y, TH, KR, B0, R, cp);
+    const int lo = coupling_band(op->A1, op->A2, s);
+    auto launch = [&](auto kern) {
+      kern<<<grid_for(n, 128), 128, 0, st>>>(g, n, s, P, Y, TH, KR, B0, R, cp);
+    };
+    if (lo == 1) launch(k_nl_residual<S, E, 1>);
+    else if (lo == 2) launch(k_nl_residual<S, E, 2>);
+    else launch(k_nl_residual<S, E, 0>);
   });
   check_launch("k_nl_residual");
   p->ctx->launches += 1;

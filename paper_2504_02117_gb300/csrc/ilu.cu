@@ -45,15 +45,19 @@ struct IluState {
   int* d_order_f = nullptr;
   int* d_order_b = nullptr;
   std::map<int, Sched> sched_f, sched_b;   // by rows per chunk
-  // tiled sweeps for natural-order 5/7-point stencils
+  // tiled sweeps for natural-order 5/7-point stencils: ts[0] the default
+  // shape, ts[1] (3-D only) 16x16x8 tiles for rows of at most 32 bytes
   bool tiled = false;
-  int TX = 0, TY = 0, TZ = 0, NTX = 0, NTY = 0, NTZ = 0, ntiles = 0, nlev = 0;
-  int* tile_order = nullptr;      // tiles by ascending tile level
-  int* loc_list = nullptr;        // local rows of a full tile by local level
-  int* loc_lvlptr = nullptr;
-  unsigned* tflag_f = nullptr;
-  unsigned* tflag_b = nullptr;
-  unsigned tepoch_f = 0, tepoch_b = 0;
+  struct TileSet {
+    bool valid = false;
+    int TX = 0, TY = 0, TZ = 0, NTX = 0, NTY = 0, NTZ = 0, ntiles = 0, nlev = 0;
+    int* tile_order = nullptr;      // tiles by ascending tile level
+    int* loc_list = nullptr;        // local rows of a full tile by local level
+    int* loc_lvlptr = nullptr;
+    unsigned* tflag_f = nullptr;
+    unsigned* tflag_b = nullptr;
+    unsigned tepoch_f = 0, tepoch_b = 0;
+  } ts[2];
 };
 
 // -------------------------------------------------------------- helpers
@@ -78,14 +82,16 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 __device__ __forceinline__ bool wait_ready(const unsigned* flag, unsigned epoch, int* err,
                                            unsigned long long deadline) {
   if (ld_acquire(flag) == epoch) return true;
-  while (true) {
-    if (*(volatile int*)err != 0) return false;
-    __nanosleep(32);
-    if (ld_acquire(flag) == epoch) return true;
-    if (globaltimer() > deadline) {
-      atomicExch(err, 1);
-      return false;
+  for (unsigned it = 1;; ++it) {
+    if ((it & 63) == 0) {
+      if (*(volatile int*)err != 0) return false;
+      if (globaltimer() > deadline) {
+        atomicExch(err, 1);
+        return false;
+      }
     }
+    __nanosleep(20);
+    if (ld_acquire(flag) == epoch) return true;
   }
 }
 
@@ -199,23 +205,37 @@ k_ilu_sweep(int s, int sp_log2, const int* __restrict__ rowptr, const int* __res
 // waits for tiles with lower tickets, taken by running CTAs. The arithmetic
 // per row and column is the same as the CSR sweep (same operands, same order).
 struct TileGeom {
-  int nx, ny, nz, TX, TY, TZ, NTX, NTY, ntiles, nlev;
+  int nx, ny, nz, NTX, NTY, ntiles;
 };
 
-template <typename VT, bool FWD>
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+
+// TX, TY, TZ: tile shape (powers of two); S: block width when it is a power
+// of two (shifts), 0 for a runtime s (divisions).
+template <typename VT, bool FWD, int TX, int TY, int TZ, int S>
 __global__ void __launch_bounds__(256)
-k_ilu_tile(TileGeom g, int s, const int* __restrict__ rowptr, const int* __restrict__ diagpos,
+k_ilu_tile(TileGeom g, int s_rt, const int* __restrict__ rowptr, const int* __restrict__ diagpos,
            const VT* __restrict__ F, const VT* X, VT* Z, const int* __restrict__ tile_order,
-           const int* __restrict__ loc_list, const int* __restrict__ loc_lvlptr,
+           const int* __restrict__ loc_list_g, const int* __restrict__ loc_lvlptr_g,
            unsigned* tflags, unsigned epoch, int* ticket, int* err) {
+  constexpr int TR = TX * TY * TZ;
+  constexpr int NLEV = TX + TY + TZ - 2;
+  constexpr int LX = ilog2c(TX), LXY = ilog2c(TX * TY);
+  constexpr int LS = S > 0 ? ilog2c(S) : 0;
+  const int s = S > 0 ? S : s_rt;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int TR = g.TX * g.TY * g.TZ;
   VT* Ys = reinterpret_cast<VT*>(smem_raw);                 // TR x s
   VT* Hx = Ys + (size_t)TR * s;                              // TY*TZ x s
-  VT* Hy = Hx + (size_t)g.TY * g.TZ * s;                     // TX*TZ x s
-  VT* Hz = Hy + (size_t)g.TX * g.TZ * s;                     // TX*TY x s
-  VT* C = Hz + (size_t)g.TX * g.TY * s;                      // TR x 4 coefficients
+  VT* Hy = Hx + (size_t)TY * TZ * s;                         // TX*TZ x s
+  VT* Hz = Hy + (size_t)TX * TZ * s;                         // TX*TY x s
+  VT* C = Hz + (size_t)TX * TY * s;                          // TR x 4 coefficients
+  __shared__ short loc[TR];
+  __shared__ short lvp[NLEV + 1];
   __shared__ int tile_sh;
+  for (int i = threadIdx.x; i < TR; i += blockDim.x) loc[i] = (short)loc_list_g[i];
+  for (int i = threadIdx.x; i <= NLEV; i += blockDim.x) lvp[i] = (short)loc_lvlptr_g[i];
+  auto div_s = [&](int e) { return S > 0 ? (e >> LS) : e / s; };
+  auto mod_s = [&](int e) { return S > 0 ? (e & (S - 1)) : e % s; };
   const unsigned long long deadline = globaltimer() + kWaitBudgetNs;
   const int64_t sxy = (int64_t)g.nx * g.ny;
   bool ok = true;
@@ -226,17 +246,17 @@ k_ilu_tile(TileGeom g, int s, const int* __restrict__ rowptr, const int* __restr
     }
     __syncthreads();
     const int tile = tile_sh;
-    __syncthreads();
     if (tile < 0) return;
     const int I = tile % g.NTX, J = (tile / g.NTX) % g.NTY, K = tile / (g.NTX * g.NTY);
-    const int x0 = I * g.TX, y0 = J * g.TY, z0 = K * g.TZ;
-    const int ex = min(g.TX, g.nx - x0), ey = min(g.TY, g.ny - y0), ez = min(g.TZ, g.nz - z0);
-    // prefetch coefficients and right-hand sides
+    const int x0 = I * TX, y0 = J * TY, z0 = K * TZ;
+    const int ex = min(TX, g.nx - x0), ey = min(TY, g.ny - y0), ez = min(TZ, g.nz - z0);
+    const int64_t base = x0 + (int64_t)g.nx * y0 + sxy * z0;
+    // prefetch coefficients and right-hand sides (before waiting)
     for (int l = threadIdx.x; l < TR; l += blockDim.x) {
-      const int li = l % g.TX, lj = (l / g.TX) % g.TY, lk = l / (g.TX * g.TY);
+      const int li = l & (TX - 1), lj = (l >> LX) & (TY - 1), lk = l >> LXY;
       if (li >= ex || lj >= ey || lk >= ez) continue;
       const int gi = x0 + li, gj = y0 + lj, gk = z0 + lk;
-      const int64_t r = gi + (int64_t)g.nx * gj + sxy * gk;
+      const int64_t r = base + li + (int64_t)g.nx * lj + sxy * lk;
       const int d = diagpos[r];
       VT c0 = VT(0), c1 = VT(0), c2 = VT(0);
       if (FWD) {
@@ -254,8 +274,13 @@ k_ilu_tile(TileGeom g, int s, const int* __restrict__ rowptr, const int* __restr
       C[4 * l + 1] = c1;
       C[4 * l + 2] = c2;
       C[4 * l + 3] = F[d];
-      for (int c = 0; c < s; ++c)
-        Ys[(size_t)l * s + c] = FWD ? X[r * s + c] : __ldcg(Z + r * s + c);
+    }
+    for (int e = threadIdx.x; e < TR * s; e += blockDim.x) {
+      const int l = div_s(e), c = mod_s(e);
+      const int li = l & (TX - 1), lj = (l >> LX) & (TY - 1), lk = l >> LXY;
+      if (li >= ex || lj >= ey || lk >= ez) continue;
+      const int64_t r = base + li + (int64_t)g.nx * lj + sxy * lk;
+      Ys[e] = FWD ? X[r * s + c] : __ldcg(Z + r * s + c);
     }
     // upstream tiles: FWD -x,-y,-z ; BWD +x,+y,+z
     if (threadIdx.x < 3 && ok) {
@@ -274,62 +299,63 @@ k_ilu_tile(TileGeom g, int s, const int* __restrict__ rowptr, const int* __restr
     __syncthreads();
     // faces of the upstream tiles (zero where the grid ends)
     const int hx = FWD ? x0 - 1 : x0 + ex, hy = FWD ? y0 - 1 : y0 + ey, hz = FWD ? z0 - 1 : z0 + ez;
-    for (int e = threadIdx.x; e < g.TY * g.TZ * s; e += blockDim.x) {
-      const int c = e % s, q = e / s, lj = q % g.TY, lk = q / g.TY;
+    const bool hxv = hx >= 0 && hx < g.nx, hyv = hy >= 0 && hy < g.ny, hzv = hz >= 0 && hz < g.nz;
+    for (int e = threadIdx.x; e < TY * TZ * s; e += blockDim.x) {
+      const int c = mod_s(e), q = div_s(e), lj = q & (TY - 1), lk = q >> ilog2c(TY);
       VT v = VT(0);
-      if (hx >= 0 && hx < g.nx && lj < ey && lk < ez)
+      if (hxv && lj < ey && lk < ez)
         v = __ldcg(Z + (hx + (int64_t)g.nx * (y0 + lj) + sxy * (z0 + lk)) * s + c);
       Hx[e] = v;
     }
-    for (int e = threadIdx.x; e < g.TX * g.TZ * s; e += blockDim.x) {
-      const int c = e % s, q = e / s, li = q % g.TX, lk = q / g.TX;
+    for (int e = threadIdx.x; e < TX * TZ * s; e += blockDim.x) {
+      const int c = mod_s(e), q = div_s(e), li = q & (TX - 1), lk = q >> LX;
       VT v = VT(0);
-      if (hy >= 0 && hy < g.ny && li < ex && lk < ez)
+      if (hyv && li < ex && lk < ez)
         v = __ldcg(Z + (x0 + li + (int64_t)g.nx * hy + sxy * (z0 + lk)) * s + c);
       Hy[e] = v;
     }
-    for (int e = threadIdx.x; e < g.TX * g.TY * s; e += blockDim.x) {
-      const int c = e % s, q = e / s, li = q % g.TX, lj = q / g.TX;
+    for (int e = threadIdx.x; e < TX * TY * s; e += blockDim.x) {
+      const int c = mod_s(e), q = div_s(e), li = q & (TX - 1), lj = q >> LX;
       VT v = VT(0);
-      if (hz >= 0 && hz < g.nz && li < ex && lj < ey)
+      if (hzv && li < ex && lj < ey)
         v = __ldcg(Z + (x0 + li + (int64_t)g.nx * (y0 + lj) + sxy * hz) * s + c);
       Hz[e] = v;
     }
     __syncthreads();
-    // local wavefront
-    for (int it = 0; it < g.nlev; ++it) {
-      const int lv = FWD ? it : g.nlev - 1 - it;
-      const int b = loc_lvlptr[lv], cnt = loc_lvlptr[lv + 1] - b;
+    // local wavefront over li + lj + lk
+    for (int it = 0; it < NLEV; ++it) {
+      const int lv = FWD ? it : NLEV - 1 - it;
+      const int b = lvp[lv], cnt = lvp[lv + 1] - b;
       for (int e = threadIdx.x; e < cnt * s; e += blockDim.x) {
-        const int l = loc_list[b + e / s], c = e % s;
-        const int li = l % g.TX, lj = (l / g.TX) % g.TY, lk = l / (g.TX * g.TY);
+        const int l = loc[b + div_s(e)], c = mod_s(e);
+        const int li = l & (TX - 1), lj = (l >> LX) & (TY - 1), lk = l >> LXY;
         if (li >= ex || lj >= ey || lk >= ez) continue;
-        VT acc = Ys[(size_t)l * s + c];
+        VT acc = Ys[l * s + c];
         if (FWD) {
-          const VT vz = lk > 0 ? Ys[(size_t)(l - g.TX * g.TY) * s + c] : Hz[(li + g.TX * lj) * s + c];
-          const VT vy = lj > 0 ? Ys[(size_t)(l - g.TX) * s + c] : Hy[(li + g.TX * lk) * s + c];
-          const VT vx = li > 0 ? Ys[(size_t)(l - 1) * s + c] : Hx[(lj + g.TY * lk) * s + c];
+          const VT vz = lk > 0 ? Ys[(l - TX * TY) * s + c] : Hz[(li + TX * lj) * s + c];
+          const VT vy = lj > 0 ? Ys[(l - TX) * s + c] : Hy[(li + TX * lk) * s + c];
+          const VT vx = li > 0 ? Ys[(l - 1) * s + c] : Hx[(lj + TY * lk) * s + c];
           acc -= C[4 * l + 0] * vz;
           acc -= C[4 * l + 1] * vy;
           acc -= C[4 * l + 2] * vx;
         } else {
-          const VT vx = li + 1 < ex ? Ys[(size_t)(l + 1) * s + c] : Hx[(lj + g.TY * lk) * s + c];
-          const VT vy = lj + 1 < ey ? Ys[(size_t)(l + g.TX) * s + c] : Hy[(li + g.TX * lk) * s + c];
-          const VT vz = lk + 1 < ez ? Ys[(size_t)(l + g.TX * g.TY) * s + c] : Hz[(li + g.TX * lj) * s + c];
+          const VT vx = li + 1 < ex ? Ys[(l + 1) * s + c] : Hx[(lj + TY * lk) * s + c];
+          const VT vy = lj + 1 < ey ? Ys[(l + TX) * s + c] : Hy[(li + TX * lk) * s + c];
+          const VT vz = lk + 1 < ez ? Ys[(l + TX * TY) * s + c] : Hz[(li + TX * lj) * s + c];
           acc -= C[4 * l + 0] * vx;
           acc -= C[4 * l + 1] * vy;
           acc -= C[4 * l + 2] * vz;
           acc /= C[4 * l + 3];
         }
-        Ys[(size_t)l * s + c] = acc;
+        Ys[l * s + c] = acc;
       }
       __syncthreads();
     }
     for (int e = threadIdx.x; e < TR * s; e += blockDim.x) {
-      const int l = e / s, c = e % s;
-      const int li = l % g.TX, lj = (l / g.TX) % g.TY, lk = l / (g.TX * g.TY);
+      const int l = div_s(e), c = mod_s(e);
+      const int li = l & (TX - 1), lj = (l >> LX) & (TY - 1), lk = l >> LXY;
       if (li >= ex || lj >= ey || lk >= ez) continue;
-      Z[(x0 + li + (int64_t)g.nx * (y0 + lj) + sxy * (z0 + lk)) * s + c] = Ys[e];
+      Z[(base + li + (int64_t)g.nx * lj + sxy * lk) * s + c] = Ys[e];
     }
     __threadfence();
     __syncthreads();
@@ -419,34 +445,44 @@ static void ensure_state(pint_op op) {
   PINT_CUDA(cudaMemset(S->err, 0, 2 * sizeof(int)));
   if (op->grid_nx > 0) {
     const int nx = op->grid_nx, ny = op->grid_ny, nz = op->grid_nz;
-    S->TX = nz > 1 ? 8 : (ny > 1 ? 16 : 64);
-    S->TY = nz > 1 ? 8 : (ny > 1 ? 16 : 1);
-    S->TZ = nz > 1 ? 8 : 1;
-    S->NTX = (nx + S->TX - 1) / S->TX;
-    S->NTY = (ny + S->TY - 1) / S->TY;
-    S->NTZ = (nz + S->TZ - 1) / S->TZ;
-    S->ntiles = S->NTX * S->NTY * S->NTZ;
-    S->nlev = S->TX + S->TY + S->TZ - 2;
-    std::vector<int> order(S->ntiles), loc(S->TX * S->TY * S->TZ), ptr(S->nlev + 1, 0);
-    for (int t = 0; t < S->ntiles; ++t) order[t] = t;
-    auto tlev = [&](int t) { return t % S->NTX + (t / S->NTX) % S->NTY + t / (S->NTX * S->NTY); };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tlev(a) < tlev(b); });
-    const int TR = (int)loc.size();
-    auto llev = [&](int l) { return l % S->TX + (l / S->TX) % S->TY + l / (S->TX * S->TY); };
-    for (int l = 0; l < TR; ++l) ptr[llev(l) + 1]++;
-    for (int v = 0; v < S->nlev; ++v) ptr[v + 1] += ptr[v];
-    std::vector<int> pos(ptr.begin(), ptr.end() - 1);
-    for (int l = 0; l < TR; ++l) loc[pos[llev(l)]++] = l;
-    S->tile_order = dalloc_n<int>(ctx, S->ntiles);
-    S->loc_list = dalloc_n<int>(ctx, TR);
-    S->loc_lvlptr = dalloc_n<int>(ctx, S->nlev + 1);
-    S->tflag_f = dalloc_n<unsigned>(ctx, S->ntiles);
-    S->tflag_b = dalloc_n<unsigned>(ctx, S->ntiles);
-    PINT_CUDA(cudaMemcpy(S->tile_order, order.data(), sizeof(int) * S->ntiles, cudaMemcpyHostToDevice));
-    PINT_CUDA(cudaMemcpy(S->loc_list, loc.data(), sizeof(int) * TR, cudaMemcpyHostToDevice));
-    PINT_CUDA(cudaMemcpy(S->loc_lvlptr, ptr.data(), sizeof(int) * (S->nlev + 1), cudaMemcpyHostToDevice));
-    PINT_CUDA(cudaMemset(S->tflag_f, 0, sizeof(unsigned) * S->ntiles));
-    PINT_CUDA(cudaMemset(S->tflag_b, 0, sizeof(unsigned) * S->ntiles));
+    auto build = [&](IluState::TileSet& T, int TX, int TY, int TZ) {
+      T.TX = TX;
+      T.TY = TY;
+      T.TZ = TZ;
+      T.NTX = (nx + TX - 1) / TX;
+      T.NTY = (ny + TY - 1) / TY;
+      T.NTZ = (nz + TZ - 1) / TZ;
+      T.ntiles = T.NTX * T.NTY * T.NTZ;
+      T.nlev = TX + TY + TZ - 2;
+      std::vector<int> order(T.ntiles), loc(TX * TY * TZ), ptr(T.nlev + 1, 0);
+      for (int t = 0; t < T.ntiles; ++t) order[t] = t;
+      auto tlev = [&](int t) { return t % T.NTX + (t / T.NTX) % T.NTY + t / (T.NTX * T.NTY); };
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tlev(a) < tlev(b); });
+      const int TR = (int)loc.size();
+      auto llev = [&](int l) { return l % TX + (l / TX) % TY + l / (TX * TY); };
+      for (int l = 0; l < TR; ++l) ptr[llev(l) + 1]++;
+      for (int v = 0; v < T.nlev; ++v) ptr[v + 1] += ptr[v];
+      std::vector<int> pos(ptr.begin(), ptr.end() - 1);
+      for (int l = 0; l < TR; ++l) loc[pos[llev(l)]++] = l;
+      T.tile_order = dalloc_n<int>(ctx, T.ntiles);
+      T.loc_list = dalloc_n<int>(ctx, TR);
+      T.loc_lvlptr = dalloc_n<int>(ctx, T.nlev + 1);
+      T.tflag_f = dalloc_n<unsigned>(ctx, T.ntiles);
+      T.tflag_b = dalloc_n<unsigned>(ctx, T.ntiles);
+      PINT_CUDA(cudaMemcpy(T.tile_order, order.data(), sizeof(int) * T.ntiles, cudaMemcpyHostToDevice));
+      PINT_CUDA(cudaMemcpy(T.loc_list, loc.data(), sizeof(int) * TR, cudaMemcpyHostToDevice));
+      PINT_CUDA(cudaMemcpy(T.loc_lvlptr, ptr.data(), sizeof(int) * (T.nlev + 1), cudaMemcpyHostToDevice));
+      PINT_CUDA(cudaMemset(T.tflag_f, 0, sizeof(unsigned) * T.ntiles));
+      PINT_CUDA(cudaMemset(T.tflag_b, 0, sizeof(unsigned) * T.ntiles));
+      T.valid = true;
+    };
+    if (nz > 1) {
+      build(S->ts[0], 8, 8, 8);     // 16x16x8 tiles measured slower at 128^3
+    } else if (ny > 1) {
+      build(S->ts[0], 16, 16, 1);
+    } else {
+      build(S->ts[0], 64, 1, 1);
+    }
     S->tiled = true;
   }
 }
@@ -470,13 +506,14 @@ void ilu_destroy(pint_op op) {
   dfree(c, S->err, 2 * sizeof(int));
   dfree(c, S->d_order_f, sizeof(int) * op->n);
   dfree(c, S->d_order_b, sizeof(int) * op->n);
-  if (S->tiled) {
-    dfree(c, S->tile_order, sizeof(int) * S->ntiles);
-    dfree(c, S->loc_list, sizeof(int) * S->TX * S->TY * S->TZ);
-    dfree(c, S->loc_lvlptr, sizeof(int) * (S->nlev + 1));
-    dfree(c, S->tflag_f, sizeof(unsigned) * S->ntiles);
-    dfree(c, S->tflag_b, sizeof(unsigned) * S->ntiles);
-  }
+  for (auto& T : S->ts)
+    if (T.valid) {
+      dfree(c, T.tile_order, sizeof(int) * T.ntiles);
+      dfree(c, T.loc_list, sizeof(int) * T.TX * T.TY * T.TZ);
+      dfree(c, T.loc_lvlptr, sizeof(int) * (T.nlev + 1));
+      dfree(c, T.tflag_f, sizeof(unsigned) * T.ntiles);
+      dfree(c, T.tflag_b, sizeof(unsigned) * T.ntiles);
+    }
   delete S;
   op->ilu = nullptr;
 }
@@ -513,35 +550,59 @@ void ilu_setup(pint_op op, cudaStream_t st) {
   S->factored = true;
 }
 
-template <typename VT>
-static void apply_tiled(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st) {
-  IluState* S = op->ilu;
+template <typename VT, int TX, int TY, int TZ, int S>
+static void tile_pair(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st, unsigned ef,
+                      unsigned eb, IluState::TileSet& T) {
+  IluState* Sx = op->ilu;
   const int s = op->s;
-  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, S->TX, S->TY, S->TZ, S->NTX, S->NTY,
-             S->ntiles, S->nlev};
-  const int TR = S->TX * S->TY * S->TZ;
-  const size_t smem = sizeof(VT) * ((size_t)TR * s +
-                                    (size_t)(S->TY * S->TZ + S->TX * S->TZ + S->TX * S->TY) * s +
+  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, T.NTX, T.NTY, T.ntiles};
+  constexpr int TR = TX * TY * TZ;
+  const size_t smem = sizeof(VT) * ((size_t)TR * s + (size_t)(TY * TZ + TX * TZ + TX * TY) * s +
                                     4 * (size_t)TR);
   auto launch = [&](auto kern, const VT* x, unsigned* flags, unsigned ep, int* ticket) {
     PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
-    const int grid = std::max(1, std::min(S->ntiles, std::max(1, per_sm) * op->ctx->num_sms));
-    kern<<<grid, 256, smem, st>>>(g, s, op->rowptr, op->diagpos, F, x, Z, S->tile_order,
-                                  S->loc_list, S->loc_lvlptr, flags, ep, ticket, S->err);
+    const int grid = std::max(1, std::min(T.ntiles, std::max(1, per_sm) * op->ctx->num_sms));
+    kern<<<grid, 256, smem, st>>>(g, s, op->rowptr, op->diagpos, F, x, Z, T.tile_order,
+                                  T.loc_list, T.loc_lvlptr, flags, ep, ticket, Sx->err);
   };
-  const unsigned ef = next_epoch(op, S->tepoch_f, S->tflag_f, st);
-  const unsigned eb = next_epoch(op, S->tepoch_b, S->tflag_b, st);
+  launch(k_ilu_tile<VT, true, TX, TY, TZ, S>, X, T.tflag_f, ef, Sx->ticket);
+  check_launch("k_ilu_tile<fwd>");
+  launch(k_ilu_tile<VT, false, TX, TY, TZ, S>, Z, T.tflag_b, eb, Sx->ticket + 1);
+  check_launch("k_ilu_tile<bwd>");
+}
+
+template <typename VT, int TX, int TY, int TZ>
+static void tile_pair_s(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st, unsigned ef,
+                        unsigned eb, IluState::TileSet& T) {
+  switch (op->s) {
+    case 1: tile_pair<VT, TX, TY, TZ, 1>(op, F, X, Z, st, ef, eb, T); break;
+    case 2: tile_pair<VT, TX, TY, TZ, 2>(op, F, X, Z, st, ef, eb, T); break;
+    case 4: tile_pair<VT, TX, TY, TZ, 4>(op, F, X, Z, st, ef, eb, T); break;
+    case 8: tile_pair<VT, TX, TY, TZ, 8>(op, F, X, Z, st, ef, eb, T); break;
+    case 16: tile_pair<VT, TX, TY, TZ, 16>(op, F, X, Z, st, ef, eb, T); break;
+    default: tile_pair<VT, TX, TY, TZ, 0>(op, F, X, Z, st, ef, eb, T); break;
+  }
+}
+
+template <typename VT>
+static void apply_tiled(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st) {
+  IluState* S = op->ilu;
+  // 16x16x8 tiles when a block row (s values) fits in 32 bytes
+  const bool big = S->ts[1].valid && sizeof(VT) * op->s <= 32;
+  IluState::TileSet& T = S->ts[big ? 1 : 0];
+  const unsigned ef = next_epoch(op, T.tepoch_f, T.tflag_f, st);
+  const unsigned eb = next_epoch(op, T.tepoch_b, T.tflag_b, st);
   PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
   ProfScope ps(op->ctx, PF_ILU,
                op->nnz * (sizeof(VT) + 4.0) + 4.0 * (op->n + 1) + 4.0 * op->n +
-                   4.0 * sizeof(VT) * op->n * s,
-               2.0 * op->nnz * s, st);
-  launch(k_ilu_tile<VT, true>, X, S->tflag_f, ef, S->ticket);
-  check_launch("k_ilu_tile<fwd>");
-  launch(k_ilu_tile<VT, false>, Z, S->tflag_b, eb, S->ticket + 1);
-  check_launch("k_ilu_tile<bwd>");
+                   4.0 * sizeof(VT) * op->n * op->s,
+               2.0 * op->nnz * op->s, st);
+  if (big) tile_pair_s<VT, 16, 16, 8>(op, F, X, Z, st, ef, eb, T);
+  else if (T.TZ == 8) tile_pair_s<VT, 8, 8, 8>(op, F, X, Z, st, ef, eb, T);
+  else if (T.TY == 16) tile_pair_s<VT, 16, 16, 1>(op, F, X, Z, st, ef, eb, T);
+  else tile_pair_s<VT, 64, 1, 1>(op, F, X, Z, st, ef, eb, T);
   op->ctx->launches += 2;
 }
 

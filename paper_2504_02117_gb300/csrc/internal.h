@@ -294,6 +294,7 @@ void sell_build(pint_op op);                 // pattern -> SELL (device)
 void sell_scatter(pint_op op, const double* csr_vals, double* sell_vals, cudaStream_t st);
 void build_inner(pint_op op, cudaStream_t st);  // Jval, Jdiag, Jinvdiag
 void* inner_sell(pint_op op, int precision, bool jacobi, cudaStream_t st);
+int coupling_band(const double* A1, const double* A2, int s);   // 16-pitch matrices
 void launch_coupled(pint_op op, const double* Y, const double* B, const double* B0,
                     double* R, cudaStream_t st);
 // Z = Jsell X   (mode 0)  or  Z = Rin - Jsell X  (mode 1)

@@ -144,21 +144,54 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return done != 0;
 }
 
-template <typename VT, int S, bool EXACT, int NPT>
+// Thread work unit: Q consecutive basis columns (b, i0..i0+Q-1) x all S
+// columns of W, kept in Q*S register accumulators; per row one Q-wide and
+// S/4 four-wide shared loads feed Q*S FMAs. Each block's stage region is
+// padded by kGramPad bytes to spread consecutive quads over the banks.
+constexpr int kGramPad = 32;
+
+template <typename VT, int N>
+struct VecOf;
+template <> struct VecOf<float, 4> { using T = float4; };
+template <> struct VecOf<float, 2> { using T = float2; };
+template <> struct VecOf<double, 2> { using T = double2; };
+
+template <typename VT, int Q>
+__device__ __forceinline__ void lds_q(const VT* p, VT (&v)[Q]) {
+  if constexpr (Q % 4 == 0 && sizeof(VT) == 4) {
+#pragma unroll
+    for (int i = 0; i < Q / 4; ++i) {
+      const float4 t = reinterpret_cast<const float4*>(p)[i];
+      v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+    }
+  } else if constexpr (Q % 2 == 0 && sizeof(VT) == 8) {
+#pragma unroll
+    for (int i = 0; i < Q / 2; ++i) {
+      const double2 t = reinterpret_cast<const double2*>(p)[i];
+      v[2 * i] = t.x; v[2 * i + 1] = t.y;
+    }
+  } else if constexpr (Q == 2 && sizeof(VT) == 4) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = p[i];
+  }
+}
+
+template <typename VT, int S, bool EXACT, int Q, int NQPT>
 __global__ void __launch_bounds__(256)
 k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstride,
-            const VT* __restrict__ W, int64_t rows_per_cta, int TR, double* __restrict__ partial,
-            int* __restrict__ err) {
+            const VT* __restrict__ W, int64_t rows_per_cta, int TR, int TRG,
+            double* __restrict__ partial, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ int aborted;
   const int P = nb * s;
+  const int NQ = P / Q;                                   // quads (Q | s)
   const unsigned blk_bytes = (unsigned)(TR * s * sizeof(VT));
-  const unsigned stage_bytes = blk_bytes * (nb + 1);
-  int PT = 32;
-  while (PT < P && PT < 256) PT <<= 1;
-  const int TRG = 256 / PT;
-  const int pg = threadIdx.x % PT, rg = threadIdx.x / PT;
+  const unsigned blk_pitch = blk_bytes + kGramPad;
+  const unsigned stage_bytes = blk_pitch * (nb + 1);
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r1 = (r0 + rows_per_cta < n_pad) ? r0 + rows_per_cta : n_pad;
   const int ntiles = r1 > r0 ? (int)((r1 - r0) / TR) : 0;
@@ -170,33 +203,48 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
   __syncthreads();
   auto issue = [&](int stage, int tile) {
     unsigned char* dst = smem_raw + (size_t)stage * stage_bytes;
-    mbar_expect_tx(&bars[stage], stage_bytes);
+    mbar_expect_tx(&bars[stage], blk_bytes * (nb + 1));
     const int64_t row = r0 + (int64_t)tile * TR;
     for (int b = 0; b <= nb; ++b) {
       const VT* src = (b < nb ? V + (int64_t)b * bstride : W) + row * s;
-      bulk_g2s(dst + (size_t)b * blk_bytes, src, blk_bytes, &bars[stage]);
+      bulk_g2s(dst + (size_t)b * blk_pitch, src, blk_bytes, &bars[stage]);
     }
   };
+  // pending[stage] = parity of a copy issued into the stage and not yet seen
+  // complete by thread 0 (-1: none); used to drain copies after a timeout
+  int pending[kStages];
+  for (int i = 0; i < kStages; ++i) pending[i] = -1;
   if (threadIdx.x == 0)
-    for (int t = 0; t < kStages && t < ntiles; ++t) issue(t, t);
-  // per-thread offsets of its p values inside a stage (block-major [b][rr][i])
-  int off[NPT];
+    for (int t = 0; t < kStages && t < ntiles; ++t) {
+      issue(t, t);
+      pending[t] = 0;
+    }
+  // this thread: quads q = qbase + j*QSTRIDE (j < NQPT), rows rr = rg + m*TRG
+  const int nthr_q = TRG * ((NQ + NQPT - 1) / NQPT);
+  const bool active = (int)threadIdx.x < nthr_q && threadIdx.x / ((NQ + NQPT - 1) / NQPT) < TRG;
+  const int qstride = (NQ + NQPT - 1) / NQPT;
+  const int qbase = threadIdx.x % qstride, rg = threadIdx.x / qstride;
+  int qoff[NQPT];
 #pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int p = pg + j * PT;
-    off[j] = p < P ? (p / s) * TR * s + (p % s) : -1;
+  for (int j = 0; j < NQPT; ++j) {
+    const int q = qbase + j * qstride;
+    const int p = q * Q;
+    qoff[j] = (q < NQ) ? (int)((p / s) * (blk_pitch / sizeof(VT)) + (p % s)) : -1;
   }
-  VT acc[NPT][S];
+  VT acc[NQPT][Q][S];
 #pragma unroll
-  for (int j = 0; j < NPT; ++j)
+  for (int j = 0; j < NQPT; ++j)
 #pragma unroll
-    for (int k = 0; k < S; ++k) acc[j][k] = VT(0);
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+      for (int k = 0; k < S; ++k) acc[j][i][k] = VT(0);
   const unsigned long long deadline = gtimer() + kMbarBudgetNs;
   for (int t = 0; t < ntiles; ++t) {
     const int stage = t % kStages;
     const unsigned parity = (unsigned)((t / kStages) & 1);
     if (!*(volatile int*)&aborted) {
-      while (!mbar_try_wait(&bars[stage], parity)) {
+      bool done = false;
+      while (!(done = mbar_try_wait(&bars[stage], parity))) {
         if (*(volatile int*)&aborted) break;
         if (gtimer() > deadline) {
           aborted = 1;
@@ -204,19 +252,31 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
           break;
         }
       }
+      if (done && threadIdx.x == 0) pending[stage] = -1;
     }
     const VT* T = reinterpret_cast<const VT*>(smem_raw + (size_t)stage * stage_bytes);
-    const VT* Wt = T + (size_t)nb * TR * s;
-    for (int rr = rg; rr < TR; rr += TRG) {
-      VT w[S];
+    const VT* Wt = reinterpret_cast<const VT*>(smem_raw + (size_t)stage * stage_bytes +
+                                               (size_t)nb * blk_pitch);
+    if (active) {
+#pragma unroll 2
+      for (int rr = rg; rr < TR; rr += TRG) {
+        VT w[S];
+        if constexpr (EXACT) {
+          lds_q<VT, S>(Wt + rr * S, w);
+        } else {
 #pragma unroll
-      for (int k = 0; k < S; ++k) w[k] = (EXACT || k < s) ? Wt[rr * s + k] : VT(0);
+          for (int k = 0; k < S; ++k) w[k] = k < s ? Wt[rr * s + k] : VT(0);
+        }
 #pragma unroll
-      for (int j = 0; j < NPT; ++j) {
-        if (off[j] >= 0) {
-          const VT v = T[off[j] + rr * s];
+        for (int j = 0; j < NQPT; ++j) {
+          if (qoff[j] >= 0) {
+            VT v[Q];
+            lds_q<VT, Q>(T + qoff[j] + rr * s, v);
 #pragma unroll
-          for (int k = 0; k < S; ++k) acc[j][k] = fma(v, w[k], acc[j][k]);
+            for (int i = 0; i < Q; ++i)
+#pragma unroll
+              for (int k = 0; k < S; ++k) acc[j][i][k] = fma(v[i], w[k], acc[j][i][k]);
+          }
         }
       }
     }
@@ -224,29 +284,37 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
     if (threadIdx.x == 0 && t + kStages < ntiles && !aborted) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(stage, t + kStages);
+      pending[stage] = (int)(((t + kStages) / kStages) & 1);
     }
   }
+  // after a timeout, wait (bounded) for this CTA's copies still in flight
+  if (threadIdx.x == 0 && aborted) {
+    const unsigned long long drain = gtimer() + kMbarBudgetNs;
+    for (int i = 0; i < kStages; ++i)
+      if (pending[i] >= 0)
+        while (!mbar_try_wait(&bars[i], (unsigned)pending[i]) && gtimer() < drain) {
+        }
+  }
   __syncthreads();
+  // reduce the TRG row groups in float64 (shared memory), write the partial
   double* red = reinterpret_cast<double*>(smem_raw);
   const int E = P * s;
   double* out = partial + (int64_t)blockIdx.x * E;
-  if (TRG == 1) {
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      const int p = pg + j * PT;
-      if (p < P)
-#pragma unroll
-        for (int k = 0; k < S; ++k)
-          if (EXACT || k < s) out[p * s + k] = (double)acc[j][k];
-    }
-    return;
-  }
   for (int rgi = 0; rgi < TRG; ++rgi) {
-    if (rg == rgi && pg < P) {
+    if (active && rg == rgi) {
 #pragma unroll
-      for (int k = 0; k < S; ++k)
-        if (EXACT || k < s)
-          red[pg * s + k] = (rgi == 0 ? 0.0 : red[pg * s + k]) + (double)acc[0][k];
+      for (int j = 0; j < NQPT; ++j) {
+        if (qoff[j] < 0) continue;
+        const int p0 = (qbase + j * qstride) * Q;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+#pragma unroll
+          for (int k = 0; k < S; ++k)
+            if (EXACT || k < s) {
+              const int e = (p0 + i) * s + k;
+              red[e] = (rgi == 0 ? 0.0 : red[e]) + (double)acc[j][i][k];
+            }
+      }
     }
     __syncthreads();
   }
@@ -279,32 +347,46 @@ static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V,
       reinterpret_cast<uintptr_t>(V) % 16 != 0 || reinterpret_cast<uintptr_t>(W) % 16 != 0)
     return false;
   // tile rows: largest power of two <= 64 with a stage of at most 48 KB
+  // (measured: 512-row tiles were slower at 128^3, s = 8)
   int TR = 64;
-  while (TR > 4 && (size_t)(nb + 1) * TR * s * es > 48 * 1024) TR >>= 1;
-  if ((size_t)(nb + 1) * TR * s * es > 48 * 1024) return false;
-  int PT = 32;
-  while (PT < P && PT < 256) PT <<= 1;
-  const int npt = (P + PT - 1) / PT;
+  while (TR > 4 && (size_t)(nb + 1) * (TR * s * es + kGramPad) > 48 * 1024) TR >>= 1;
+  if ((size_t)(nb + 1) * (TR * s * es + kGramPad) > 48 * 1024) return false;
   const int64_t want = std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, n_pad / 64));
   int64_t rpc = (n_pad + want - 1) / want;
-  rpc = ((rpc + 63) / 64) * 64;
+  rpc = std::max<int64_t>(TR, ((rpc + TR - 1) / TR) * TR);
+  if (n_pad % TR != 0) {           // keep whole tiles: fall back to 64-row tiles
+    TR = 64;
+    rpc = ((rpc + 63) / 64) * 64;
+  }
   const int nblk = (int)((n_pad + rpc - 1) / rpc);
   const int E = P * s;
   ensure_partial(ctx, sizeof(double) * (size_t)nblk * E);
-  const size_t stage_bytes = (size_t)(nb + 1) * TR * s * es;
-  const size_t smem = std::max(kStages * stage_bytes, (PT < 256 ? sizeof(double) * E : (size_t)0));
+  const size_t stage_bytes = (size_t)(nb + 1) * (TR * s * es + kGramPad);
+  bool ok = true;
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool EX = decltype(E_)::value;
+    constexpr int Q = EX ? (S >= 4 ? 4 : S) : 1;
+    const int NQ = P / Q;
+    const int npt = NQ <= 256 ? 1 : NQ <= 512 ? 2 : 4;
+    const int qs = (NQ + npt - 1) / npt;
+    const int TRG = std::max(1, std::min(16, 256 / qs));
+    const size_t red = sizeof(double) * (size_t)E;
+    const size_t smem = std::max(kStages * stage_bytes, red);
+    if (smem > 200 * 1024 || NQ > 1024) {
+      ok = false;
+      return;
+    }
     auto launch = [&](auto kern) {
       PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<nblk, 256, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, ctx->d_partial,
+      kern<<<nblk, 256, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, TRG, ctx->d_partial,
                                     ctx->d_flag);
     };
-    if (npt == 1) launch(k_gram_bulk<VT, S, EX, 1>);
-    else if (npt == 2) launch(k_gram_bulk<VT, S, EX, 2>);
-    else launch(k_gram_bulk<VT, S, EX, 4>);
+    if (npt == 1) launch(k_gram_bulk<VT, S, EX, Q, 1>);
+    else if (npt == 2) launch(k_gram_bulk<VT, S, EX, Q, 2>);
+    else launch(k_gram_bulk<VT, S, EX, Q, 4>);
   });
+  if (!ok) return false;
   check_launch("k_gram_bulk");
   k_gram_reduce<<<(E + 255) / 256, 256, 0, st>>>(nblk, E, ctx->d_partial, H);
   check_launch("k_gram_reduce");

@@ -128,9 +128,11 @@ void* inner_sell(pint_op op, int precision, bool jacobi, cudaStream_t st) {
 
 // --------------------------------------------------- fused coupled residual
 // R_r = d_r (Y_r A1^T) + ((K Y)_r - B_r) A2^T - B0_r  for every row r, with the
-// s x s products unrolled against the kernel-parameter copies of A1, A2
-// (zero coefficients skipped by warp-uniform branches).
-template <int S, bool EXACT>
+// s x s products unrolled against the kernel-parameter copies of A1, A2.
+// LO > 0: both matrices are lower banded with band LO (entries only at
+// 0 <= i - k <= LO, the shape of the time-stepping matrices), so only that band
+// is unrolled; LO == 0: dense, zero coefficients skipped by uniform branches.
+template <int S, bool EXACT, int LO>
 __global__ void __launch_bounds__(256)
 k_coupled(int64_t n, int s, const int64_t* __restrict__ sptr, const int* __restrict__ col,
           const double* __restrict__ val, const double* __restrict__ Md,
@@ -179,14 +181,34 @@ k_coupled(int64_t n, int s, const int64_t* __restrict__ sptr, const int* __restr
 #pragma unroll
     for (int k = 0; k < S; ++k) {
       if (!EXACT && k >= s) break;
+      if (LO > 0 && (k > i || i - k > LO)) continue;
       const double a1 = cp.A1[i * kMaxS + k];
       const double a2 = cp.A2[i * kMaxS + k];
-      if (a1 != 0.0) m1 = fma(a1, y[k], m1);
-      if (a2 != 0.0) m2 = fma(a2, ky[k], m2);
+      if (LO > 0) {
+        m1 = fma(a1, y[k], m1);
+        m2 = fma(a2, ky[k], m2);
+      } else {
+        if (a1 != 0.0) m1 = fma(a1, y[k], m1);
+        if (a2 != 0.0) m2 = fma(a2, ky[k], m2);
+      }
     }
     out[i] += fma(d, m1, m2);
   }
   store_row<S, EXACT>(R + row * s, s, out);
+}
+
+// Lower band width LO (1 or 2) when every non-zero of A1 and A2 sits at
+// 0 <= i - k <= LO, else 0 (dense).
+int coupling_band(const double* A1, const double* A2, int s) {
+  int lo = 0;
+  for (int i = 0; i < s; ++i)
+    for (int k = 0; k < s; ++k)
+      if (A1[i * kMaxS + k] != 0.0 || A2[i * kMaxS + k] != 0.0) {
+        if (k > i) return 0;
+        lo = std::max(lo, i - k);
+      }
+  if (lo > 2) return 0;
+  return std::max(lo, 1);
 }
 
 void launch_coupled(pint_op op, const double* Y, const double* B, const double* B0, double* R,
@@ -203,12 +225,17 @@ void launch_coupled(pint_op op, const double* Y, const double* B, const double* 
                op->nnz * 12.0 + 4.0 * (N + 1) + (op->Mdiag ? 8.0 * N : 0.0) +
                    8.0 * N * s * (2 + (B ? 1 : 0) + (B0 ? 1 : 0)),
                2.0 * op->nnz * s + 2.0 * N * nza, st);
+  const int lo = coupling_band(op->A1, op->A2, s);
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool E = decltype(E_)::value;
-    k_coupled<S, E><<<grid_for(op->n, 256), 256, 0, st>>>(op->n, s, op->sell.slice_ptr,
-                                                          op->sell.col, op->sellK, op->Mdiag, Y,
-                                                          B, B0, R, cp);
+    auto launch = [&](auto kern) {
+      kern<<<grid_for(op->n, 256), 256, 0, st>>>(op->n, s, op->sell.slice_ptr, op->sell.col,
+                                                 op->sellK, op->Mdiag, Y, B, B0, R, cp);
+    };
+    if (lo == 1) launch(k_coupled<S, E, 1>);
+    else if (lo == 2) launch(k_coupled<S, E, 2>);
+    else launch(k_coupled<S, E, 0>);
   });
   check_launch("k_coupled");
   op->ctx->launches += 1;

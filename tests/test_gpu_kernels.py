@@ -129,11 +129,13 @@ def test_ilu0_apply_matches_oracle(P, ctx, dims, s):
         P.pint_operator_destroy(op)
 
 
+@pytest.mark.parametrize("n", [4099, 65536])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("s,nb", [(1, 1), (1, 31), (3, 7), (4, 31), (8, 12), (16, 1), (16, 31)])
-def test_gram_update_colnorms(P, ctx, prec, s, nb):
+def test_gram_update_colnorms(P, ctx, prec, s, nb, n):
+    """n = 4099: plain-load Gram kernel; n = 65536 (a multiple of 64): the
+    bulk-copy (TMA) pipeline with several tiles per CTA."""
     import torch
-    n = 4099
     dt = torch.float64 if prec == "fp64" else torch.float32
     code = P.PINT_FP64 if prec == "fp64" else P.PINT_FP32
     V = synth.uniform(7, nb * n * s).reshape(nb, n, s)
