@@ -40,61 +40,134 @@ UNIT = "time-step*DOF/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (non-tensor and tensor alike)
 
 
+WORKLOADS = {
+    # name: (cells per direction, s, precond, precision, description)
+    "convdiff3d": (128, 8, "ilu0", "fp32",
+                   "3-D conv.-diffusion {n}^3, log-normal D (sigma 1), implicit Euler tau=1e-3, "
+                   "slab of s steps, block GMRES(30)+{pc}, tol 1e-10"),
+    "convdiff2d": (64, 4, "jacobi", "fp64",
+                   "2-D conv.-diffusion {n}^2, D=1, v=(1,0.5), implicit Euler tau=1e-3, slab of "
+                   "s steps, block GMRES(30)+{pc}, tol 1e-10"),
+    "diffreact": (512, 2, "ilu0", "fp32",
+                  "2-D diffusion-reaction {n}^2, SDIRK2 window of s=2 stages pipelined over 4 "
+                  "steps (Algorithm 1), Newton + block GMRES(30)+{pc}"),
+    "richards": (96, 8, "ilu0", "fp32",
+                 "3-D Richards {n}^3, van Genuchten alpha=1 n=2, K_S=exp(2g) correlated 8 "
+                 "cells, implicit Euler tau=1/96 window s=8 pipelined over 16 steps, Newton + "
+                 "block GMRES(30)+{pc}"),
+}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="pint", choices=["pint", "reference"])
-    p.add_argument("--n", type=int, default=128, help="cells per direction")
-    p.add_argument("--s", type=int, default=8, help="coupled time steps (block width)")
-    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
-    p.add_argument("--precond", default="ilu0", choices=["ilu0", "jacobi"])
+    p.add_argument("--workload", default="convdiff3d", choices=sorted(WORKLOADS))
+    p.add_argument("--n", type=int, default=None, help="cells per direction")
+    p.add_argument("--s", type=int, default=None, help="coupled time steps (block width)")
+    p.add_argument("--precision", default=None, choices=["fp64", "fp32", "bf16"])
+    p.add_argument("--precond", default=None, choices=["ilu0", "jacobi"])
     p.add_argument("--inner-tol", type=float, default=None)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--sweep", action="store_true",
                    help="also time one solve per (s, precision) for s=1..16")
     p.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
-    return p.parse_args()
+    a = p.parse_args()
+    dn, ds, dpc, dprec, _ = WORKLOADS[a.workload]
+    a.n = a.n or dn
+    a.s = a.s or ds
+    a.precond = a.precond or dpc
+    a.precision = a.precision or dprec
+    return a
+
+
+def linear(args):
+    return args.workload in ("convdiff3d", "convdiff2d")
 
 
 def inner_tol_for(args, s):
     if args.inner_tol is not None:
         return args.inner_tol
+    if not linear(args):
+        return 1e-5 if args.precision == "fp64" else 1e-4     # Sec. 4.2: 1e-5
     if s > 1:
         return 1e-2                       # Sec. 4.1: loose inner solves for s > 1
     return 1e-10 if args.precision == "fp64" else 1e-5
 
 
+def nl_stages(args):
+    return 8 if args.workload == "diffreact" else 16
+
+
 # ----------------------------------------------------------------- oracle
-def oracle_sample(n, s, reps=1):
-    """Time the oracle's slab solve on an n^3 sample of the workload (this
-    process runs with single-threaded BLAS)."""
+def oracle_sample(args, n, reps=1):
+    """Time the oracle on an n-cell-per-direction sample of the workload (this
+    process runs with single-threaded BLAS). Returns time steps, cells, times."""
     import numpy as np
     import synth
-    from oracle import coupling, fv, slab
-    w = synth.convdiff_3d(n, s)
-    D = synth.diffusion_field(w)
-    K = fv.convdiff_matrix(w.dims, D, w.velocity)
-    A, _, _ = coupling.implicit_euler()
-    A1, A2, _ = coupling.multistep_matrices(A, s, w.tau)
-    B = synth.rhs_block(w)
+    from oracle import coupling, fv, newton, slab
+    s = args.s
     times = []
+    if args.workload in ("convdiff3d", "convdiff2d"):
+        w = synth.convdiff_3d(n, s) if args.workload == "convdiff3d" else synth.convdiff_2d_64(s)
+        if args.workload == "convdiff2d" and n != 64:
+            w.dims = (n, n, 1)
+        D = synth.diffusion_field(w)
+        K = fv.convdiff_matrix(w.dims, D, w.velocity)
+        A, _, _ = coupling.implicit_euler()
+        A1, A2, _ = coupling.multistep_matrices(A, s, w.tau)
+        B = synth.rhs_block(w)
+        for _ in range(reps):
+            t = time.perf_counter()
+            slab.slab_solve(K, np.ones(w.n), A1, A2, B, None, tol=w.tol,
+                            inner_tol=1e-2 if s > 1 else 1e-10, precond=args.precond)
+            times.append(time.perf_counter() - t)
+        return {"n": w.n, "steps": s, "times": times}
+    if args.workload == "diffreact":
+        dims = (n, n, 1)
+        prob = newton.DiffReactProblem(dims)
+        A, _, c = coupling.sdirk2()
+        tau, y0, tol = 1e-2, np.full(n * n, 0.5), 1e-8
+        G = nl_stages(args)
+        for _ in range(reps):
+            t = time.perf_counter()
+            newton.pipelined_block_newton(prob, A, c, tau, y0, G, s, tol=tol, inner_tol=1e-5,
+                                          precond=args.precond)
+            times.append(time.perf_counter() - t)
+        return {"n": n * n, "steps": G // 2, "times": times}
+    dims = (n, n, n)
+    w = synth.richards_3d(n, s)
+    Ks = np.exp(2.0 * synth.correlated_field(w.seed_coef, dims[::-1], 8.0 * n / 96.0))
+    vg = fv.VanGenuchten(1.0, 2.0, 0.05, 0.4)
+    prob = newton.RichardsProblem(dims, Ks, vg, 1.0 / 16.0)
+    A, _, c = coupling.implicit_euler()
+    z, _ = fv.richards_cells(dims)
+    G = nl_stages(args)
     for _ in range(reps):
         t = time.perf_counter()
-        slab.slab_solve(K, np.ones(w.n), A1, A2, B, None, tol=w.tol,
-                        inner_tol=1e-2 if s > 1 else 1e-10, precond="ilu0")
+        newton.pipelined_block_newton(prob, A, c, 1.0 / 96.0, -z, G, s, tol=1e-8, inner_tol=1e-5,
+                                      precond=args.precond, max_step=1.0)
         times.append(time.perf_counter() - t)
-    return {"n": w.n, "s": s, "times": times}
+    return {"n": n ** 3, "steps": G, "times": times}
 
 
-def run_oracle_subprocess(n, s, reps):
+def oracle_sample_size(args):
+    return {"convdiff3d": 48, "convdiff2d": 64, "diffreact": 160, "richards": 20}[args.workload]
+
+
+def reference_sample_size(args):
+    return {"convdiff3d": 32, "convdiff2d": 64, "diffreact": 64, "richards": 12}[args.workload]
+
+
+def run_oracle_subprocess(args, n, reps):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n),
-                        "--s", str(s), "--steps", str(reps)],
-                       capture_output=True, text=True, env=env, timeout=1800)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n), "--s", str(args.s),
+           "--steps", str(reps), "--workload", args.workload, "--precond", args.precond]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
@@ -214,41 +287,167 @@ def roofline(fam, prof, hbm_peak, peak_kind, precision, workload):
             "launches": prof["launches"], "avg_launch_us": per_launch_s * 1e6}
 
 
+# ------------------------------------------------------------------ cases
+class LinearCase:
+    """One step = one slab solve of s coupled implicit-Euler steps."""
+
+    def __init__(self, P, ctx, args):
+        import numpy as np
+        import torch
+        import synth
+        self.P, self.ctx, self.args = P, ctx, args
+        s = args.s
+        w = synth.convdiff_3d(args.n, s) if args.workload == "convdiff3d" else \
+            synth.convdiff_2d_64(s)
+        if args.workload == "convdiff2d":
+            w.dims = (args.n, args.n, 1)
+        self.w = w
+        self.n, self.s, self.time_steps = w.n, s, s
+        D = synth.diffusion_field(w).ravel()
+        self.B = synth.rhs_block(w)
+        self.op = P.pint_fv_convdiff(ctx, *w.dims, D, w.velocity)
+        P.pint_set_coupling(ctx, self.op, (np.eye(s) - np.eye(s, k=-1)) / w.tau, np.eye(s))
+        o = P.pint_opts_default()
+        o.tol = w.tol
+        o.inner_tol = inner_tol_for(args, s)
+        o.precond = P.PINT_PC_ILU0 if args.precond == "ilu0" else P.PINT_PC_JACOBI
+        o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[args.precision]
+        self.o = o
+        self.Bd = torch.tensor(self.B, device="cuda", dtype=torch.float64)
+        self.Y = torch.zeros(self.n, s, device="cuda", dtype=torch.float64)
+        self.nnz = int(P.pint_operator_nnz(self.op))
+
+    def step(self):
+        self.Y.zero_()
+        return self.P.pint_solve_block(self.ctx, self.op, self.Bd, None, self.Y, self.o)
+
+    def host_buffers(self):
+        import torch
+        self.Bh = torch.tensor(self.B, dtype=torch.float64).pin_memory()
+        self.Yh = torch.empty(self.n, self.s, dtype=torch.float64).pin_memory()
+        return self.Bh.numel() * 8, self.Yh.numel() * 8
+
+    def e2e_step(self):
+        self.Bd.copy_(self.Bh, non_blocking=True)
+        st = self.step()
+        self.Yh.copy_(self.Y, non_blocking=True)
+        return st
+
+    def describe(self):
+        return {"cells": self.n, "s": self.s, "nnz": self.nnz, "tau": self.w.tau,
+                "tol": self.w.tol, "inner_tol": self.o.inner_tol, "restart": self.o.restart}
+
+    def close(self):
+        self.P.pint_operator_destroy(self.op)
+
+
+class PipelineCase:
+    """One step = Algorithm 1 over all stages of the run (pipelined windows)."""
+
+    def __init__(self, P, ctx, args):
+        import numpy as np
+        import torch
+        import synth
+        self.P, self.ctx, self.args = P, ctx, args
+        n, s = args.n, args.s
+        self.s = s
+        self.G = nl_stages(args)
+        VG = (1.0, 2.0, 0.05, 0.4, 1.0 / 16.0)
+        if args.workload == "diffreact":
+            dims = (n, n, 1)
+            self.prob = P.pint_problem_create(ctx, P.PINT_PROBLEM_DIFFREACT, *dims)
+            self.A = np.array([[1 - 2 ** -0.5, 0.0], [2 ** -0.5, 1 - 2 ** -0.5]])
+            self.c = np.array([1 - 2 ** -0.5, 1.0])
+            self.tau, self.tol = 1e-2, 1e-8
+            y0 = np.full(n * n, 0.5)
+            self.time_steps = self.G // 2
+            self.max_step = 0.0
+        else:
+            dims = (n, n, n)
+            w = synth.richards_3d(n, s)
+            Ks = np.exp(2.0 * synth.correlated_field(w.seed_coef, dims[::-1], 8.0 * n / 96.0))
+            self.Ksd = torch.tensor(Ks.ravel(), device="cuda", dtype=torch.float64)
+            self.prob = P.pint_problem_create(ctx, P.PINT_PROBLEM_RICHARDS, *dims, params=VG,
+                                              field=self.Ksd)
+            self.A, self.c = np.array([[1.0]]), np.array([1.0])
+            self.tau, self.tol = 1.0 / 96.0, 1e-8
+            z = (np.arange(n) + 0.5) / n
+            y0 = -np.broadcast_to(z[:, None, None], (n, n, n)).ravel().copy()
+            self.time_steps = self.G
+            self.max_step = 1.0
+        self.n = int(np.prod(dims))
+        self.y0 = y0
+        self.y0d = torch.tensor(y0, device="cuda", dtype=torch.float64)
+        self.out = torch.zeros(self.n, self.G, device="cuda", dtype=torch.float64)
+        o = P.pint_opts_default()
+        o.tol = self.tol
+        o.inner_tol = inner_tol_for(args, s)
+        o.max_outer = 60
+        o.max_step = self.max_step
+        o.precond = P.PINT_PC_ILU0 if args.precond == "ilu0" else P.PINT_PC_JACOBI
+        o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[args.precision]
+        self.o = o
+        self.nnz = int(P.pint_operator_nnz(P.pint_problem_operator(self.prob)))
+
+    def step(self):
+        return self.P.pint_pipeline_run(self.ctx, self.prob, self.A, self.c, self.tau, self.s,
+                                        self.y0d, self.G, self.out, self.o)
+
+    def host_buffers(self):
+        import torch
+        self.y0h = torch.tensor(self.y0, dtype=torch.float64).pin_memory()
+        self.outh = torch.empty(self.n, self.G, dtype=torch.float64).pin_memory()
+        return self.y0h.numel() * 8, self.outh.numel() * 8
+
+    def e2e_step(self):
+        self.y0d.copy_(self.y0h, non_blocking=True)
+        st = self.step()
+        self.outh.copy_(self.out, non_blocking=True)
+        return st
+
+    def describe(self):
+        return {"cells": self.n, "s": self.s, "stages": self.G, "nnz": self.nnz, "tau": self.tau,
+                "tol": self.tol, "inner_tol": self.o.inner_tol, "restart": self.o.restart,
+                "max_step": self.max_step}
+
+    def close(self):
+        self.P.pint_problem_destroy(self.prob)
+
+
 # ------------------------------------------------------------------ main
 def main():
     args = parse()
     if args.oracle_sample:
-        r = oracle_sample(args.oracle_sample, args.s, max(1, args.steps))
+        r = oracle_sample(args, args.oracle_sample, max(1, args.steps))
         print(json.dumps(r))
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    wl_name = f"convdiff3d_{args.n}^3_lognormal_s{args.s}_implicit-euler_{args.precond}"
+    desc = WORKLOADS[args.workload][4].format(n=args.n, pc=args.precond)
+    wl_name = f"{args.workload}_n{args.n}_s{args.s}_{args.precond}"
 
     if args.impl == "reference":
         if rank != 0:
             return
-        return reference_arm(args, wl_name, world)
+        return reference_arm(args, wl_name, desc, world)
 
     # CPU baseline first: a spawned single-threaded process, before any GPU call
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
+        samp = oracle_sample_size(args)
         try:
-            samp = 48
-            r = run_oracle_subprocess(samp, args.s, 1)
-            v = r["s"] * r["n"] / min(r["times"])
+            r = run_oracle_subprocess(args, samp, 1)
+            v = r["steps"] * r["n"] / min(r["times"])
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"one full oracle slab solve (FP64, ILU(0), same recipe) on "
-                             f"{samp}^3 = {r['n']} cells, s={args.s}: {min(r['times']):.1f} s"}
+                   "sample": f"one oracle run (FP64, {args.precond}, same recipe) on {r['n']} "
+                             f"cells, {r['steps']} time steps: {min(r['times']):.1f} s"}
         except Exception as e:          # report, do not hide
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {e}"[:300]}
 
-    import numpy as np
     import torch
-    import synth
     import paper_2504_02117_gb300 as P
 
     torch.cuda.set_device(local)
@@ -256,33 +455,16 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    w = synth.convdiff_3d(args.n, args.s)
-    D = synth.diffusion_field(w).ravel()
-    B = synth.rhs_block(w)
-    n, s = w.n, args.s
     ctx = P.pint_create(local)
-    op = P.pint_fv_convdiff(ctx, *w.dims, D, w.velocity)
-    A1 = (np.eye(s) - np.eye(s, k=-1)) / w.tau          # implicit Euler, Eq. multistep
-    A2 = np.eye(s)
-    P.pint_set_coupling(ctx, op, A1, A2)
-    prec = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[args.precision]
-    o = P.pint_opts_default()
-    o.tol = w.tol
-    o.inner_tol = inner_tol_for(args, s)
-    o.precond = P.PINT_PC_ILU0 if args.precond == "ilu0" else P.PINT_PC_JACOBI
-    o.precision = prec
-    Bd = torch.tensor(B, device="cuda", dtype=torch.float64)
-    Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
+    case = LinearCase(P, ctx, args) if linear(args) else PipelineCase(P, ctx, args)
     stream = torch.cuda.current_stream()
 
-    # setup (ILU factorisation happens on the first solve): untimed
+    # set-up (ILU factorisation happens on the first solve): untimed
     t0 = time.perf_counter()
-    st0 = P.pint_solve_block(ctx, op, Bd, None, Y, o)
-    setup_solve_s = time.perf_counter() - t0
+    st0 = case.step()
+    setup_s = time.perf_counter() - t0
     for _ in range(max(0, args.warmup - 1)):
-        Y.zero_()
-        P.pint_solve_block(ctx, op, Bd, None, Y, o)
+        case.step()
 
     def barrier():
         if dist is not None:
@@ -300,9 +482,7 @@ def main():
         barrier()
         ev0.record(stream)
         for _ in range(args.steps):
-            Y.zero_()
-            st = P.pint_solve_block(ctx, op, Bd, None, Y, o)
-            stats.append(st.as_dict(s))
+            stats.append(case.step().as_dict(case.s))
         ev1.record(stream)
         barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
@@ -313,26 +493,19 @@ def main():
         t = torch.tensor([elapsed_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms = float(t.item())
-    value = world * args.steps * s * n / (elapsed_ms / 1e3)
-
-    # correctness of the timed result: residual relative to F (device check)
-    relres = max(max(st["col_relres"]) for st in stats)
+    value = world * args.steps * case.time_steps * case.n / (elapsed_ms / 1e3)
     converged = all(st["status"] == 0 for st in stats)
 
     # ------------------------------------------------------------- e2e leg
     e2e = None
     if not args.no_e2e:
-        Bh = torch.tensor(B, dtype=torch.float64).pin_memory()
-        Yh = torch.empty(n, s, dtype=torch.float64).pin_memory()
+        bi, bo = case.host_buffers()
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            Bd.copy_(Bh, non_blocking=True)
-            Y.zero_()
-            P.pint_solve_block(ctx, op, Bd, None, Y, o)
-            Yh.copy_(Y, non_blocking=True)
+            case.e2e_step()
         e1.record(stream)
         barrier()
         e_ms = e0.elapsed_time(e1)
@@ -340,12 +513,12 @@ def main():
             t = torch.tensor([e_ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e_ms = float(t.item())
-        e2e = {"value": world * args.steps * s * n / (e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(Bh.numel() * 8), "d2h_bytes_per_step": int(Yh.numel() * 8),
+        e2e = {"value": world * args.steps * case.time_steps * case.n / (e_ms / 1e3),
+               "unit": UNIT, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
                "ms_per_step": e_ms / args.steps}
 
     if rank != 0:
-        P.pint_operator_destroy(op)
+        case.close()
         P.pint_destroy(ctx)
         if dist is not None:
             dist.destroy_process_group()
@@ -360,17 +533,18 @@ def main():
             kernels[k] = {"launches": f["launches"], "ms": round(f["ms"], 3),
                           "share": round(f["ms"] / total_prof, 4),
                           "GB/s": round(f["bytes"] / max(f["ms"], 1e-9) / 1e6, 1)}
+    cfg = {"workload": wl_name, "description": desc, "precision": args.precision,
+           "precond": args.precond, "time_steps_per_step": case.time_steps,
+           "parallelism": f"replicas x{world}",
+           "l2": "inputs larger than L2 (matrix + Krylov basis >> 129 MB), no flush"
+           if case.n >= 1 << 20 else "small workload: partly L2-resident, no flush"}
+    cfg.update(case.describe())
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else f"f64+{args.precision}",
-        "data": "synthetic",
-        "config": {"workload": wl_name, "cells": n, "s": s, "nnz": int(P.pint_operator_nnz(op)),
-                   "tau": w.tau, "tol": w.tol, "inner_tol": o.inner_tol, "restart": o.restart,
-                   "precision": args.precision, "precond": args.precond,
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (matrix and basis >> 129 MB), no flush"},
+        "data": "synthetic", "config": cfg,
         "roofline": roofline(dominant, fams[dominant], hbm_peak, peak_kind, args.precision,
                              wl_name),
         "spmm_roofline": roofline("spmm", fams["spmm"], hbm_peak, peak_kind, args.precision,
@@ -378,15 +552,15 @@ def main():
         "kernels": kernels,
         "iterations": {"outer": stats[-1]["outer_its"], "inner": stats[-1]["inner_its"],
                        "restarts": stats[-1]["restarts"]},
-        "converged": converged, "max_col_relres": relres,
-        "setup": {"first_solve_s": setup_solve_s, "ilu_setup_ms": st0.setup_ms},
+        "converged": converged, "max_col_relres": max(max(st["col_relres"]) for st in stats),
+        "setup": {"first_step_s": setup_s, "precond_setup_ms": st0.setup_ms},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(), "impl": "pint",
     }
-    if args.sweep:
-        out["sweep"] = sweep(P, ctx, args, w)
+    if args.sweep and linear(args):
+        out["sweep"] = sweep(P, ctx, args, case.w)
     print(json.dumps(out), flush=True)
-    P.pint_operator_destroy(op)
+    case.close()
     P.pint_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
@@ -403,6 +577,7 @@ def sweep(P, ctx, args, w0):
     for prec_name in ("fp64", "fp32"):
         for s in (1, 2, 4, 8, 16):
             w = synth.convdiff_3d(args.n, s)
+            w.dims = w0.dims
             op = P.pint_fv_convdiff(ctx, *w.dims, D, w.velocity)
             P.pint_set_coupling(ctx, op, (np.eye(s) - np.eye(s, k=-1)) / w.tau, np.eye(s))
             o = P.pint_opts_default()
@@ -433,21 +608,23 @@ def sweep(P, ctx, args, w0):
     return res
 
 
-def reference_arm(args, wl_name, world):
+def reference_arm(args, wl_name, desc, world):
     """The oracle as it stands, timed on this host's cores, on a bounded
     sample of the workload per step."""
-    samp = 32
-    r = run_oracle_subprocess(samp, args.s, args.warmup + args.steps)
+    samp = reference_sample_size(args)
+    r = run_oracle_subprocess(args, samp, args.warmup + args.steps)
     times = r["times"][args.warmup:]
     per = statistics.mean(times)
-    v = r["s"] * r["n"] / per
+    v = r["steps"] * r["n"] / per
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": wl_name, "sample_cells": r["n"], "s": args.s},
+           "config": {"workload": wl_name, "description": desc, "sample_cells": r["n"],
+                      "s": args.s},
            "impl": "reference",
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"oracle slab solve on {samp}^3 cells per step"},
+                            "sample": f"oracle run on {r['n']} cells ({r['steps']} time steps) "
+                                      f"per step"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -58,6 +58,18 @@ struct IluState {
     unsigned* tflag_b = nullptr;
     unsigned tepoch_f = 0, tepoch_b = 0;
   } ts[2];
+  // row-of-tiles sweeps (stencil operators): tile shape, row order, flags,
+  // stencil-format factors L4 / U4 ([n][4], float64 and float32)
+  bool rows = false;
+  int RX = 0, RY = 0, RZ = 0, RNTX = 0, RNTY = 0, RNTZ = 0, rntiles = 0, nrows = 0;
+  int* row_order = nullptr;
+  unsigned* rflag_f = nullptr;
+  unsigned* rflag_b = nullptr;
+  unsigned repoch_f = 0, repoch_b = 0;
+  double* L4d = nullptr;
+  double* U4d = nullptr;
+  float* L4f = nullptr;
+  float* U4f = nullptr;
 };
 
 // -------------------------------------------------------------- helpers
@@ -363,6 +375,351 @@ k_ilu_tile(TileGeom g, int s_rt, const int* __restrict__ rowptr, const int* __re
   }
 }
 
+// Pencil variant of the tiled sweep (s <= 8): thread (c, lj, lk) owns the
+// x-line of column c at (lj, lk) of the tile and keeps its TX values, their
+// coefficients and its halo values in registers. Step t of the local
+// wavefront handles cell li = t - lj - lk (forward; mirrored backward): the
+// x-neighbour is in the thread's own registers, the y- and z-neighbours are
+// read from the shared tile written one step earlier. Same operands, same
+// order of operations per cell as the CSR sweep.
+template <typename VT, bool FWD, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(512, 1)
+k_ilu_pencil(TileGeom g, int s, const int* __restrict__ rowptr, const int* __restrict__ diagpos,
+             const VT* __restrict__ F, const VT* X, VT* Z, const int* __restrict__ tile_order,
+             unsigned* tflags, unsigned epoch, int* ticket, int* err) {
+  constexpr int NSTEP = TX + TY + TZ - 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  VT* Ys = reinterpret_cast<VT*>(smem_raw);     // [lk][lj][li][c]
+  __shared__ int tile_sh;
+  const int c = threadIdx.x % s;
+  const int q = threadIdx.x / s;
+  const int lj = q % TY, lk = q / TY;
+  const unsigned long long deadline = globaltimer() + kWaitBudgetNs;
+  const int64_t sxy = (int64_t)g.nx * g.ny;
+  auto sidx = [&](int li_, int lj_, int lk_) { return ((lk_ * TY + lj_) * TX + li_) * s + c; };
+  bool ok = true;
+  while (true) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(ticket, 1);
+      tile_sh = t < g.ntiles ? tile_order[FWD ? t : g.ntiles - 1 - t] : -1;
+    }
+    __syncthreads();
+    const int tile = tile_sh;
+    if (tile < 0) return;
+    const int I = tile % g.NTX, J = (tile / g.NTX) % g.NTY, K = tile / (g.NTX * g.NTY);
+    const int x0 = I * TX, y0 = J * TY, z0 = K * TZ;
+    const int ex = min(TX, g.nx - x0), ey = min(TY, g.ny - y0), ez = min(TZ, g.nz - z0);
+    const bool mine = lj < ey && lk < ez;
+    const int gj = y0 + lj, gk = z0 + lk;
+    const int64_t lbase = x0 + (int64_t)g.nx * gj + sxy * gk;   // row of li = 0
+    VT y[TX], c0[TX], c1[TX], c2[TX], cd[TX];
+    // prefetch the line's coefficients and right-hand side (before waiting)
+#pragma unroll
+    for (int li = 0; li < TX; ++li) {
+      y[li] = c0[li] = c1[li] = c2[li] = VT(0);
+      cd[li] = VT(1);
+      if (mine && li < ex) {
+        const int64_t r = lbase + li;
+        const int gi = x0 + li;
+        const int d = diagpos[r];
+        if (FWD) {
+          int p = rowptr[r];
+          if (gk > 0) c0[li] = F[p++];      // -z
+          if (gj > 0) c1[li] = F[p++];      // -y
+          if (gi > 0) c2[li] = F[p++];      // -x
+          y[li] = X[r * s + c];
+        } else {
+          int p = d + 1;
+          if (gi + 1 < g.nx) c0[li] = F[p++];   // +x
+          if (gj + 1 < g.ny) c1[li] = F[p++];   // +y
+          if (gk + 1 < g.nz) c2[li] = F[p++];   // +z
+          cd[li] = F[d];
+          y[li] = __ldcg(Z + r * s + c);
+        }
+      }
+    }
+    if (threadIdx.x < 3 && ok) {
+      int nt = -1;
+      if (FWD) {
+        if (threadIdx.x == 0 && I > 0) nt = tile - 1;
+        if (threadIdx.x == 1 && J > 0) nt = tile - g.NTX;
+        if (threadIdx.x == 2 && K > 0) nt = tile - g.NTX * g.NTY;
+      } else {
+        if (threadIdx.x == 0 && x0 + ex < g.nx) nt = tile + 1;
+        if (threadIdx.x == 1 && y0 + ey < g.ny) nt = tile + g.NTX;
+        if (threadIdx.x == 2 && z0 + ez < g.nz) nt = tile + g.NTX * g.NTY;
+      }
+      if (nt >= 0) ok = wait_ready(tflags + nt, epoch, err, deadline);
+    }
+    __syncthreads();
+    // halo values from the upstream tiles (zero where the grid ends)
+    VT hx = VT(0), hy[TX], hz[TX];
+#pragma unroll
+    for (int li = 0; li < TX; ++li) hy[li] = hz[li] = VT(0);
+    if (mine) {
+      if (FWD) {
+        if (x0 > 0) hx = __ldcg(Z + (lbase - 1) * s + c);
+        if (lj == 0 && gj > 0) {
+#pragma unroll
+          for (int li = 0; li < TX; ++li)
+            if (li < ex) hy[li] = __ldcg(Z + (lbase + li - g.nx) * s + c);
+        }
+        if (lk == 0 && gk > 0) {
+#pragma unroll
+          for (int li = 0; li < TX; ++li)
+            if (li < ex) hz[li] = __ldcg(Z + (lbase + li - sxy) * s + c);
+        }
+      } else {
+        if (x0 + ex < g.nx) hx = __ldcg(Z + (lbase + ex) * s + c);
+        if (lj == ey - 1 && gj + 1 < g.ny) {
+#pragma unroll
+          for (int li = 0; li < TX; ++li)
+            if (li < ex) hy[li] = __ldcg(Z + (lbase + li + g.nx) * s + c);
+        }
+        if (lk == ez - 1 && gk + 1 < g.nz) {
+#pragma unroll
+          for (int li = 0; li < TX; ++li)
+            if (li < ex) hz[li] = __ldcg(Z + (lbase + li + sxy) * s + c);
+        }
+      }
+    }
+    // local wavefront
+    for (int t = 0; t < NSTEP; ++t) {
+      if (mine) {
+        // forward: li = t - lj - lk ; backward: mirrored coordinates
+        const int d = FWD ? t - lj - lk : t - (ey - 1 - lj) - (ez - 1 - lk);
+#pragma unroll
+        for (int li = 0; li < TX; ++li) {
+          const int want = FWD ? li : ex - 1 - li;
+          if (d == want && li < ex) {
+            VT acc = y[li];
+            if (FWD) {
+              const VT vz = lk > 0 ? Ys[sidx(li, lj, lk - 1)] : hz[li];
+              const VT vy = lj > 0 ? Ys[sidx(li, lj - 1, lk)] : hy[li];
+              const VT vx = li > 0 ? y[li > 0 ? li - 1 : 0] : hx;
+              acc -= c0[li] * vz;
+              acc -= c1[li] * vy;
+              acc -= c2[li] * vx;
+            } else {
+              const VT vx = li + 1 < ex ? y[li + 1 < TX ? li + 1 : li] : hx;
+              const VT vy = lj + 1 < ey ? Ys[sidx(li, lj + 1, lk)] : hy[li];
+              const VT vz = lk + 1 < ez ? Ys[sidx(li, lj, lk + 1)] : hz[li];
+              acc -= c0[li] * vx;
+              acc -= c1[li] * vy;
+              acc -= c2[li] * vz;
+              acc /= cd[li];
+            }
+            y[li] = acc;
+            Ys[sidx(li, lj, lk)] = acc;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (mine) {
+#pragma unroll
+      for (int li = 0; li < TX; ++li)
+        if (li < ex) Z[(lbase + li) * s + c] = y[li];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(tflags + tile, epoch);
+  }
+}
+
+// Stencil-format copy of the factors: per row four coefficients,
+// FWD (L): (-z, -y, -x, 0); BWD (U): (+x, +y, +z, diag); absent neighbours 0.
+template <typename VT>
+__global__ void k_ilu_stencil_coefs(TileGeom g, int64_t n, const int* __restrict__ rowptr,
+                                    const int* __restrict__ diagpos, const double* __restrict__ F,
+                                    VT* __restrict__ L4, VT* __restrict__ U4) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int i = (int)(r % g.nx), j = (int)((r / g.nx) % g.ny), k = (int)(r / ((int64_t)g.nx * g.ny));
+  double l[3] = {0, 0, 0}, u[4] = {0, 0, 0, 0};
+  int p = rowptr[r];
+  if (k > 0) l[0] = F[p++];
+  if (j > 0) l[1] = F[p++];
+  if (i > 0) l[2] = F[p++];
+  const int d = diagpos[r];
+  p = d + 1;
+  if (i + 1 < g.nx) u[0] = F[p++];
+  if (j + 1 < g.ny) u[1] = F[p++];
+  if (k + 1 < g.nz) u[2] = F[p++];
+  u[3] = F[d];
+  for (int q = 0; q < 3; ++q) L4[4 * r + q] = (VT)l[q];
+  L4[4 * r + 3] = VT(0);
+  for (int q = 0; q < 4; ++q) U4[4 * r + q] = (VT)u[q];
+}
+
+// Row-of-tiles sweep: a CTA takes one x-row of tiles (fixed J, K; tickets
+// in order of J + K, so it only waits for rows with lower tickets) and
+// sweeps its tiles along x. The x-neighbour of a tile's first cells is the
+// last cell of the previous tile of the same row, carried in a register; the
+// y- and z-neighbours come from the rows (J-1, K) and (J, K-1) through one
+// flag per tile (bounded waits). Inside a tile, thread (c, lj, lk) owns the
+// x-pencil of column c and step t of the local wavefront handles its cell
+// li = t - lj - lk (mirrored backward); values and coefficients are staged
+// in shared memory. Same operands and order of operations per cell as the
+// CSR sweep.
+template <typename VT, bool FWD, int TX, int TY, int TZ, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
+           const int* __restrict__ row_order, int nrows, unsigned* tflags, unsigned epoch,
+           int* ticket, int* err) {
+  constexpr int NSTEP = TX + TY + TZ - 2;
+  constexpr int TR = TX * TY * TZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  VT* Ys = reinterpret_cast<VT*>(smem_raw);        // [lk][lj][li][c]
+  VT* Cs = Ys + (size_t)TR * s;                     // [lk][lj][li][4]
+  VT* Hy = Cs + (size_t)TR * 4;                     // [lk][li][c]
+  VT* Hz = Hy + (size_t)TZ * TX * s;                // [lj][li][c]
+  __shared__ int row_sh;
+  const int c = threadIdx.x % s;
+  const int q = threadIdx.x / s;
+  const int lj = q % TY, lk = q / TY;
+  const unsigned long long deadline = globaltimer() + kWaitBudgetNs;
+  const int64_t sxy = (int64_t)g.nx * g.ny;
+  const int NTZ = (g.nz + TZ - 1) / TZ;
+  bool ok = true;
+  // this pencil's right-hand side and coefficients for one tile, loaded into
+  // registers with all loads in flight together (unrolled, guarded)
+  VT xv[TX], cv[TX][4];
+  auto fetch = [&](int x0, int ex, int64_t lbase, bool mine) {
+#pragma unroll
+    for (int li = 0; li < TX; ++li) {
+      if (mine && li < ex) {
+        const int64_t r = lbase + li;
+        xv[li] = FWD ? X[r * s + c] : __ldcg(Z + r * s + c);
+        if (c == 0) {
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) cv[li][k4] = C4[4 * r + k4];
+        }
+      }
+    }
+  };
+  while (true) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(ticket, 1);
+      row_sh = t < nrows ? row_order[FWD ? t : nrows - 1 - t] : -1;
+    }
+    __syncthreads();
+    const int row = row_sh;
+    if (row < 0) return;
+    const int J = row % g.NTY, K = row / g.NTY;
+    const int y0 = J * TY, z0 = K * TZ;
+    const int ey = min(TY, g.ny - y0), ez = min(TZ, g.nz - z0);
+    const bool mine = lj < ey && lk < ez;
+    const int gj = y0 + lj, gk = z0 + lk;
+    const int cellb = (lk * TY + lj) * TX;
+    VT hx = VT(0);                                   // carried x-neighbour
+    {
+      const int I = FWD ? 0 : g.NTX - 1;
+      const int x0 = I * TX;
+      fetch(x0, min(TX, g.nx - x0), x0 + (int64_t)g.nx * gj + sxy * gk, mine);
+    }
+    for (int it = 0; it < g.NTX; ++it) {
+      const int I = FWD ? it : g.NTX - 1 - it;
+      const int x0 = I * TX;
+      const int ex = min(TX, g.nx - x0);
+      const int tile = I + g.NTX * (J + g.NTY * K);
+      const int64_t lbase = x0 + (int64_t)g.nx * gj + sxy * gk;   // row of li = 0
+      // stage the prefetched pencil into shared memory
+      if (mine) {
+#pragma unroll
+        for (int li = 0; li < TX; ++li) {
+          if (li < ex) {
+            Ys[(cellb + li) * s + c] = xv[li];
+            if (c == 0) {
+#pragma unroll
+              for (int k4 = 0; k4 < 4; ++k4) Cs[(cellb + li) * 4 + k4] = cv[li][k4];
+            }
+          }
+        }
+      }
+      // upstream rows: FWD (J-1, K), (J, K-1); BWD (J+1, K), (J, K+1)
+      if (threadIdx.x < 2 && ok) {
+        int nt = -1;
+        if (FWD) {
+          if (threadIdx.x == 0 && J > 0) nt = tile - g.NTX;
+          if (threadIdx.x == 1 && K > 0) nt = tile - g.NTX * g.NTY;
+        } else {
+          if (threadIdx.x == 0 && J + 1 < g.NTY) nt = tile + g.NTX;
+          if (threadIdx.x == 1 && K + 1 < NTZ) nt = tile + g.NTX * g.NTY;
+        }
+        if (nt >= 0) ok = wait_ready(tflags + nt, epoch, err, deadline);
+      }
+      __syncthreads();
+      // faces of the y / z upstream rows (zero where the grid ends)
+      if (mine) {
+        const bool ybnd = FWD ? lj == 0 : lj == ey - 1;
+        const bool zbnd = FWD ? lk == 0 : lk == ez - 1;
+        const int64_t yoff = FWD ? -(int64_t)g.nx : (int64_t)g.nx;
+        const int64_t zoff = FWD ? -sxy : sxy;
+        const bool yin = FWD ? gj > 0 : gj + 1 < g.ny;
+        const bool zin = FWD ? gk > 0 : gk + 1 < g.nz;
+        VT hyv[TX], hzv[TX];
+#pragma unroll
+        for (int li = 0; li < TX; ++li) {
+          hyv[li] = (ybnd && yin && li < ex) ? __ldcg(Z + (lbase + li + yoff) * s + c) : VT(0);
+          hzv[li] = (zbnd && zin && li < ex) ? __ldcg(Z + (lbase + li + zoff) * s + c) : VT(0);
+        }
+#pragma unroll
+        for (int li = 0; li < TX; ++li) {
+          if (ybnd) Hy[(lk * TX + li) * s + c] = hyv[li];
+          if (zbnd) Hz[(lj * TX + li) * s + c] = hzv[li];
+        }
+      }
+      __syncthreads();
+      for (int t = 0; t < NSTEP; ++t) {
+        const int li = FWD ? t - lj - lk : (ex - 1) - (t - (ey - 1 - lj) - (ez - 1 - lk));
+        if (mine && li >= 0 && li < ex) {
+          const int cell = cellb + li;
+          VT acc = Ys[cell * s + c];
+          const VT* cf = Cs + cell * 4;
+          if (FWD) {
+            const VT vz = lk > 0 ? Ys[(cell - TY * TX) * s + c] : Hz[(lj * TX + li) * s + c];
+            const VT vy = lj > 0 ? Ys[(cell - TX) * s + c] : Hy[(lk * TX + li) * s + c];
+            const VT vx = li > 0 ? Ys[(cell - 1) * s + c] : hx;
+            acc -= cf[0] * vz;
+            acc -= cf[1] * vy;
+            acc -= cf[2] * vx;
+          } else {
+            const VT vx = li + 1 < ex ? Ys[(cell + 1) * s + c] : hx;
+            const VT vy = lj + 1 < ey ? Ys[(cell + TX) * s + c] : Hy[(lk * TX + li) * s + c];
+            const VT vz = lk + 1 < ez ? Ys[(cell + TY * TX) * s + c] : Hz[(lj * TX + li) * s + c];
+            acc -= cf[0] * vx;
+            acc -= cf[1] * vy;
+            acc -= cf[2] * vz;
+            acc /= cf[3];
+          }
+          Ys[cell * s + c] = acc;
+        }
+        __syncthreads();
+      }
+      if (mine) {
+        hx = Ys[(cellb + (FWD ? ex - 1 : 0)) * s + c];
+#pragma unroll
+        for (int li = 0; li < TX; ++li)
+          if (li < ex) Z[(lbase + li) * s + c] = Ys[(cellb + li) * s + c];
+      }
+      // prefetch the next tile of the row while this one is published
+      if (it + 1 < g.NTX) {
+        const int In = FWD ? it + 1 : g.NTX - 2 - it;
+        const int xn = In * TX;
+        fetch(xn, min(TX, g.nx - xn), xn + (int64_t)g.nx * gj + sxy * gk, mine);
+      }
+      // publish: every store of the CTA happens-before thread 0's fence and
+      // release through the barrier
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(tflags + tile, epoch);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------ host side
 static void levels(const pint_op op, bool forward, std::vector<int>& order,
                    std::vector<int>& lvlptr) {
@@ -484,6 +841,31 @@ static void ensure_state(pint_op op) {
       build(S->ts[0], 64, 1, 1);
     }
     S->tiled = true;
+    // row-of-tiles structures
+    S->RX = nz > 1 ? 8 : (ny > 1 ? 16 : 64);
+    S->RY = nz > 1 ? 8 : (ny > 1 ? 8 : 1);
+    S->RZ = nz > 1 ? 8 : 1;
+    S->RNTX = (nx + S->RX - 1) / S->RX;
+    S->RNTY = (ny + S->RY - 1) / S->RY;
+    S->RNTZ = (nz + S->RZ - 1) / S->RZ;
+    S->rntiles = S->RNTX * S->RNTY * S->RNTZ;
+    S->nrows = S->RNTY * S->RNTZ;
+    std::vector<int> ro(S->nrows);
+    for (int r = 0; r < S->nrows; ++r) ro[r] = r;
+    std::stable_sort(ro.begin(), ro.end(), [&](int a, int b) {
+      return a % S->RNTY + a / S->RNTY < b % S->RNTY + b / S->RNTY;
+    });
+    S->row_order = dalloc_n<int>(ctx, S->nrows);
+    S->rflag_f = dalloc_n<unsigned>(ctx, S->rntiles);
+    S->rflag_b = dalloc_n<unsigned>(ctx, S->rntiles);
+    S->L4d = dalloc_n<double>(ctx, 4 * op->n);
+    S->U4d = dalloc_n<double>(ctx, 4 * op->n);
+    S->L4f = dalloc_n<float>(ctx, 4 * op->n);
+    S->U4f = dalloc_n<float>(ctx, 4 * op->n);
+    PINT_CUDA(cudaMemcpy(S->row_order, ro.data(), sizeof(int) * S->nrows, cudaMemcpyHostToDevice));
+    PINT_CUDA(cudaMemset(S->rflag_f, 0, sizeof(unsigned) * S->rntiles));
+    PINT_CUDA(cudaMemset(S->rflag_b, 0, sizeof(unsigned) * S->rntiles));
+    S->rows = true;
   }
 }
 
@@ -506,6 +888,15 @@ void ilu_destroy(pint_op op) {
   dfree(c, S->err, 2 * sizeof(int));
   dfree(c, S->d_order_f, sizeof(int) * op->n);
   dfree(c, S->d_order_b, sizeof(int) * op->n);
+  if (S->rows) {
+    dfree(c, S->row_order, sizeof(int) * S->nrows);
+    dfree(c, S->rflag_f, sizeof(unsigned) * S->rntiles);
+    dfree(c, S->rflag_b, sizeof(unsigned) * S->rntiles);
+    dfree(c, S->L4d, sizeof(double) * 4 * op->n);
+    dfree(c, S->U4d, sizeof(double) * 4 * op->n);
+    dfree(c, S->L4f, sizeof(float) * 4 * op->n);
+    dfree(c, S->U4f, sizeof(float) * 4 * op->n);
+  }
   for (auto& T : S->ts)
     if (T.valid) {
       dfree(c, T.tile_order, sizeof(int) * T.ntiles);
@@ -545,6 +936,15 @@ void ilu_setup(pint_op op, cudaStream_t st) {
   k_cast_f32<<<grid_for(op->nnz, 256), 256, 0, st>>>(op->nnz, S->F64, S->F32);
   check_launch("k_cast_f32");
   op->ctx->launches += 2;
+  if (S->rows) {
+    TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, 0, 0, 0};
+    k_ilu_stencil_coefs<double><<<grid_for(op->n, 256), 256, 0, st>>>(
+        g, op->n, op->rowptr, op->diagpos, S->F64, S->L4d, S->U4d);
+    k_ilu_stencil_coefs<float><<<grid_for(op->n, 256), 256, 0, st>>>(
+        g, op->n, op->rowptr, op->diagpos, S->F64, S->L4f, S->U4f);
+    check_launch("k_ilu_stencil_coefs");
+    op->ctx->launches += 2;
+  }
   PINT_CUDA(cudaStreamSynchronize(st));
   ilu_check(op);
   S->factored = true;
@@ -586,6 +986,28 @@ static void tile_pair_s(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_
   }
 }
 
+template <typename VT, int TX, int TY, int TZ>
+static void pencil_pair(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st, unsigned ef,
+                        unsigned eb, IluState::TileSet& T) {
+  IluState* Sx = op->ilu;
+  const int s = op->s;
+  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, T.NTX, T.NTY, T.ntiles};
+  const int threads = TY * TZ * s;
+  const size_t smem = sizeof(VT) * (size_t)TX * TY * TZ * s;
+  auto launch = [&](auto kern, const VT* x, unsigned* flags, unsigned ep, int* ticket) {
+    PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    const int grid = std::max(1, std::min(T.ntiles, std::max(1, per_sm) * op->ctx->num_sms));
+    kern<<<grid, threads, smem, st>>>(g, s, op->rowptr, op->diagpos, F, x, Z, T.tile_order, flags,
+                                      ep, ticket, Sx->err);
+  };
+  launch(k_ilu_pencil<VT, true, TX, TY, TZ>, X, T.tflag_f, ef, Sx->ticket);
+  check_launch("k_ilu_pencil<fwd>");
+  launch(k_ilu_pencil<VT, false, TX, TY, TZ>, Z, T.tflag_b, eb, Sx->ticket + 1);
+  check_launch("k_ilu_pencil<bwd>");
+}
+
 template <typename VT>
 static void apply_tiled(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st) {
   IluState* S = op->ilu;
@@ -600,15 +1022,63 @@ static void apply_tiled(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_
                    4.0 * sizeof(VT) * op->n * op->s,
                2.0 * op->nnz * op->s, st);
   if (big) tile_pair_s<VT, 16, 16, 8>(op, F, X, Z, st, ef, eb, T);
+  else if (T.TZ == 8 && op->s <= 8) pencil_pair<VT, 8, 8, 8>(op, F, X, Z, st, ef, eb, T);
+  else if (T.TY == 16 && op->s <= 8 && sizeof(VT) == 4)   // float64 16-wide lines spill
+    pencil_pair<VT, 16, 16, 1>(op, F, X, Z, st, ef, eb, T);
   else if (T.TZ == 8) tile_pair_s<VT, 8, 8, 8>(op, F, X, Z, st, ef, eb, T);
   else if (T.TY == 16) tile_pair_s<VT, 16, 16, 1>(op, F, X, Z, st, ef, eb, T);
   else tile_pair_s<VT, 64, 1, 1>(op, F, X, Z, st, ef, eb, T);
   op->ctx->launches += 2;
 }
 
+template <typename VT, int TX, int TY, int TZ, int MAXT>
+static void rows_pair(pint_op op, const VT* L4, const VT* U4, const VT* X, VT* Z,
+                      cudaStream_t st) {
+  IluState* S = op->ilu;
+  const int s = op->s;
+  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, S->RNTX, S->RNTY, S->rntiles};
+  const int threads = TY * TZ * s;
+  constexpr int TR = TX * TY * TZ;
+  const size_t smem = sizeof(VT) * ((size_t)TR * s + (size_t)TR * 4 + (size_t)TZ * TX * s +
+                                    (size_t)TY * TX * s);
+  const unsigned ef = next_epoch(op, S->repoch_f, S->rflag_f, st);
+  const unsigned eb = next_epoch(op, S->repoch_b, S->rflag_b, st);
+  PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
+  ProfScope ps(op->ctx, PF_ILU,
+               8.0 * sizeof(VT) * op->n + 4.0 * sizeof(VT) * op->n * s, 2.0 * op->nnz * s, st);
+  auto launch = [&](auto kern, const VT* C, const VT* x, unsigned* flags, unsigned ep, int* tk) {
+    PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    const int grid = std::max(1, std::min(S->nrows, std::max(1, per_sm) * op->ctx->num_sms));
+    kern<<<grid, threads, smem, st>>>(g, s, C, x, Z, S->row_order, S->nrows, flags, ep, tk,
+                                      S->err);
+  };
+  launch(k_ilu_rows<VT, true, TX, TY, TZ, MAXT>, L4, X, S->rflag_f, ef, S->ticket);
+  check_launch("k_ilu_rows<fwd>");
+  launch(k_ilu_rows<VT, false, TX, TY, TZ, MAXT>, U4, Z, S->rflag_b, eb, S->ticket + 1);
+  check_launch("k_ilu_rows<bwd>");
+  op->ctx->launches += 2;
+}
+
+template <typename VT>
+static void apply_rows(pint_op op, const VT* L4, const VT* U4, const VT* X, VT* Z,
+                       cudaStream_t st) {
+  IluState* S = op->ilu;
+  if (S->RZ == 8 && op->s <= 8) rows_pair<VT, 8, 8, 8, 512>(op, L4, U4, X, Z, st);
+  else if (S->RZ == 8) rows_pair<VT, 8, 8, 8, 1024>(op, L4, U4, X, Z, st);
+  else if (S->RY == 8) rows_pair<VT, 16, 8, 1, 128>(op, L4, U4, X, Z, st);
+  else rows_pair<VT, 64, 1, 1, 16>(op, L4, U4, X, Z, st);
+}
+
 template <typename VT>
 static void apply_t(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st) {
   IluState* S = op->ilu;
+  if (S->rows && op->s * S->RY * S->RZ <= 1024) {
+    if constexpr (sizeof(VT) == 8) apply_rows<double>(op, S->L4d, S->U4d, X, Z, st);
+    else apply_rows<float>(op, S->L4f, S->U4f, X, Z, st);
+    return;
+  }
   if (S->tiled) {
     apply_tiled<VT>(op, F, X, Z, st);
     return;

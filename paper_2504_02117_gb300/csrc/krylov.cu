@@ -179,8 +179,8 @@ __device__ __forceinline__ void lds_q(const VT* p, VT (&v)[Q]) {
   }
 }
 
-template <typename VT, int S, bool EXACT, int Q, int NQPT>
-__global__ void __launch_bounds__(256)
+template <typename VT, int S, bool EXACT, int Q, int NQPT, int NT>
+__global__ void __launch_bounds__(NT)
 k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstride,
             const VT* __restrict__ W, int64_t rows_per_cta, int TR, int TRG,
             double* __restrict__ partial, int* __restrict__ err) {
@@ -201,12 +201,17 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // Copies of one stage are issued by threads 0..nb (one block each); thread
+  // 0 also posts the expected byte count. A copy may complete before the
+  // expect_tx is posted: the phase still needs thread 0's arrival.
   auto issue = [&](int stage, int tile) {
     unsigned char* dst = smem_raw + (size_t)stage * stage_bytes;
-    mbar_expect_tx(&bars[stage], blk_bytes * (nb + 1));
-    const int64_t row = r0 + (int64_t)tile * TR;
-    for (int b = 0; b <= nb; ++b) {
+    if (threadIdx.x == 0) mbar_expect_tx(&bars[stage], blk_bytes * (nb + 1));
+    const int b = threadIdx.x;
+    if (b <= nb) {
+      const int64_t row = r0 + (int64_t)tile * TR;
       const VT* src = (b < nb ? V + (int64_t)b * bstride : W) + row * s;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_g2s(dst + (size_t)b * blk_pitch, src, blk_bytes, &bars[stage]);
     }
   };
@@ -214,11 +219,10 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
   // complete by thread 0 (-1: none); used to drain copies after a timeout
   int pending[kStages];
   for (int i = 0; i < kStages; ++i) pending[i] = -1;
-  if (threadIdx.x == 0)
-    for (int t = 0; t < kStages && t < ntiles; ++t) {
-      issue(t, t);
-      pending[t] = 0;
-    }
+  for (int t = 0; t < kStages && t < ntiles; ++t) {
+    issue(t, t);
+    pending[t] = 0;
+  }
   // this thread: quads q = qbase + j*QSTRIDE (j < NQPT), rows rr = rg + m*TRG
   const int nthr_q = TRG * ((NQ + NQPT - 1) / NQPT);
   const bool active = (int)threadIdx.x < nthr_q && threadIdx.x / ((NQ + NQPT - 1) / NQPT) < TRG;
@@ -281,8 +285,7 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && t + kStages < ntiles && !aborted) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (t + kStages < ntiles && !aborted) {
       issue(stage, t + kStages);
       pending[stage] = (int)(((t + kStages) / kStages) & 1);
     }
@@ -318,10 +321,27 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < E; e += 256) out[e] = red[e];
+  for (int e = threadIdx.x; e < E; e += NT) out[e] = red[e];
 }
 
-// H[e] = sum_blk partial[blk][e]  (fixed order: deterministic)
+// H[e] = sum_blk partial[blk][e]. One warp per entry: lane l sums blocks
+// l, l+32, ... (independent loads in flight), then a fixed shuffle tree; the
+// order is fixed, so the result is deterministic.
+__global__ void k_gram_reduce_w(int nblk, int E, const double* __restrict__ partial,
+                                double* __restrict__ H) {
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= E) return;
+  double v = 0.0;
+#pragma unroll 4
+  for (int b = lane; b < nblk; b += 32) v += partial[(int64_t)b * E + e];
+  v = warp_sum(v);
+  if (lane == 0) H[e] = v;
+}
+#define k_gram_reduce_launch(E_, nblk_, partial_, H_, st_) \
+  k_gram_reduce_w<<<((E_) + 7) / 8, 256, 0, (st_)>>>((nblk_), (E_), (partial_), (H_))
+
+// one thread per entry (small partial counts: the no-allocation variant)
 __global__ void k_gram_reduce(int nblk, int E, const double* __restrict__ partial,
                               double* __restrict__ H) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,10 +387,11 @@ static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V,
     constexpr int S = decltype(S_)::value;
     constexpr bool EX = decltype(E_)::value;
     constexpr int Q = EX ? (S >= 4 ? 4 : S) : 1;
+    constexpr int NT = 256;           // (512 threads measured slower)
     const int NQ = P / Q;
-    const int npt = NQ <= 256 ? 1 : NQ <= 512 ? 2 : 4;
+    const int npt = NQ <= NT ? 1 : NQ <= 2 * NT ? 2 : 4;
     const int qs = (NQ + npt - 1) / npt;
-    const int TRG = std::max(1, std::min(16, 256 / qs));
+    const int TRG = std::max(1, std::min(32, NT / qs));
     const size_t red = sizeof(double) * (size_t)E;
     const size_t smem = std::max(kStages * stage_bytes, red);
     if (smem > 200 * 1024 || NQ > 1024) {
@@ -379,16 +400,16 @@ static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V,
     }
     auto launch = [&](auto kern) {
       PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<nblk, 256, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, TRG, ctx->d_partial,
-                                    ctx->d_flag);
+      kern<<<nblk, NT, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, TRG, ctx->d_partial,
+                                   ctx->d_flag);
     };
-    if (npt == 1) launch(k_gram_bulk<VT, S, EX, Q, 1>);
-    else if (npt == 2) launch(k_gram_bulk<VT, S, EX, Q, 2>);
-    else launch(k_gram_bulk<VT, S, EX, Q, 4>);
+    if (npt == 1) launch(k_gram_bulk<VT, S, EX, Q, 1, NT>);
+    else if (npt == 2) launch(k_gram_bulk<VT, S, EX, Q, 2, NT>);
+    else launch(k_gram_bulk<VT, S, EX, Q, 4, NT>);
   });
   if (!ok) return false;
   check_launch("k_gram_bulk");
-  k_gram_reduce<<<(E + 255) / 256, 256, 0, st>>>(nblk, E, ctx->d_partial, H);
+  k_gram_reduce_launch(E, nblk, ctx->d_partial, H, st);
   check_launch("k_gram_reduce");
   ctx->launches += 2;
   return true;
@@ -426,7 +447,7 @@ static void gram_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t 
     else launch(k_gram<VT, S, EX, 4>);
   });
   check_launch("k_gram");
-  k_gram_reduce<<<(E + 255) / 256, 256, 0, st>>>(nblk, E, ctx->d_partial, H);
+  k_gram_reduce_launch(E, nblk, ctx->d_partial, H, st);
   check_launch("k_gram_reduce");
   ctx->launches += 2;
 }
@@ -631,10 +652,132 @@ static void cholqr_pass(pint_ctx ctx, int64_t n, int s, VT* W, double* R, double
   ctx->launches += 2;
 }
 
+// Streaming self-Gram for narrow blocks (S <= 8): G = W^T W (upper triangle
+// accumulated per thread over its rows, float64 across threads and CTAs).
+// SCALE: first W[r] <- W[r] Rinv (written back), then accumulate the new row:
+// the scaling of one CholQR pass fused with the Gram of the next.
+template <typename VT, int S, bool SCALE>
+__global__ void __launch_bounds__(256)
+k_syrk(int64_t n, VT* __restrict__ W, const double* __restrict__ Ri,
+       double* __restrict__ partial) {
+  constexpr int NT = S * (S + 1) / 2;
+  __shared__ VT Rs[S * S];
+  __shared__ double red[8][NT];
+  if (SCALE) {
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) Rs[e] = (VT)Ri[e];
+    __syncthreads();
+  }
+  VT acc[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) acc[t] = VT(0);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    VT w[S];
+    load_row<S, true>(W + r * S, S, w);
+    if (SCALE) {
+      VT o[S];
+#pragma unroll
+      for (int k = 0; k < S; ++k) o[k] = VT(0);
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int k = i; k < S; ++k) o[k] = fma(w[i], Rs[i * S + k], o[k]);
+      store_row<S, true>(W + r * S, S, o);
+#pragma unroll
+      for (int k = 0; k < S; ++k) w[k] = o[k];
+    }
+    int t = 0;
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int k = i; k < S; ++k) {
+        acc[t] = fma(w[i], w[k], acc[t]);
+        ++t;
+      }
+  }
+  // warp reduction in the vector precision (float64 arithmetic is scarce),
+  // float64 across warps and CTAs
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const VT v = warp_sum(acc[t]);
+    if (lane == 0) red[warp][t] = (double)v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    double v = 0.0;
+    for (int w8 = 0; w8 < 8; ++w8) v += red[w8][t];
+    // expand the upper triangle to the full S x S partial
+    int i = 0, rem = t;
+    while (rem >= S - i) {
+      rem -= S - i;
+      ++i;
+    }
+    const int k = i + rem;
+    partial[(int64_t)blockIdx.x * S * S + i * S + k] = v;
+    partial[(int64_t)blockIdx.x * S * S + k * S + i] = v;
+  }
+}
+
+template <typename VT, int S>
+static void syrk_t(pint_ctx ctx, int64_t n, VT* W, const double* Rinv, double* G, bool scale,
+                   cudaStream_t st) {
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(4LL * ctx->num_sms, (n + 255) / 256));
+  ensure_partial(ctx, sizeof(double) * (size_t)nblk * S * S);
+  ProfScope ps(ctx, PF_CHOLQR, sizeof(VT) * (double)n * S * (scale ? 2 : 1),
+               (double)n * S * S * (scale ? 2 : 1), st);
+  if (scale)
+    k_syrk<VT, S, true><<<nblk, 256, 0, st>>>(n, W, Rinv, ctx->d_partial);
+  else
+    k_syrk<VT, S, false><<<nblk, 256, 0, st>>>(n, W, Rinv, ctx->d_partial);
+  check_launch("k_syrk");
+  k_gram_reduce_launch(S * S, nblk, ctx->d_partial, G, st);
+  check_launch("k_gram_reduce");
+  ctx->launches += 2;
+}
+
+// CholQR2 for S in {1, 2, 4, 8}: syrk -> chol -> syrk(scale) -> chol -> scale.
+template <typename VT, int S>
+static void cholqr2_narrow(pint_ctx ctx, int64_t n, VT* W, double* R, double defl,
+                           int* defl_count, cudaStream_t st) {
+  CholScratch cs = chol_scratch(ctx);
+  syrk_t<VT, S>(ctx, n, W, nullptr, cs.G, false, st);
+  {
+    ProfScope ps(ctx, PF_CHOLQR, 0.0, 1.0 * S * S * S, st);
+    k_chol<<<1, 256, 0, st>>>(S, cs.G, defl, cs.R1, cs.Rinv, defl_count);
+    check_launch("k_chol");
+  }
+  syrk_t<VT, S>(ctx, n, W, cs.Rinv, cs.G, true, st);
+  ProfScope ps(ctx, PF_CHOLQR, 2.0 * sizeof(VT) * n * S, 1.0 * n * S * S, st);
+  k_chol<<<1, 256, 0, st>>>(S, cs.G, defl, cs.R2, cs.Rinv, defl_count);
+  check_launch("k_chol");
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(8LL * ctx->num_sms, (n + 255) / 256));
+  k_rowmul<VT, S, true><<<g, 256, 0, st>>>(n, S, W, cs.Rinv);
+  check_launch("k_rowmul");
+  k_small_mm<<<1, 256, 0, st>>>(S, cs.R2, cs.R1, R);
+  check_launch("k_small_mm");
+  ctx->launches += 4;
+}
+
 void cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W, double* R,
              int* defl_count, cudaStream_t st, int64_t n_pad) {
   CholScratch cs = chol_scratch(ctx);
   const double defl = precision == PINT_FP64 ? 1e-14 : 1e-8;
+  if (s == 1 || s == 2 || s == 4 || s == 8) {
+    auto run = [&](auto tag) {
+      using VT = decltype(tag);
+      VT* w = static_cast<VT*>(W);
+      switch (s) {
+        case 1: cholqr2_narrow<VT, 1>(ctx, n, w, R, defl, defl_count, st); break;
+        case 2: cholqr2_narrow<VT, 2>(ctx, n, w, R, defl, defl_count, st); break;
+        case 4: cholqr2_narrow<VT, 4>(ctx, n, w, R, defl, defl_count, st); break;
+        default: cholqr2_narrow<VT, 8>(ctx, n, w, R, defl, defl_count, st); break;
+      }
+    };
+    if (precision == PINT_FP64) run(double(0));
+    else run(float(0));
+    return;
+  }
   if (precision == PINT_FP64) {
     cholqr_pass<double>(ctx, n, s, (double*)W, cs.R1, defl, defl_count, st, n_pad);
     cholqr_pass<double>(ctx, n, s, (double*)W, cs.R2, defl, defl_count, st, n_pad);
@@ -662,17 +805,19 @@ k_hess_step(int j, int s, int ldh, const double* __restrict__ H1, const double* 
   __shared__ double vcur[32];
   const int L = (j + 2) * s;
   const int top = (j + 1) * s;
+  double* rs = col + s * L;          // earlier reflectors staged in shared memory
   for (int idx = threadIdx.x; idx < s * L; idx += blockDim.x) {
     const int l = idx / L, row = idx - l * L;
     col[idx] = row < top ? H1[row * s + l] + H2[row * s + l] : Rn[(row - top) * s + l];
   }
+  for (int idx = threadIdx.x; idx < j * s * kSmallLd; idx += blockDim.x) rs[idx] = refl[idx];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool act = lane <= s;
   if (warp < s) {
     double* cl = col + warp * L;
     for (int c = 0; c < j * s; ++c) {
-      const double v = act ? refl[c * kSmallLd + lane] : 0.0;
+      const double v = act ? rs[c * kSmallLd + lane] : 0.0;
       const double x = act ? cl[c + lane] : 0.0;
       const double d = warp_sum(v * x);
       if (act) cl[c + lane] = x - 2.0 * v * d;
@@ -897,7 +1042,7 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
   PINT_CUDA(cudaMemsetAsync(w->defl, 0, 64, st));
   PINT_CUDA(cudaMemcpyAsync(Vb(0), w->Rs, es * ns, cudaMemcpyDeviceToDevice, st));
   InnerResult res{0, 0, false, 0};
-  const size_t hess_smem = 8 * (size_t)s * (m + 1) * s;
+  const size_t hess_smem = 8 * ((size_t)s * (m + 1) * s + (size_t)m * s * kSmallLd);
   const size_t back_smem = 8 * (size_t)m * s * s;
   PINT_CUDA(cudaFuncSetAttribute(k_hess_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)hess_smem));
@@ -927,7 +1072,7 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
       launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg2, Vb(j + 1), 0, st);
       cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, st, np);
       ProfScope psh(ctx, PF_HESS, 0.0, 4.0 * (j + 1) * s * s * (s + 1), st);
-      k_hess_step<<<1, 512, 8 * (size_t)s * (j + 2) * s, st>>>(
+      k_hess_step<<<1, 512, 8 * ((size_t)s * (j + 2) * s + (size_t)j * s * kSmallLd), st>>>(
           j, s, ldh, w->Hg1, w->Hg2, w->Rn, w->Hb, w->refl, w->Gr, w->target, w->est, w->flag);
       check_launch("k_hess_step");
       ctx->launches += 1;
@@ -1019,6 +1164,9 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
                "restart out of range");
   PINT_REQUIRE((int64_t)(o->restart + 1) * op->s <= 1024, PINT_ERR_INVALID,
                "(restart + 1) * s must not exceed 1024");
+  PINT_REQUIRE(8 * ((size_t)op->s * (o->restart + 1) * op->s +
+                    (size_t)o->restart * op->s * kSmallLd) <= 227 * 1024,
+               PINT_ERR_INVALID, "restart too long for this block width (Hessenberg shared memory)");
   PINT_REQUIRE(o->precision >= PINT_FP64 && o->precision <= PINT_BF16, PINT_ERR_INVALID,
                "precision");
   PINT_REQUIRE(o->precond >= PINT_PC_NONE && o->precond <= PINT_PC_ILU0, PINT_ERR_INVALID,

@@ -354,13 +354,16 @@ k_colsq(int64_t n, int s, const VT* __restrict__ X, double* __restrict__ partial
   }
 }
 
+// one warp per column, fixed summation order (deterministic)
 __global__ void k_colsq_final(int nblk, int s, const double* __restrict__ partial,
                               double* __restrict__ out) {
-  const int k = threadIdx.x;
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= s) return;
   double v = 0.0;
-  for (int b = 0; b < nblk; ++b) v += partial[b * kMaxS + k];
-  out[k] = sqrt(v);
+#pragma unroll 4
+  for (int b = lane; b < nblk; b += 32) v += partial[b * kMaxS + k];
+  v = warp_sum(v);
+  if (lane == 0) out[k] = sqrt(v);
 }
 
 void launch_colnorm(pint_ctx ctx, int precision, int64_t n, int s, const void* X, double* out,
@@ -376,7 +379,7 @@ void launch_colnorm(pint_ctx ctx, int precision, int64_t n, int s, const void* X
     else
       k_colsq<float, S, E><<<nb, 256, 0, st>>>(n, s, (const float*)X, partial);
   });
-  k_colsq_final<<<1, 32, 0, st>>>(nb, s, partial, out);
+  k_colsq_final<<<1, 32 * kMaxS, 0, st>>>(nb, s, partial, out);
   check_launch("k_colsq");
   ctx->launches += 2;
 }
@@ -418,7 +421,7 @@ __global__ void k_scale_cast(int64_t n, int s, const double* __restrict__ src, O
   if (i >= n * s) return;
   const int k = (int)(i % s);
   const double c = colnorm ? colnorm[k] : 1.0;
-  const double v = c > 0.0 ? src[i] / c : 0.0;
+  const double v = c > 0.0 ? src[i] * (1.0 / c) : 0.0;
   if constexpr (std::is_same<OT, double>::value) dst[i] = v;
   else dst[i] = __double2float_rn(v);
 }
