@@ -58,7 +58,7 @@ WORKLOADS = {
 }
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
@@ -75,7 +75,7 @@ def parse():
     p.add_argument("--sweep", action="store_true",
                    help="also time one solve per (s, precision) for s=1..16")
     p.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
-    a = p.parse_args()
+    a = p.parse_args(argv)
     dn, ds, dpc, dprec, _ = WORKLOADS[a.workload]
     a.n = a.n or dn
     a.s = a.s or ds
@@ -148,8 +148,9 @@ def oracle_sample(args, n, reps=1):
     G = nl_stages(args)
     for _ in range(reps):
         t = time.perf_counter()
-        newton.pipelined_block_newton(prob, A, c, 1.0 / 96.0, -z, G, s, tol=1e-8, inner_tol=1e-5,
-                                      precond=args.precond, max_step=1.0)
+        newton.pipelined_block_newton(prob, A, c, 1.0 / 96.0, -z, G, s, tol=1e-5, inner_tol=1e-5,
+                                      precond=args.precond, max_step=1.0, max_newton=150,
+                                      lscheme_L=vg.lipschitz())
         times.append(time.perf_counter() - t)
     return {"n": n ** 3, "steps": G, "times": times}
 
@@ -362,6 +363,7 @@ class PipelineCase:
             y0 = np.full(n * n, 0.5)
             self.time_steps = self.G // 2
             self.max_step = 0.0
+            self.lscheme = 0.0
         else:
             dims = (n, n, n)
             w = synth.richards_3d(n, s)
@@ -370,11 +372,14 @@ class PipelineCase:
             self.prob = P.pint_problem_create(ctx, P.PINT_PROBLEM_RICHARDS, *dims, params=VG,
                                               field=self.Ksd)
             self.A, self.c = np.array([[1.0]]), np.array([1.0])
-            self.tau, self.tol = 1.0 / 96.0, 1e-8
+            # Sec. 4.3: implicit Euler, tau = 1/96, the L-scheme with L the
+            # Lipschitz constant of theta, outer tolerance 1e-5
+            self.tau, self.tol = 1.0 / 96.0, 1e-5
             z = (np.arange(n) + 0.5) / n
             y0 = -np.broadcast_to(z[:, None, None], (n, n, n)).ravel().copy()
             self.time_steps = self.G
             self.max_step = 1.0
+            self.lscheme = -1.0
         self.n = int(np.prod(dims))
         self.y0 = y0
         self.y0d = torch.tensor(y0, device="cuda", dtype=torch.float64)
@@ -382,8 +387,9 @@ class PipelineCase:
         o = P.pint_opts_default()
         o.tol = self.tol
         o.inner_tol = inner_tol_for(args, s)
-        o.max_outer = 60
+        o.max_outer = 150 if self.lscheme else 60
         o.max_step = self.max_step
+        o.lscheme_L = self.lscheme
         o.precond = P.PINT_PC_ILU0 if args.precond == "ilu0" else P.PINT_PC_JACOBI
         o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[args.precision]
         self.o = o
@@ -408,7 +414,9 @@ class PipelineCase:
     def describe(self):
         return {"cells": self.n, "s": self.s, "stages": self.G, "nnz": self.nnz, "tau": self.tau,
                 "tol": self.tol, "inner_tol": self.o.inner_tol, "restart": self.o.restart,
-                "max_step": self.max_step}
+                "max_step": self.max_step,
+                "linearisation": "L-scheme (L = Lipschitz constant of theta)" if self.lscheme
+                else "simplified Newton"}
 
     def close(self):
         self.P.pint_problem_destroy(self.prob)

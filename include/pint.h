@@ -80,6 +80,13 @@ typedef struct {
   double max_step;   /* Newton calls only: if > 0, column k of the update V
                         is scaled by min(1, max_step / max_r |V_rk|) (a step
                         bound; the paper gives no globalisation). 0 = off    */
+  double lscheme_L;  /* Richards Newton calls only: 0 = Newton, J = alpha
+                        theta'(Y_0) + beta Df(t_0, Y_0). Otherwise the
+                        L-scheme of Sec. 4.3: theta' is replaced by the
+                        constant L and the conductivities are frozen at Y_0
+                        (no derivative of kr): J = alpha L I + beta A(Y_0).
+                        L > 0 is used as given; L < 0 takes the Lipschitz
+                        constant of theta (pint_vg_lipschitz)                */
   int restart;       /* GMRES restart length m, 1..PINT_MAX_RESTART (30)    */
   int max_outer;     /* outer (defect-correction / Newton) iteration limit  */
   int max_inner;     /* block Arnoldi steps per inner solve                 */
@@ -193,6 +200,11 @@ int pint_problem_create(pint_ctx ctx, pint_problem* prob, int kind, int nx,
                         int ny, int nz, const double* params,
                         const double* field, void* stream);
 int pint_problem_destroy(pint_problem prob);
+/* Lipschitz constant of the van Genuchten theta(psi) for params = {alpha, n,
+ * theta_r, theta_s}: sup theta' = (theta_s - theta_r) m n alpha x^(n-1)
+ * (1 + x^n)^(-m-1) at x^n = m, m = 1 - 1/n (the L of the L-scheme, Sec. 4.3).
+ * Host only; PINT_ERR_INVALID for n <= 1, alpha <= 0 or theta_s <= theta_r. */
+int pint_vg_lipschitz(const double* params, double* L);
 pint_op pint_problem_operator(pint_problem prob);
 /* mass_out = M(y), f_out = f(t, y) for one column y[n] (either output may
  * be NULL). */
@@ -207,9 +219,10 @@ int pint_problem_residual(pint_problem prob, const double* times,
 /* One simplified-Newton iteration of Algorithm 1 on the current window:
  * R = R(Y); if ||R_0|| <= tol * ||B0_0|| (tol alone if B0_0 = 0) set
  * *converged = 1 and
- * return; else J = alpha M'(Y_0) + beta Df(t_0, Y_0), solve J V = R with
- * block GMRES (inner_tol), Y <- Y - V (each column's step bounded by
- * opts.max_step when it is > 0), *converged = 0. Synchronous. */
+ * return; else J = alpha M'(Y_0) + beta Df(t_0, Y_0) (or the L-scheme matrix
+ * when opts.lscheme_L != 0), solve J V = R with block GMRES (inner_tol),
+ * Y <- Y - V (each column's step bounded by opts.max_step when it is > 0),
+ * *converged = 0. Synchronous. */
 int pint_newton_step(pint_problem prob, const double* times, double* Y,
                      const double* B0, const pint_opts* opts, int* converged,
                      pint_stats* stats, void* stream);
@@ -265,6 +278,10 @@ int pint_inner_apply(pint_op op, const double* X, double* Z, void* stream);
  * J on first use. */
 int pint_precond_apply(pint_op op, int precond, const double* X, double* Z,
                        void* stream);
+/* Z = P^{-1} X with the float32 copy of the ILU(0) factors that the float32
+ * and bf16 inner solves use (X, Z: float32 N x s, device, must not alias).
+ * Factors J on first use like pint_precond_apply. */
+int pint_ilu0_apply_f32(pint_op op, const float* X, float* Z, void* stream);
 /* H[(b*s+i)*s + k] = sum_r V_b[r][i] W[r][k]  ((nb*s) x s, float64, device). */
 int pint_block_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb,
                     const void* V, const void* W, double* H, void* stream);

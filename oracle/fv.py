@@ -195,6 +195,24 @@ class VanGenuchten:
         d = (self.ts - self.tr) * m * n * a * x ** (n - 1.0) * (1.0 + x ** n) ** (-m - 1.0)
         return np.where(psi >= 0.0, 0.0, d)
 
+    def lipschitz(self, samples=200001):
+        """sup_psi theta'(psi), the L of the L-scheme (Sec. 4.3): the maximum of
+        dtheta over a log-spaced scan of alpha |psi| in [1e-4, 1e4], refined by
+        golden-section search around the best sample."""
+        x = np.logspace(-4.0, 4.0, samples)
+        d = self.dtheta(-x / self.alpha)
+        i = int(np.argmax(d))
+        lo, hi = x[max(i - 1, 0)], x[min(i + 1, samples - 1)]
+        g = (np.sqrt(5.0) - 1.0) / 2.0
+        f = lambda t: float(self.dtheta(np.array([-t / self.alpha]))[0])
+        for _ in range(200):
+            a, b = hi - g * (hi - lo), lo + g * (hi - lo)
+            if f(a) >= f(b):
+                hi = b
+            else:
+                lo = a
+        return max(f(0.5 * (lo + hi)), float(d[i]))
+
     def kr(self, psi):
         x = self.theta(psi) / self.ts
         w = 1.0 - x ** (1.0 / self.m)
@@ -268,15 +286,17 @@ def richards_f(dims, t, psi, Ks, vg: VanGenuchten, dt_D):
     return f
 
 
-def richards_jacobian(dims, t, psi, Ks, vg: VanGenuchten, dt_D):
-    """Df(t,psi) (CSR) of richards_f."""
+def richards_jacobian(dims, t, psi, Ks, vg: VanGenuchten, dt_D, frozen=False):
+    """Df(t,psi) (CSR) of richards_f. frozen=True drops the derivative of kr:
+    the matrix of the linear flux operator with the conductivities fixed at
+    psi (the conductivity part of the L-scheme of Sec. 4.3)."""
     h = 1.0 / dims[0]
     n = int(np.prod(dims))
     Ksr = np.asarray(Ks, dtype=np.float64).ravel()
     z, top = richards_cells(dims)
     H = psi + z
     kr = vg.kr(psi)
-    dkr = vg.dkr(psi)
+    dkr = np.zeros_like(psi) if frozen else vg.dkr(psi)
     rows, cols, vals = [], [], []
     for _, P, Q in _faces(dims):
         kf = 2.0 * Ksr[P] * Ksr[Q] / (Ksr[P] + Ksr[Q])
@@ -299,7 +319,7 @@ def richards_jacobian(dims, t, psi, Ks, vg: VanGenuchten, dt_D):
     P = top
     up = HD > H[P]
     K = Ksr[P] * np.where(up, krD, kr[P])
-    dK = np.where(up, 0.0, Ksr[P] * dkr[P])
+    dK = np.where(up, 0.0, Ksr[P] * dkr[P])   # zero when frozen
     rows.append(P)
     cols.append(P)
     vals.append(2.0 * (K - dK * (HD - H[P])) / h**2)

@@ -85,6 +85,10 @@ class RichardsProblem:
     def jac(self, t, y):
         return fv.richards_jacobian(self.dims, t, y, self.Ks, self.vg, self.dt_D)
 
+    def jac_frozen(self, t, y):
+        """Flux operator with the conductivities frozen at y (L-scheme)."""
+        return fv.richards_jacobian(self.dims, t, y, self.Ks, self.vg, self.dt_D, frozen=True)
+
 
 def sequential_dirk_newton(prob, A, c, tau, y0, nstages, tol=1e-13, maxit=50):
     """Plain definition: one stage at a time, full Newton, sparse direct solves.
@@ -140,9 +144,23 @@ def window_residual(prob, A1, A2, times, Y, B0):
     return MY @ A1.T + FY @ A2.T - B0
 
 
+def linearisation(prob, alpha, beta, t, y, lscheme_L=None):
+    """Matrix of one outer iteration: the simplified-Newton Jacobian
+    alpha M'(y) + beta Df(t, y) (Algorithm 1), or with lscheme_L the L-scheme
+    of Sec. 4.3 (Richards): M' replaced by the constant L, the conductivities
+    frozen at y: alpha L I + beta A(y)."""
+    if lscheme_L:
+        J = sp.identity(len(y)) * (alpha * lscheme_L) + beta * prob.jac_frozen(t, y)
+    else:
+        J = sp.diags(alpha * prob.dmass(y)) + beta * prob.jac(t, y)
+    J = sp.csr_matrix(J)
+    J.sort_indices()
+    return J
+
+
 def pipelined_block_newton(prob, A, c, tau, y0, nstages, s, tol=1e-8, inner_tol=1e-5,
                            precond="ilu0", restart=30, max_newton=50, inner_maxit=1000,
-                           max_step=None):
+                           max_step=None, lscheme_L=None):
     """Algorithm 1 over `nstages` global stages with a window of s stages.
     Returns (stages N x nstages, stats dict).
 
@@ -166,9 +184,7 @@ def pipelined_block_newton(prob, A, c, tau, y0, nstages, s, tol=1e-8, inner_tol=
             R = window_residual(prob, A1, A2, times, Y, B0)
             if np.linalg.norm(R[:, 0]) <= thr or it == max_newton:
                 break
-            J = sp.csr_matrix(sp.diags(alpha * prob.dmass(Y[:, 0])) +
-                              beta * prob.jac(times[0], Y[:, 0]))
-            J.sort_indices()
+            J = linearisation(prob, alpha, beta, times[0], Y[:, 0], lscheme_L)
             Pinv = krylov.make_preconditioner(J, precond)
             V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R, inner_tol, restart,
                                          inner_maxit)

@@ -41,7 +41,7 @@ class PintError(RuntimeError):
 
 class pint_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("max_step", C.c_double),
-                ("restart", C.c_int),
+                ("lscheme_L", C.c_double), ("restart", C.c_int),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("reserved", C.c_int * 3)]
 
@@ -83,6 +83,7 @@ _SIGS = {
     "pint_shift": (_i, [_vp, _i64, _i, _vp]),
     "pint_problem_create": (_i, [_vp, C.POINTER(_vp), _i, _i, _i, _i, _vp, _vp, _vp]),
     "pint_problem_destroy": (_i, [_vp]),
+    "pint_vg_lipschitz": (_i, [_vp, C.POINTER(_d)]),
     "pint_problem_operator": (_vp, [_vp]),
     "pint_problem_eval": (_i, [_vp, _d, _vp, _vp, _vp, _vp]),
     "pint_problem_residual": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -97,6 +98,7 @@ _SIGS = {
     "pint_kernel_launches": (C.c_longlong, [_vp]),
     "pint_inner_apply": (_i, [_vp, _vp, _vp, _vp]),
     "pint_precond_apply": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "pint_ilu0_apply_f32": (_i, [_vp, _vp, _vp, _vp]),
     "pint_block_gram": (_i, [_vp, _i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
     "pint_block_update": (_i, [_vp, _i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
     "pint_block_gram_noalloc": (_i, [_i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
@@ -251,6 +253,13 @@ def pint_problem_destroy(prob):
     return lib.pint_problem_destroy(prob)
 
 
+def pint_vg_lipschitz(params):
+    """sup theta'(psi) of the van Genuchten params (alpha, n, theta_r, theta_s)."""
+    L = _d()
+    _check(lib.pint_vg_lipschitz(_ptr(_host_f64(params[:4])), C.byref(L)))
+    return L.value
+
+
 def pint_problem_operator(prob):
     return C.c_void_p(lib.pint_problem_operator(prob))
 
@@ -293,6 +302,10 @@ def pint_inner_apply(ctx, op, X, Z, stream=None):
 
 def pint_precond_apply(ctx, op, precond, X, Z, stream=None):
     _check(lib.pint_precond_apply(op, precond, _ptr(X), _ptr(Z), _stream(stream)), ctx)
+
+
+def pint_ilu0_apply_f32(ctx, op, X, Z, stream=None):
+    _check(lib.pint_ilu0_apply_f32(op, _ptr(X), _ptr(Z), _stream(stream)), ctx)
 
 
 def pint_block_gram(ctx, precision, n, s, nb, V, W, H, stream=None):

@@ -417,6 +417,23 @@ int pint_inner_apply(pint_op op, const double* X, double* Z, void* stream) {
   });
 }
 
+int pint_ilu0_apply_f32(pint_op op, const float* X, float* Z, void* stream) {
+  if (!op) return PINT_ERR_INVALID;
+  return guard(op->ctx, [&] {
+    PINT_REQUIRE(op->s >= 1, PINT_ERR_INVALID, "coupling not set");
+    require_aligned(X, "X");
+    require_aligned(Z, "Z");
+    PINT_REQUIRE(X != Z, PINT_ERR_INVALID, "X and Z must not alias");
+    cudaStream_t st = as_stream(stream);
+    if (!op->j_valid) build_inner(op, st);
+    ilu_setup(op, st);
+    ilu_apply(op, PINT_FP32, X, Z, st);
+    PINT_CUDA(cudaStreamSynchronize(st));
+    ilu_check(op);
+    return PINT_OK;
+  });
+}
+
 int pint_precond_apply(pint_op op, int precond, const double* X, double* Z, void* stream) {
   if (!op) return PINT_ERR_INVALID;
   return guard(op->ctx, [&] {

@@ -322,8 +322,12 @@ __global__ void k_nl_eval(Grid g, int64_t n, const __grid_constant__ NlParams P,
 
 // Row r of J = alpha M'(y) + beta Df(t, y) in the stencil CSR order; y is
 // column 0 of a row-major N x ys block. Also writes diag(J) and its inverse.
+//
+// Richards with lsL > 0: the L-scheme matrix alpha lsL I + beta A(y), A the
+// flux operator with the conductivities frozen at y (kr not differentiated).
 __global__ void k_nl_jacobian(Grid g, int64_t n, const __grid_constant__ NlParams P,
                               const double* __restrict__ Y, int ys, double alpha, double beta,
+                              double lsL,
                               const int* __restrict__ rowptr, double* __restrict__ J,
                               double* __restrict__ Jd, double* __restrict__ Jinv) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,8 +350,9 @@ __global__ void k_nl_jacobian(Grid g, int64_t n, const __grid_constant__ NlParam
   } else {
     const Soil& so = P.soil;
     const double zP = (k + 0.5) * g.h, KsP = P.Ks[r];
-    const double krP = vg_kr(so, yp), dkrP = vg_dkr(so, yp);
-    diag = alpha * vg_dtheta(so, yp);
+    const bool frozen = lsL > 0.0;
+    const double krP = vg_kr(so, yp), dkrP = frozen ? 0.0 : vg_dkr(so, yp);
+    diag = frozen ? alpha * lsL : alpha * vg_dtheta(so, yp);
     for (int d = 0; d < 6; ++d) {
       const int64_t q = nbr(g, r, i, j, k, d);
       if (q < 0) continue;
@@ -357,7 +362,7 @@ __global__ void k_nl_jacobian(Grid g, int64_t n, const __grid_constant__ NlParam
       const double HP = yp + zP, HQ = yq + zQ;
       const bool upQ = (HQ > HP) || (HQ == HP && q < r);
       const double K = kf * (upQ ? vg_kr(so, yq) : krP);
-      const double dKQ = upQ ? kf * vg_dkr(so, yq) : 0.0;
+      const double dKQ = (upQ && !frozen) ? kf * vg_dkr(so, yq) : 0.0;
       const double dKP = upQ ? 0.0 : kf * dkrP;
       const double dH = HQ - HP;
       diag += beta * (K - dKP * dH) * g.ih2;
@@ -466,7 +471,17 @@ static void nl_eval(pint_problem p, double t, const double* y, double* m, double
   p->ctx->launches += 1;
 }
 
-static void nl_jacobian(pint_problem p, double t, const double* Y, int ys, cudaStream_t st) {
+// sup over psi of theta'(psi) for van Genuchten: with x = alpha |psi|,
+// theta' = (ts - tr) m n alpha x^(n-1) (1 + x^n)^(-m-1), stationary where
+// (n-1)(1 + x^n) = (m+1) n x^n, i.e. x^n = (n-1)/(mn+1) = m for m = 1 - 1/n.
+static double vg_lipschitz(double a, double n, double tr, double ts) {
+  const double m = 1.0 - 1.0 / n;
+  const double x = std::pow(m, 1.0 / n);
+  return (ts - tr) * m * n * a * std::pow(x, n - 1.0) * std::pow(1.0 + m, -m - 1.0);
+}
+
+static void nl_jacobian(pint_problem p, double t, const double* Y, int ys, double lsL,
+                        cudaStream_t st) {
   pint_op op = p->op;
   op_clear_inner_cache(op);
   if (!op->Jval) {
@@ -477,8 +492,8 @@ static void nl_jacobian(pint_problem p, double t, const double* Y, int ys, cudaS
   NlParams P = params_of(p, &t, 1);
   ProfScope ps(p->ctx, PF_NL, 8.0 * op->nnz + 24.0 * p->n, 60.0 * p->n, st);
   k_nl_jacobian<<<grid_for(p->n, 128), 128, 0, st>>>(grid_of(p), p->n, P, Y, ys, op->alpha,
-                                                     op->beta, op->rowptr, op->Jval, op->Jdiag,
-                                                     op->Jinvdiag);
+                                                     op->beta, lsL, op->rowptr, op->Jval,
+                                                     op->Jdiag, op->Jinvdiag);
   check_launch("k_nl_jacobian");
   p->ctx->launches += 1;
   op->j_valid = true;
@@ -494,6 +509,9 @@ static double now_ms() {
 // solve J V = R for all s columns; Y <- Y - V.
 static void newton_step(pint_problem p, const double* times, double* Y, const double* B0,
                         const pint_opts* o, int* converged, pint_stats* stats, cudaStream_t st) {
+  PINT_REQUIRE(std::isfinite(o->lscheme_L) &&
+                   (o->lscheme_L == 0.0 || p->kind == PINT_PROBLEM_RICHARDS),
+               PINT_ERR_INVALID, "the L-scheme (lscheme_L != 0) applies to Richards problems");
   pint_op op = p->op;
   pint_ctx ctx = p->ctx;
   const int s = op->s;
@@ -525,7 +543,9 @@ static void newton_step(pint_problem p, const double* times, double* Y, const do
     return;
   }
   *converged = 0;
-  nl_jacobian(p, times[0], Y, s, st);
+  double lsL = o->lscheme_L;
+  if (lsL < 0.0) lsL = vg_lipschitz(p->vg_a, p->vg_n, p->th_r, p->th_s);
+  nl_jacobian(p, times[0], Y, s, lsL, st);
   const double ts = now_ms();
   if (o->precond == PINT_PC_ILU0) ilu_setup(op, st);
   if (stats) stats->setup_ms += now_ms() - ts;
@@ -707,6 +727,14 @@ int pint_problem_create(pint_ctx ctx, pint_problem* out, int kind, int nx, int n
     *out = p;
     return PINT_OK;
   });
+}
+
+int pint_vg_lipschitz(const double* params, double* L) {
+  if (!params || !L) return PINT_ERR_INVALID;
+  const double a = params[0], n = params[1], tr = params[2], ts = params[3];
+  if (!(n > 1.0) || !(a > 0.0) || !(ts > tr)) return PINT_ERR_INVALID;
+  *L = vg_lipschitz(a, n, tr, ts);
+  return PINT_OK;
 }
 
 int pint_problem_destroy(pint_problem p) {

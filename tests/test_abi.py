@@ -67,3 +67,15 @@ def test_dirk_builder_matches_oracle():
             R1, R2, _ = coupling.multistep_matrices(tab[0], steps, 0.1)
             np.testing.assert_array_equal(A1, R1)
             np.testing.assert_array_equal(A2, R2)
+
+
+def test_vg_lipschitz_host_call_matches_oracle():
+    """pint_vg_lipschitz (closed form) against the oracle's numerical
+    supremum of theta', including the paper's silt loam (L = 4.501e-2)."""
+    import paper_2504_02117_gb300 as P
+    from oracle import fv
+    for prm in [(1.0, 2.0, 0.05, 0.4), (0.423, 2.06, 0.131, 0.396), (3.0, 1.4, 0.0, 0.5)]:
+        L = P.pint_vg_lipschitz(prm)
+        assert abs(L - fv.VanGenuchten(*prm).lipschitz()) <= 1e-12 * L
+    with pytest.raises(P.PintError):
+        P.pint_vg_lipschitz((1.0, 1.0, 0.05, 0.4))

@@ -151,3 +151,75 @@ def test_pipeline_richards_equals_sequential(P, ctx):
         assert np.all(err < 1e-10), err
     finally:
         P.pint_problem_destroy(prob)
+
+
+def test_lscheme_matrix_matches_oracle(P, ctx):
+    """With opts.lscheme_L < 0 the outer iteration's matrix is the L-scheme
+    matrix of Sec. 4.3, alpha L I + beta A(y_0) with L the Lipschitz constant
+    of theta and the conductivities frozen at y_0."""
+    import torch
+    dims = (7, 6, 5)
+    prob, oprob, n = _make(P, ctx, "richards", dims)
+    try:
+        y = _state("richards", dims, n, 1, 5)[:, 0]
+        s, tau = 2, 0.01
+        A, _, c = coupling.implicit_euler()
+        A1, A2, terms, times = coupling.window_matrices(A, c, tau, 0, s)
+        op = P.pint_problem_operator(prob)
+        P.pint_set_coupling(ctx, op, A1, A2)
+        o = P.pint_opts_default()
+        o.tol = 1e-30
+        o.inner_tol = 1e-3
+        o.precond = P.PINT_PC_JACOBI
+        o.lscheme_L = -1.0
+        conv, st = P.pint_newton_step(ctx, prob, times, _dev(np.column_stack([y, y])),
+                                      _dev(np.zeros((n, s))), o)
+        assert not conv
+        X = synth.uniform(6, n * s).reshape(n, s)
+        Z = torch.empty(n, s, device="cuda", dtype=torch.float64)
+        P.pint_inner_apply(ctx, op, _dev(X), Z)
+        J = newton.linearisation(oprob, A1[0, 0], A2[0, 0], times[0], y,
+                                 fv.VanGenuchten(*VG[:4]).lipschitz())
+        h2 = float(dims[0]) ** 2
+        np.testing.assert_allclose(Z.cpu().numpy(), J @ X, rtol=1e-11, atol=1e-11 * h2)
+        # the L-scheme is a Richards option only
+        dprob, _, _ = _make(P, ctx, "diffreact", (9, 8, 1))
+        try:
+            P.pint_set_coupling(ctx, P.pint_problem_operator(dprob), A1, A2)
+            with pytest.raises(P.PintError):
+                P.pint_newton_step(ctx, dprob, times, _dev(np.full((72, s), 0.5)),
+                                   _dev(np.zeros((72, s))), o)
+        finally:
+            P.pint_problem_destroy(dprob)
+    finally:
+        P.pint_problem_destroy(prob)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_pipeline_richards_lscheme_equals_sequential(P, ctx, prec):
+    """Algorithm 1 with the L-scheme outer iteration reaches the stages of
+    sequential Newton stepping (the plain definition) on 8^3 cells."""
+    import torch
+    dims = (8, 8, 8)
+    prob, oprob, n = _make(P, ctx, "richards", dims)
+    try:
+        A, _, c = coupling.implicit_euler()
+        tau, G, s = 1.0 / 96.0, 6, 4
+        z, _ = fv.richards_cells(dims)
+        y0 = -z
+        out = torch.zeros(n, G, device="cuda", dtype=torch.float64)
+        o = P.pint_opts_default()
+        o.tol = 1e-10
+        o.inner_tol = 1e-8 if prec == "fp64" else 1e-5
+        o.precond = P.PINT_PC_ILU0
+        o.precision = P.PINT_FP64 if prec == "fp64" else P.PINT_FP32
+        o.max_outer = 150
+        o.max_step = 1.0
+        o.lscheme_L = -1.0
+        P.pint_pipeline_run(ctx, prob, A, c, tau, s, _dev(y0), G, out, o)
+        Yseq, _ = newton.sequential_dirk_newton(oprob, A, c, tau, y0, G)
+        # ||R_0|| <= 1e-10 ||B0_0|| bounds the stage error by ~1e-7 (see the
+        # oracle's own L-scheme test)
+        np.testing.assert_allclose(out.cpu().numpy(), Yseq, rtol=0, atol=2e-7)
+    finally:
+        P.pint_problem_destroy(prob)

@@ -139,3 +139,57 @@ def test_richards_hydrostatic_is_steady_without_boundary_flux():
     mask[top] = False
     np.testing.assert_allclose(f[mask], 0.0, atol=1e-12)
     assert np.all(f[top] > 0.0)      # psi_D = -2 below hydrostatic: water leaves
+
+
+def test_vg_lipschitz_matches_paper_silt_loam():
+    """Sec. 4.3 chooses L as the Lipschitz constant of Theta for the silt loam
+    of its parameter table (alpha 0.423, n 2.06, theta_R 0.131, theta_S 0.396)
+    and prints L = 4.501e-2."""
+    vg = fv.VanGenuchten(0.423, 2.06, 0.131, 0.396)
+    assert abs(vg.lipschitz() - 4.501e-2) < 0.0005e-2
+
+
+def test_vg_lipschitz_is_the_supremum():
+    """L bounds theta' everywhere and is attained, at alpha |psi| = m^(1/n)
+    (the stationary point of theta')."""
+    for a, n, tr, ts in [(1.0, 2.0, 0.05, 0.4), (0.423, 2.06, 0.131, 0.396), (3.0, 1.4, 0.0, 0.5)]:
+        vg = fv.VanGenuchten(a, n, tr, ts)
+        L = vg.lipschitz()
+        psi = -np.logspace(-6, 6, 20001)
+        assert np.all(vg.dtheta(psi) <= L * (1 + 1e-12))
+        m = 1.0 - 1.0 / n
+        x = m ** (1.0 / n)
+        np.testing.assert_allclose(vg.dtheta(np.array([-x / a]))[0], L, rtol=1e-12)
+        # theta is L-Lipschitz: |theta(p) - theta(q)| <= L |p - q|
+        p, q = psi[:-1], psi[1:]
+        assert np.all(np.abs(vg.theta(p) - vg.theta(q)) <= L * np.abs(p - q) * (1 + 1e-9))
+
+
+def test_richards_frozen_jacobian():
+    """The L-scheme's conductivity part: symmetric (one conductivity per face,
+    harmonic K_S), equal to the full Jacobian where kr is constant (saturated
+    soil, psi > 0), and the exact derivative of f with kr held at psi0."""
+    dims = (5, 4, 3)
+    n = 60
+    rng = np.random.default_rng(3)
+    Ks = np.exp(rng.standard_normal(dims[::-1]))
+    vg = fv.VanGenuchten(1.0, 2.0, 0.05, 0.4)
+    z, _ = fv.richards_cells(dims)
+    psi = -z - 0.3 + 0.2 * rng.random(n)
+    A = fv.richards_jacobian(dims, 0.02, psi, Ks, vg, 1 / 16, frozen=True).toarray()
+    np.testing.assert_allclose(A, A.T, rtol=1e-13, atol=1e-12)
+    wet = 0.5 + rng.random(n)
+    np.testing.assert_allclose(
+        fv.richards_jacobian(dims, 0.02, wet, Ks, vg, 1 / 16, frozen=True).toarray(),
+        fv.richards_jacobian(dims, 0.02, wet, Ks, vg, 1 / 16).toarray(), rtol=1e-13, atol=1e-12)
+    # with kr frozen f is affine in psi as long as no face changes its upwind
+    # side: f(psi0 + d) - f_frozen... checked on a small perturbation
+    d = 1e-7 * rng.standard_normal(n)
+    kr0 = vg.kr(psi)
+
+    class Frozen(fv.VanGenuchten):
+        def kr(self, p):
+            return kr0
+    f0 = fv.richards_f(dims, 0.02, psi, Ks, Frozen(1.0, 2.0, 0.05, 0.4), 1 / 16)
+    f1 = fv.richards_f(dims, 0.02, psi + d, Ks, Frozen(1.0, 2.0, 0.05, 0.4), 1 / 16)
+    np.testing.assert_allclose(f1 - f0, A @ d, rtol=1e-5, atol=1e-12)

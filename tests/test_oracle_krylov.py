@@ -148,3 +148,37 @@ def test_ilu0_matches_brute_force_and_pattern_property():
     mask = Jd != 0
     np.testing.assert_allclose(LU[mask], Jd[mask], rtol=1e-12, atol=1e-9)
     assert L.nnz + U.nnz == J.nnz + J.shape[0]
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (7, 6, 1), (2, 3, 4), (1, 5, 2), (3, 1, 4),
+                                  (9, 1, 1)])
+def test_ilu0_stencil_equals_generic_ilu0(dims):
+    """The plane-by-plane stencil ILU(0) gives the same factors and the same
+    P^{-1} X as the generic IKJ elimination, including grids with axes of
+    extent 1 (where stencil offsets coincide)."""
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(11)
+    K = fv.convdiff_matrix(dims, np.exp(rng.standard_normal(dims[::-1])), (1.0, -0.5, 0.3))
+    J = sp.csr_matrix(sp.diags(10.0 + rng.uniform(-1, 1, n)) + K)
+    J.sort_indices()
+    L, U = krylov.ilu0(J)
+    d, lower, upper = krylov.ilu0_stencil(dims, J)
+    np.testing.assert_allclose(d, U.diagonal(), rtol=1e-13)
+    Uoff = sp.triu(U, k=1).toarray()
+    for o, u in upper.items():
+        idx = np.nonzero(u)[0]
+        np.testing.assert_array_equal(Uoff[idx, idx + o], u[idx])   # U keeps J's upper part
+    X = rng.standard_normal((n, 3))
+    np.testing.assert_allclose(krylov.ilu0_stencil_apply(dims, (d, lower, upper), X),
+                               krylov.ilu0_apply(L, U)(X), rtol=1e-12, atol=1e-13)
+
+
+def test_ilu0_stencil_tridiagonal_is_exact_solve():
+    """On a 1-D grid ILU(0) is the exact LU: P^{-1} = J^{-1}."""
+    dims = (40, 1, 1)
+    rng = np.random.default_rng(12)
+    K = fv.convdiff_matrix(dims, np.exp(rng.standard_normal((1, 1, 40))), (1.0, 0.0, 0.0))
+    J = sp.csr_matrix(sp.identity(40) * 50.0 + K)
+    b = rng.standard_normal((40, 2))
+    Z = krylov.ilu0_stencil_apply(dims, krylov.ilu0_stencil(dims, J), b)
+    np.testing.assert_allclose(J @ Z, b, rtol=1e-12, atol=1e-12)

@@ -133,3 +133,26 @@ def test_pipelined_richards_equals_sequential():
     Ypl, st = newton.pipelined_block_newton(prob, A, c, tau, -z, G, 4, tol=1e-12,
                                             inner_tol=1e-6)
     np.testing.assert_allclose(Ypl, Yseq, rtol=1e-9, atol=1e-10)
+
+
+def test_pipelined_richards_lscheme_equals_sequential():
+    """Algorithm 1 with the L-scheme of Sec. 4.3 as the outer iteration (L =
+    Lipschitz constant of theta, conductivities frozen at the first column)
+    converges, linearly, to the same stages as sequential Newton stepping.
+    The trailing columns iterate with the first column's frozen conductivities
+    and need the step bound, as with Newton."""
+    import synth
+    dims = (6, 6, 6)
+    Ks = np.exp(2.0 * synth.correlated_field(4, dims[::-1], 2.0))
+    vg = fv.VanGenuchten(1.0, 2.0, 0.05, 0.4)
+    z, _ = fv.richards_cells(dims)
+    prob = newton.RichardsProblem(dims, Ks, vg, 1 / 16)
+    A, _, c = coupling.implicit_euler()
+    Yseq, _ = newton.sequential_dirk_newton(prob, A, c, 1 / 96, -z, 5)
+    Ypl, st = newton.pipelined_block_newton(prob, A, c, 1 / 96, -z, 5, 4, tol=1e-10,
+                                            inner_tol=1e-8, max_newton=120, max_step=1.0,
+                                            lscheme_L=vg.lipschitz())
+    assert max(st["newton"]) < 120
+    # ||R_0|| <= 1e-10 ||B0_0|| ~ 4e-8 and ||J^-1|| <= 1 here (diag J >= alpha
+    # theta' >= 1 on these heads): stage errors below 1e-7
+    np.testing.assert_allclose(Ypl, Yseq, rtol=0, atol=1e-7)
