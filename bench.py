@@ -72,6 +72,8 @@ def parse(argv=None):
     p.add_argument("--inner-tol", type=float, default=None)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-fp64", action="store_true",
+                   help="skip the pure-FP64 run of the same workload")
     p.add_argument("--sweep", action="store_true",
                    help="also time one solve per (s, precision) for s=1..16")
     p.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -532,6 +534,11 @@ def main():
             dist.destroy_process_group()
         return
 
+    # ---------------------------------------- the same workload in pure FP64
+    fp64 = None
+    if args.precision != "fp64" and not args.no_fp64:
+        fp64 = fp64_variant(P, case, args, stream)
+
     hbm_peak, peak_kind = measured_peaks()
     total_prof = sum(f["ms"] for f in fams.values()) or 1.0
     dominant = max((k for k in fams if k not in ("vec",)), key=lambda k: fams[k]["ms"])
@@ -562,6 +569,7 @@ def main():
                        "restarts": stats[-1]["restarts"]},
         "converged": converged, "max_col_relres": max(max(st["col_relres"]) for st in stats),
         "setup": {"first_step_s": setup_s, "precond_setup_ms": st0.setup_ms},
+        "fp64": fp64,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(), "impl": "pint",
     }
@@ -572,6 +580,37 @@ def main():
     P.pint_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def fp64_variant(P, case, args, stream):
+    """Time the same step with the FP64 inner solve (one warm-up, then up to
+    two timed steps): the "mixed vs FP64" half of the metric."""
+    import torch
+    prec0, tol0 = case.o.precision, case.o.inner_tol
+    case.o.precision = P.PINT_FP64
+    ns = argparse.Namespace(**vars(args))
+    ns.precision = "fp64"
+    case.o.inner_tol = inner_tol_for(ns, case.s)
+    try:
+        case.step()
+        k = max(1, min(2, args.steps))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sts = [case.step().as_dict(case.s) for _ in range(k)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        return {"value": case.time_steps * case.n / (ms / 1e3), "unit": UNIT,
+                "ms_per_step": ms, "steps": k, "inner_tol": case.o.inner_tol,
+                "outer": sts[-1]["outer_its"], "inner": sts[-1]["inner_its"],
+                "converged": all(x["status"] == 0 for x in sts),
+                "max_col_relres": max(max(x["col_relres"]) for x in sts)}
+    except Exception as e:              # report, do not hide
+        return {"value": None, "error": str(e)[:300]}
+    finally:
+        case.o.precision, case.o.inner_tol = prec0, tol0
 
 
 def sweep(P, ctx, args, w0):
