@@ -53,7 +53,7 @@ WORKLOADS = {
                   "steps (Algorithm 1), Newton + block GMRES(30)+{pc}"),
     "richards": (96, 8, "ilu0", "fp32",
                  "3-D Richards {n}^3, van Genuchten alpha=1 n=2, K_S=exp(2g) correlated 8 "
-                 "cells, implicit Euler tau=1/96 window s=8 pipelined over 16 steps, Newton + "
+                 "cells, implicit Euler tau=1/96 window s=8 pipelined over 8 steps, L-scheme + "
                  "block GMRES(30)+{pc}"),
 }
 
@@ -93,6 +93,8 @@ def linear(args):
 def inner_tol_for(args, s):
     if args.inner_tol is not None:
         return args.inner_tol
+    if args.workload == "richards":
+        return 1e-2       # L-scheme: linear outer convergence, loose inner solves suffice
     if not linear(args):
         return 1e-5 if args.precision == "fp64" else 1e-4     # Sec. 4.2: 1e-5
     if s > 1:
@@ -101,7 +103,7 @@ def inner_tol_for(args, s):
 
 
 def nl_stages(args):
-    return 8 if args.workload == "diffreact" else 16
+    return 8          # diffreact: 4 SDIRK2 steps; richards: 8 implicit-Euler steps
 
 
 # ----------------------------------------------------------------- oracle
@@ -150,7 +152,7 @@ def oracle_sample(args, n, reps=1):
     G = nl_stages(args)
     for _ in range(reps):
         t = time.perf_counter()
-        newton.pipelined_block_newton(prob, A, c, 1.0 / 96.0, -z, G, s, tol=1e-5, inner_tol=1e-5,
+        newton.pipelined_block_newton(prob, A, c, 1.0 / 96.0, -z, G, s, tol=1e-5, inner_tol=1e-2,
                                       precond=args.precond, max_step=1.0, max_newton=150,
                                       lscheme_L=vg.lipschitz())
         times.append(time.perf_counter() - t)
@@ -482,8 +484,8 @@ def main():
         torch.cuda.synchronize()
 
     # ---------------------------------------------------------- timed region
-    P.pint_profile_reset(ctx)
-    P.pint_profile_enable(ctx, True)
+    # K steps with the profiler off give `value`; K more steps with the
+    # library's per-family CUDA-event profiler on give the roofline table
     l0 = P.pint_kernel_launches(ctx)
     stats = []
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -497,14 +499,26 @@ def main():
         barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
     launches = P.pint_kernel_launches(ctx) - l0
-    P.pint_profile_enable(ctx, False)
-    fams = {name: P.pint_profile_read(ctx, k) for k, name in enumerate(P.KERNEL_FAMILIES)}
     if dist is not None:
         t = torch.tensor([elapsed_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms = float(t.item())
     value = world * args.steps * case.time_steps * case.n / (elapsed_ms / 1e3)
     converged = all(st["status"] == 0 for st in stats)
+
+    P.pint_profile_reset(ctx)
+    P.pint_profile_enable(ctx, True)
+    barrier()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        case.step()
+    p1.record(stream)
+    barrier()
+    profiled_ms = p0.elapsed_time(p1) / args.steps
+    P.pint_profile_enable(ctx, False)
+    fams = {name: P.pint_profile_read(ctx, k) for k, name in enumerate(P.KERNEL_FAMILIES)}
 
     # ------------------------------------------------------------- e2e leg
     e2e = None
@@ -564,7 +578,7 @@ def main():
                              wl_name),
         "spmm_roofline": roofline("spmm", fams["spmm"], hbm_peak, peak_kind, args.precision,
                                   wl_name),
-        "kernels": kernels,
+        "kernels": kernels, "profiled_ms_per_step": profiled_ms,
         "iterations": {"outer": stats[-1]["outer_its"], "inner": stats[-1]["inner_its"],
                        "restarts": stats[-1]["restarts"]},
         "converged": converged, "max_col_relres": max(max(st["col_relres"]) for st in stats),

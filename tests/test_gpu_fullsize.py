@@ -151,7 +151,7 @@ def test_gram_and_update_full_size_sampled(P, ctx, prec):
 @pytest.mark.parametrize("workload", ["diffreact", "richards"])
 def test_pipeline_full_size_stage_equations(P, ctx, workload):
     """Algorithm 1 as the bench runs it (512^2 SDIRK2 window s = 2 over 8
-    stages; 96^3 implicit Euler window s = 8 over 16 steps): every stored
+    stages; 96^3 implicit Euler window s = 8 over 8 steps): every stored
     stage satisfies its sequential stage equation, recomputed by the oracle
     from the stored stages, to the outer tolerance relative to ||B0||."""
     case = bench.PipelineCase(P, ctx, bench.parse(["--workload", workload]))
