@@ -528,7 +528,9 @@ k_ilu_pencil(TileGeom g, int s, const int* __restrict__ rowptr, const int* __res
 }
 
 // Stencil-format copy of the factors: per row four coefficients,
-// FWD (L): (-z, -y, -x, 0); BWD (U): (+x, +y, +z, diag); absent neighbours 0.
+// FWD (L): (-z, -y, -x, 0); BWD (U): (+x, +y, +z, 1/diag); absent
+// neighbours 0. The reciprocal (rounded once, in float64) turns the
+// backward sweep's division into a multiplication.
 template <typename VT>
 __global__ void k_ilu_stencil_coefs(TileGeom g, int64_t n, const int* __restrict__ rowptr,
                                     const int* __restrict__ diagpos, const double* __restrict__ F,
@@ -546,7 +548,7 @@ __global__ void k_ilu_stencil_coefs(TileGeom g, int64_t n, const int* __restrict
   if (i + 1 < g.nx) u[0] = F[p++];
   if (j + 1 < g.ny) u[1] = F[p++];
   if (k + 1 < g.nz) u[2] = F[p++];
-  u[3] = F[d];
+  u[3] = 1.0 / F[d];
   for (int q = 0; q < 3; ++q) L4[4 * r + q] = (VT)l[q];
   L4[4 * r + 3] = VT(0);
   for (int q = 0; q < 4; ++q) U4[4 * r + q] = (VT)u[q];
@@ -637,6 +639,13 @@ k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
           }
         }
       }
+      // prefetch the next tile of the row now: its loads are in flight while
+      // this tile waits, computes and publishes
+      if (it + 1 < g.NTX) {
+        const int In = FWD ? it + 1 : g.NTX - 2 - it;
+        const int xn = In * TX;
+        fetch(xn, min(TX, g.nx - xn), xn + (int64_t)g.nx * gj + sxy * gk, mine);
+      }
       // upstream rows: FWD (J-1, K), (J, K-1); BWD (J+1, K), (J, K+1)
       if (threadIdx.x < 2 && ok) {
         int nt = -1;
@@ -691,30 +700,40 @@ k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
             acc -= cf[0] * vx;
             acc -= cf[1] * vy;
             acc -= cf[2] * vz;
-            acc /= cf[3];
+            acc *= cf[3];
           }
           Ys[cell * s + c] = acc;
         }
         __syncthreads();
       }
+      // Publish first what the downstream rows read: the pencils of the
+      // last y row and the last z layer of the tile (FWD; the first ones
+      // BWD). The release then waits only for those stores; the interior
+      // stores and the next tile's loads are issued after it.
+      const bool face = mine && (FWD ? ((lj == ey - 1 && J + 1 < g.NTY) || (lk == ez - 1 && K + 1 < NTZ))
+                                     : ((lj == 0 && J > 0) || (lk == 0 && K > 0)));
+      VT zv[TX];
       if (mine) {
         hx = Ys[(cellb + (FWD ? ex - 1 : 0)) * s + c];
 #pragma unroll
+        for (int li = 0; li < TX; ++li) zv[li] = li < ex ? Ys[(cellb + li) * s + c] : VT(0);
+      }
+      if (face) {
+#pragma unroll
         for (int li = 0; li < TX; ++li)
-          if (li < ex) Z[(lbase + li) * s + c] = Ys[(cellb + li) * s + c];
+          if (li < ex) Z[(lbase + li) * s + c] = zv[li];
       }
-      // prefetch the next tile of the row while this one is published
-      if (it + 1 < g.NTX) {
-        const int In = FWD ? it + 1 : g.NTX - 2 - it;
-        const int xn = In * TX;
-        fetch(xn, min(TX, g.nx - xn), xn + (int64_t)g.nx * gj + sxy * gk, mine);
-      }
-      // publish: every store of the CTA happens-before thread 0's fence and
-      // release through the barrier
+      // every face store of the CTA happens-before thread 0's fence and
+      // release through the barrier (which also ends all reads of Ys)
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
         st_release(tflags + tile, epoch);
+      }
+      if (mine && !face) {
+#pragma unroll
+        for (int li = 0; li < TX; ++li)
+          if (li < ex) Z[(lbase + li) * s + c] = zv[li];
       }
     }
   }
@@ -772,9 +791,10 @@ static Sched& schedule(pint_op op, bool forward, int rpw) {
   return cache.emplace(rpw, sc).first->second;
 }
 
-static unsigned next_epoch(pint_op op, unsigned& e, unsigned* flags, cudaStream_t st) {
+static unsigned next_epoch(pint_op op, unsigned& e, unsigned* flags, cudaStream_t st,
+                           int64_t count = -1) {
   if (e >= 0xFFFFFF00u) {
-    PINT_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned) * op->n, st));
+    PINT_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned) * (count < 0 ? op->n : count), st));
     e = 0;
   }
   return ++e;
@@ -1014,8 +1034,8 @@ static void apply_tiled(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_
   // 16x16x8 tiles when a block row (s values) fits in 32 bytes
   const bool big = S->ts[1].valid && sizeof(VT) * op->s <= 32;
   IluState::TileSet& T = S->ts[big ? 1 : 0];
-  const unsigned ef = next_epoch(op, T.tepoch_f, T.tflag_f, st);
-  const unsigned eb = next_epoch(op, T.tepoch_b, T.tflag_b, st);
+  const unsigned ef = next_epoch(op, T.tepoch_f, T.tflag_f, st, T.ntiles);
+  const unsigned eb = next_epoch(op, T.tepoch_b, T.tflag_b, st, T.ntiles);
   PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
   ProfScope ps(op->ctx, PF_ILU,
                op->nnz * (sizeof(VT) + 4.0) + 4.0 * (op->n + 1) + 4.0 * op->n +
@@ -1041,8 +1061,8 @@ static void rows_pair(pint_op op, const VT* L4, const VT* U4, const VT* X, VT* Z
   constexpr int TR = TX * TY * TZ;
   const size_t smem = sizeof(VT) * ((size_t)TR * s + (size_t)TR * 4 + (size_t)TZ * TX * s +
                                     (size_t)TY * TX * s);
-  const unsigned ef = next_epoch(op, S->repoch_f, S->rflag_f, st);
-  const unsigned eb = next_epoch(op, S->repoch_b, S->rflag_b, st);
+  const unsigned ef = next_epoch(op, S->repoch_f, S->rflag_f, st, S->rntiles);
+  const unsigned eb = next_epoch(op, S->repoch_b, S->rflag_b, st, S->rntiles);
   PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
   ProfScope ps(op->ctx, PF_ILU,
                8.0 * sizeof(VT) * op->n + 4.0 * sizeof(VT) * op->n * s, 2.0 * op->nnz * s, st);

@@ -242,3 +242,28 @@ def test_ilu0_apply_1d_tiles(P, ctx):
         np.testing.assert_allclose(J @ Z.cpu().numpy(), X, rtol=1e-12, atol=1e-12)
     finally:
         P.pint_operator_destroy(op)
+
+
+@pytest.mark.parametrize("dims", [(24, 16, 32), (16, 48, 16)])
+@pytest.mark.parametrize("s", [1, 2, 3, 8])
+def test_ilu0_apply_f32_row_sweeps(P, ctx, dims, s):
+    """Float32 ILU(0) through the row-of-tiles sweep (several rows and tiles
+    per direction, published faces, reciprocal diagonal) against the oracle's
+    float64 ILU(0)."""
+    import torch
+    D, K, n = _problem(dims, 12)
+    v = (1.0, -0.5, 0.25)
+    op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), v)
+    try:
+        tau = 1e-3
+        P.pint_set_coupling(ctx, op, np.eye(s) / tau, np.eye(s))
+        J = sp.csr_matrix(sp.identity(n) / tau + K)
+        J.sort_indices()
+        X = synth.uniform(13, n * s).reshape(n, s).astype(np.float32)
+        Z = torch.empty(n, s, device="cuda", dtype=torch.float32)
+        P.pint_ilu0_apply_f32(ctx, op, _dev(X, torch.float32), Z)
+        ref = krylov.ilu0_apply(*krylov.ilu0(J))(X.astype(np.float64))
+        err = np.linalg.norm(Z.cpu().numpy().astype(np.float64) - ref, axis=0)
+        assert np.all(err <= 1e-5 * np.linalg.norm(ref, axis=0)), err / np.linalg.norm(ref, axis=0)
+    finally:
+        P.pint_operator_destroy(op)
