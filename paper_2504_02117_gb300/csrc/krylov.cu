@@ -30,7 +30,7 @@ template <typename VT, int S, bool EXACT, int NPT>
 __global__ void __launch_bounds__(256)
 k_gram(int64_t n, int s, int nb, const VT* __restrict__ V, int64_t bstride,
        const VT* __restrict__ W, int64_t rows_per_cta, double* __restrict__ partial) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   VT* T = reinterpret_cast<VT*>(smem_raw);
   const int P = nb * s;
   const int pitch = P + s;
@@ -469,7 +469,7 @@ template <typename VT, int S, bool EXACT, int MODE>
 __global__ void __launch_bounds__(256)
 k_update(int64_t n, int s, int nb, const VT* __restrict__ V, int64_t bstride,
          const double* __restrict__ H, VT* __restrict__ W) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   VT* Hs = reinterpret_cast<VT*>(smem_raw);
   const int P = nb * s;
   for (int e = threadIdx.x; e < P * S; e += blockDim.x) {
@@ -547,6 +547,7 @@ __global__ void k_chol(int s, const double* __restrict__ G, double defl, double*
   __shared__ double Gs[kMaxS][kMaxS + 1];
   __shared__ double Rs[kMaxS][kMaxS + 1];
   __shared__ double g0[kMaxS];
+  __shared__ double dinv[kMaxS];     // 1 / R[k][k] (0 when deflated)
   __shared__ int dead[kMaxS];
   const int t = threadIdx.x, i = t / kMaxS, j = t % kMaxS;
   if (i < s && j < s) {
@@ -562,10 +563,11 @@ __global__ void k_chol(int s, const double* __restrict__ G, double defl, double*
       const bool isdead = !(g0[k] > 0.0) || !(d > defl * g0[k]);
       dead[k] = isdead ? 1 : 0;
       piv = isdead ? 0.0 : sqrt(d);
+      dinv[k] = isdead ? 0.0 : 1.0 / piv;     // the one division of step k
       if (isdead && defl_count) atomicAdd(defl_count, 1);
     }
     __syncthreads();
-    if (t < s && t >= k) Rs[k][t] = dead[k] ? 0.0 : (t == k ? piv : Gs[k][t] / piv);
+    if (t < s && t >= k) Rs[k][t] = dead[k] ? 0.0 : (t == k ? piv : Gs[k][t] * dinv[k]);
     __syncthreads();
     if (i < s && j < s && i > k && j > k) Gs[i][j] -= Rs[k][i] * Rs[k][j];
     __syncthreads();
@@ -579,7 +581,7 @@ __global__ void k_chol(int s, const double* __restrict__ G, double defl, double*
       if (!dead[k]) {
         v = (t == k) ? 1.0 : 0.0;
         for (int c = 0; c < k; ++c) v -= row[c] * Rs[c][k];
-        v /= Rs[k][k];
+        v *= dinv[k];
       }
       row[k] = v;
     }
@@ -793,29 +795,43 @@ void cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W, double* R,
 
 // ---------------------------------------------- block Hessenberg (a8)
 // Column block j: [H1 + H2 ; Rn] ((j+2)s x s) -> apply the js earlier
-// reflectors, make s new reflectors of length s+1, rotate Gr, write the
-// per-column residual estimates and flag = {all converged, non-finite}.
-// One CTA of 512 threads; warp l owns column l.
-__global__ void __launch_bounds__(512)
-k_hess_step(int j, int s, int ldh, const double* __restrict__ H1, const double* __restrict__ H2,
-            const double* __restrict__ Rn, double* __restrict__ Hb, double* __restrict__ refl,
-            double* __restrict__ Gr, const double* __restrict__ target, double* __restrict__ est,
-            int* __restrict__ flag) {
-  extern __shared__ double col[];
-  __shared__ double vcur[32];
-  const int L = (j + 2) * s;
-  const int top = (j + 1) * s;
-  double* rs = col + s * L;          // earlier reflectors staged in shared memory
-  for (int idx = threadIdx.x; idx < s * L; idx += blockDim.x) {
-    const int l = idx / L, row = idx - l * L;
-    col[idx] = row < top ? H1[row * s + l] + H2[row * s + l] : Rn[(row - top) * s + l];
-  }
-  for (int idx = threadIdx.x; idx < j * s * kSmallLd; idx += blockDim.x) rs[idx] = refl[idx];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// reflectors (k_hess_old, one CTA per column: the columns are independent
+// and the float64 work of one SM is the limit), then make s new reflectors
+// of length s+1, rotate Gr, write the per-column residual estimates and
+// flag = {all converged, non-finite} (k_hess_step, one CTA).
+
+// sum over the lanes 0..15 (all others hold 0 or are not read)
+__device__ __forceinline__ double half_warp_sum(double v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// CTA l: column l of the block, staged with the earlier reflectors in shared
+// memory; lane r < s+1 holds row c + r of reflector c's window.
+__global__ void __launch_bounds__(32)
+k_hess_old(int j, int s, int ldh, const double* __restrict__ H1, const double* __restrict__ H2,
+           const double* __restrict__ Rn, double* __restrict__ Hb,
+           const double* __restrict__ refl) {
+  extern __shared__ double hs[];
+  const int l = blockIdx.x, lane = threadIdx.x;
+  const int L = (j + 2) * s, top = (j + 1) * s;
+  double* cl = hs;                   // the column, L rows
+  double* rs = hs + L;               // js reflectors, pitch kSmallLd
+  for (int row = lane; row < L; row += 32)
+    cl[row] = row < top ? H1[row * s + l] + H2[row * s + l] : Rn[(row - top) * s + l];
+  for (int idx = lane; idx < j * s * kSmallLd; idx += 32) rs[idx] = refl[idx];
+  __syncwarp();
   const bool act = lane <= s;
-  if (warp < s) {
-    double* cl = col + warp * L;
+  if (s < 16) {
+    for (int c = 0; c < j * s; ++c) {
+      const double v = act ? rs[c * kSmallLd + lane] : 0.0;
+      const double x = act ? cl[c + lane] : 0.0;
+      const double d = half_warp_sum(v * x);
+      if (act) cl[c + lane] = x - 2.0 * v * d;
+      __syncwarp();
+    }
+  } else {
     for (int c = 0; c < j * s; ++c) {
       const double v = act ? rs[c * kSmallLd + lane] : 0.0;
       const double x = act ? cl[c + lane] : 0.0;
@@ -824,7 +840,26 @@ k_hess_step(int j, int s, int ldh, const double* __restrict__ H1, const double* 
       __syncwarp();
     }
   }
+  for (int row = lane; row < L; row += 32) Hb[(int64_t)(j * s + l) * ldh + row] = cl[row];
+}
+
+// One CTA of 512 threads; warp l owns column l (already rotated by the
+// earlier reflectors, read from Hb).
+__global__ void __launch_bounds__(512)
+k_hess_step(int j, int s, int ldh, double* __restrict__ Hb, double* __restrict__ refl,
+            double* __restrict__ Gr, const double* __restrict__ target, double* __restrict__ est,
+            int* __restrict__ flag) {
+  extern __shared__ double col[];
+  __shared__ double vcur[32];
+  const int L = (j + 2) * s;
+  const int top = (j + 1) * s;
+  for (int idx = threadIdx.x; idx < s * L; idx += blockDim.x) {
+    const int l = idx / L, row = idx - l * L;
+    col[idx] = Hb[(int64_t)(j * s + l) * ldh + row];
+  }
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane <= s;
   for (int l = 0; l < s; ++l) {
     const int c = j * s + l;
     if (warp == l) {
@@ -1042,10 +1077,13 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
   PINT_CUDA(cudaMemsetAsync(w->defl, 0, 64, st));
   PINT_CUDA(cudaMemcpyAsync(Vb(0), w->Rs, es * ns, cudaMemcpyDeviceToDevice, st));
   InnerResult res{0, 0, false, 0};
-  const size_t hess_smem = 8 * ((size_t)s * (m + 1) * s + (size_t)m * s * kSmallLd);
+  const size_t hess_smem = 8 * (size_t)s * (m + 1) * s;
+  const size_t old_smem = 8 * ((size_t)(m + 1) * s + (size_t)m * s * kSmallLd);
   const size_t back_smem = 8 * (size_t)m * s * s;
   PINT_CUDA(cudaFuncSetAttribute(k_hess_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)hess_smem));
+  PINT_CUDA(cudaFuncSetAttribute(k_hess_old, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)old_smem));
   PINT_CUDA(cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)back_smem));
   while (res.its < o->max_inner) {
@@ -1072,10 +1110,13 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
       launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg2, Vb(j + 1), 0, st);
       cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, st, np);
       ProfScope psh(ctx, PF_HESS, 0.0, 4.0 * (j + 1) * s * s * (s + 1), st);
-      k_hess_step<<<1, 512, 8 * ((size_t)s * (j + 2) * s + (size_t)j * s * kSmallLd), st>>>(
-          j, s, ldh, w->Hg1, w->Hg2, w->Rn, w->Hb, w->refl, w->Gr, w->target, w->est, w->flag);
+      k_hess_old<<<s, 32, 8 * ((size_t)(j + 2) * s + (size_t)j * s * kSmallLd), st>>>(
+          j, s, ldh, w->Hg1, w->Hg2, w->Rn, w->Hb, w->refl);
+      check_launch("k_hess_old");
+      k_hess_step<<<1, 512, 8 * (size_t)s * (j + 2) * s, st>>>(j, s, ldh, w->Hb, w->refl, w->Gr,
+                                                             w->target, w->est, w->flag);
       check_launch("k_hess_step");
-      ctx->launches += 1;
+      ctx->launches += 2;
       res.its += 1;
       PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
       PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 2, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
