@@ -643,7 +643,8 @@ def sweep(P, ctx, args, w0):
             P.pint_set_coupling(ctx, op, (np.eye(s) - np.eye(s, k=-1)) / w.tau, np.eye(s))
             o = P.pint_opts_default()
             o.tol = w.tol
-            ns = argparse.Namespace(inner_tol=args.inner_tol, precision=prec_name)
+            ns = argparse.Namespace(**vars(args))
+            ns.precision = prec_name
             o.inner_tol = inner_tol_for(ns, s)
             o.precond = P.PINT_PC_ILU0
             o.precision = P.PINT_FP64 if prec_name == "fp64" else P.PINT_FP32
