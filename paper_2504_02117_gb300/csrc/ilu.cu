@@ -89,6 +89,21 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only) and its groups
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src_gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst_smem)),
+               "l"(src_gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// all committed groups but the most recent one have completed
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
 // Wait until flag == epoch. Returns false (and raises *err) when the budget
 // is exhausted, or at once when another thread has raised *err.
 __device__ __forceinline__ bool wait_ready(const unsigned* flag, unsigned epoch, int* err,
@@ -573,8 +588,8 @@ k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
   constexpr int TR = TX * TY * TZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   VT* Ys = reinterpret_cast<VT*>(smem_raw);        // [lk][lj][li][c]
-  VT* Cs = Ys + (size_t)TR * s;                     // [lk][lj][li][4]
-  VT* Hy = Cs + (size_t)TR * 4;                     // [lk][li][c]
+  VT* Cb = Ys + (size_t)TR * s;                     // 2 x [lk][lj][li][4]
+  VT* Hy = Cb + (size_t)2 * TR * 4;                 // [lk][li][c]
   VT* Hz = Hy + (size_t)TZ * TX * s;                // [lj][li][c]
   __shared__ int row_sh;
   const int c = threadIdx.x % s;
@@ -584,21 +599,33 @@ k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
   const int64_t sxy = (int64_t)g.nx * g.ny;
   const int NTZ = (g.nz + TZ - 1) / TZ;
   bool ok = true;
-  // this pencil's right-hand side and coefficients for one tile, loaded into
-  // registers with all loads in flight together (unrolled, guarded)
-  VT xv[TX], cv[TX][4];
+  // this pencil's right-hand side for one tile, loaded into registers with
+  // all loads in flight together (unrolled, guarded)
+  VT xv[TX];
   auto fetch = [&](int x0, int ex, int64_t lbase, bool mine) {
 #pragma unroll
     for (int li = 0; li < TX; ++li) {
       if (mine && li < ex) {
         const int64_t r = lbase + li;
         xv[li] = FWD ? X[r * s + c] : __ldcg(Z + r * s + c);
-        if (c == 0) {
-#pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4) cv[li][k4] = C4[4 * r + k4];
-        }
       }
     }
+  };
+  // the tile's coefficients: asynchronous 16-byte copies straight into one
+  // of two shared buffers, one commit group per tile
+  auto fetch_coefs = [&](int I, int y0, int z0, int ey, int ez, VT* dst) {
+    const int x0 = I * TX, ex = min(TX, g.nx - x0);
+    constexpr int CH = 4 * (int)sizeof(VT) / 16;     // 16-byte chunks per cell
+    for (int e = threadIdx.x; e < TR * CH; e += blockDim.x) {
+      const int cell = e / CH, part = e - cell * CH;
+      const int li = cell % TX, qq = cell / TX, ljj = qq % TY, lkk = qq / TY;
+      if (li < ex && ljj < ey && lkk < ez) {
+        const int64_t r = x0 + li + (int64_t)g.nx * (y0 + ljj) + sxy * (z0 + lkk);
+        cp_async16(dst + (size_t)cell * 4 + part * (16 / sizeof(VT)),
+                   C4 + 4 * r + part * (16 / sizeof(VT)));
+      }
+    }
+    cp_async_commit();
   };
   while (true) {
     if (threadIdx.x == 0) {
@@ -619,6 +646,7 @@ k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
       const int I = FWD ? 0 : g.NTX - 1;
       const int x0 = I * TX;
       fetch(x0, min(TX, g.nx - x0), x0 + (int64_t)g.nx * gj + sxy * gk, mine);
+      fetch_coefs(I, y0, z0, ey, ez, Cb);
     }
     for (int it = 0; it < g.NTX; ++it) {
       const int I = FWD ? it : g.NTX - 1 - it;
@@ -626,18 +654,12 @@ k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
       const int ex = min(TX, g.nx - x0);
       const int tile = I + g.NTX * (J + g.NTY * K);
       const int64_t lbase = x0 + (int64_t)g.nx * gj + sxy * gk;   // row of li = 0
+      const VT* Cs = Cb + (size_t)(it & 1) * TR * 4;
       // stage the prefetched pencil into shared memory
       if (mine) {
 #pragma unroll
-        for (int li = 0; li < TX; ++li) {
-          if (li < ex) {
-            Ys[(cellb + li) * s + c] = xv[li];
-            if (c == 0) {
-#pragma unroll
-              for (int k4 = 0; k4 < 4; ++k4) Cs[(cellb + li) * 4 + k4] = cv[li][k4];
-            }
-          }
-        }
+        for (int li = 0; li < TX; ++li)
+          if (li < ex) Ys[(cellb + li) * s + c] = xv[li];
       }
       // prefetch the next tile of the row now: its loads are in flight while
       // this tile waits, computes and publishes
@@ -645,7 +667,11 @@ k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
         const int In = FWD ? it + 1 : g.NTX - 2 - it;
         const int xn = In * TX;
         fetch(xn, min(TX, g.nx - xn), xn + (int64_t)g.nx * gj + sxy * gk, mine);
+        fetch_coefs(In, y0, z0, ey, ez, Cb + (size_t)((it + 1) & 1) * TR * 4);
+      } else {
+        cp_async_commit();                         // keep one group per tile
       }
+      cp_async_wait_prev();                        // this tile's coefficients have landed
       // upstream rows: FWD (J-1, K), (J, K-1); BWD (J+1, K), (J, K+1)
       if (threadIdx.x < 2 && ok) {
         int nt = -1;
@@ -1051,16 +1077,23 @@ static void apply_tiled(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_
   op->ctx->launches += 2;
 }
 
+// shared memory of k_ilu_rows: the tile (s values per cell), two coefficient
+// tiles and the y / z halos
+template <typename VT>
+static size_t rows_smem(int TX, int TY, int TZ, int s) {
+  const size_t TR = (size_t)TX * TY * TZ;
+  return sizeof(VT) * (TR * s + 2 * TR * 4 + (size_t)TZ * TX * s + (size_t)TY * TX * s);
+}
+
 template <typename VT, int TX, int TY, int TZ, int MAXT>
 static void rows_pair(pint_op op, const VT* L4, const VT* U4, const VT* X, VT* Z,
                       cudaStream_t st) {
   IluState* S = op->ilu;
   const int s = op->s;
-  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, S->RNTX, S->RNTY, S->rntiles};
+  const int NTX = (op->grid_nx + TX - 1) / TX;      // TX == S->RX
+  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, NTX, S->RNTY, NTX * S->RNTY * S->RNTZ};
   const int threads = TY * TZ * s;
-  constexpr int TR = TX * TY * TZ;
-  const size_t smem = sizeof(VT) * ((size_t)TR * s + (size_t)TR * 4 + (size_t)TZ * TX * s +
-                                    (size_t)TY * TX * s);
+  const size_t smem = rows_smem<VT>(TX, TY, TZ, s);
   const unsigned ef = next_epoch(op, S->repoch_f, S->rflag_f, st, S->rntiles);
   const unsigned eb = next_epoch(op, S->repoch_b, S->rflag_b, st, S->rntiles);
   PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
@@ -1094,7 +1127,8 @@ static void apply_rows(pint_op op, const VT* L4, const VT* U4, const VT* X, VT* 
 template <typename VT>
 static void apply_t(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st) {
   IluState* S = op->ilu;
-  if (S->rows && op->s * S->RY * S->RZ <= 1024) {
+  if (S->rows && op->s * S->RY * S->RZ <= 1024 &&
+      rows_smem<VT>(S->RX, S->RY, S->RZ, op->s) <= 227 * 1024) {
     if constexpr (sizeof(VT) == 8) apply_rows<double>(op, S->L4d, S->U4d, X, Z, st);
     else apply_rows<float>(op, S->L4f, S->U4f, X, Z, st);
     return;

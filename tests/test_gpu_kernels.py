@@ -244,7 +244,7 @@ def test_ilu0_apply_1d_tiles(P, ctx):
         P.pint_operator_destroy(op)
 
 
-@pytest.mark.parametrize("dims", [(24, 16, 32), (16, 48, 16)])
+@pytest.mark.parametrize("dims", [(24, 16, 32), (16, 48, 16), (40, 24, 17)])
 @pytest.mark.parametrize("s", [1, 2, 3, 8])
 def test_ilu0_apply_f32_row_sweeps(P, ctx, dims, s):
     """Float32 ILU(0) through the row-of-tiles sweep (several rows and tiles
