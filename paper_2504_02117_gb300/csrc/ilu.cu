@@ -1006,7 +1006,7 @@ static void tile_pair(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t 
   const size_t smem = sizeof(VT) * ((size_t)TR * s + (size_t)(TY * TZ + TX * TZ + TX * TY) * s +
                                     4 * (size_t)TR);
   auto launch = [&](auto kern, const VT* x, unsigned* flags, unsigned ep, int* ticket) {
-    PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    smem_attr(kern, smem);
     int per_sm = 0;
     PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
     const int grid = std::max(1, std::min(T.ntiles, std::max(1, per_sm) * op->ctx->num_sms));
@@ -1041,7 +1041,7 @@ static void pencil_pair(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_
   const int threads = TY * TZ * s;
   const size_t smem = sizeof(VT) * (size_t)TX * TY * TZ * s;
   auto launch = [&](auto kern, const VT* x, unsigned* flags, unsigned ep, int* ticket) {
-    PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    smem_attr(kern, smem);
     int per_sm = 0;
     PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int grid = std::max(1, std::min(T.ntiles, std::max(1, per_sm) * op->ctx->num_sms));
@@ -1100,7 +1100,7 @@ static void rows_pair(pint_op op, const VT* L4, const VT* U4, const VT* X, VT* Z
   ProfScope ps(op->ctx, PF_ILU,
                8.0 * sizeof(VT) * op->n + 4.0 * sizeof(VT) * op->n * s, 2.0 * op->nnz * s, st);
   auto launch = [&](auto kern, const VT* C, const VT* x, unsigned* flags, unsigned ep, int* tk) {
-    PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    smem_attr(kern, smem);
     int per_sm = 0;
     PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int grid = std::max(1, std::min(S->nrows, std::max(1, per_sm) * op->ctx->num_sms));

@@ -6,6 +6,9 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -246,6 +249,26 @@ namespace pint {
 
 // Records (when the context's profiler is on) a CUDA event pair around the
 // launches made in its scope and books algorithmic bytes / flops to `fam`.
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than was set before (per kernel and device): the attribute call is a host
+// round trip on every launch otherwise.
+inline void smem_attr_raw(const void* kern, size_t bytes) {
+  if (bytes <= 48 * 1024) return;                 // the default limit
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set;
+  int dev = 0;
+  PINT_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set[{kern, dev}];
+  if (bytes <= cur) return;
+  PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+}
+template <typename K>
+inline void smem_attr(K* kern, size_t bytes) {
+  smem_attr_raw(reinterpret_cast<const void*>(kern), bytes);
+}
+
 struct ProfScope {
   pint_ctx c;
   int fam;

@@ -399,7 +399,7 @@ static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V,
       return;
     }
     auto launch = [&](auto kern) {
-      PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      smem_attr(kern, smem);
       kern<<<nblk, NT, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, TRG, ctx->d_partial,
                                    ctx->d_flag);
     };
@@ -439,7 +439,7 @@ static void gram_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t 
     constexpr int S = decltype(S_)::value;
     constexpr bool EX = decltype(E_)::value;
     auto launch = [&](auto kern) {
-      PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      smem_attr(kern, smem);
       kern<<<nblk, 256, smem, st>>>(n, s, nb, V, bstride, W, rpc, ctx->d_partial);
     };
     if (npt == 1) launch(k_gram<VT, S, EX, 1>);
@@ -519,7 +519,7 @@ static void update_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_
     const unsigned g = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>(4LL * ctx->num_sms, (n + 255) / 256));
     auto launch = [&](auto kern) {
-      PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      smem_attr(kern, smem);
       kern<<<g, 256, smem, st>>>(n, s, nb, V, bstride, H, W);
     };
     if (mode == 0) launch(k_update<VT, S, EX, 0>);
@@ -1080,12 +1080,35 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
   const size_t hess_smem = 8 * (size_t)s * (m + 1) * s;
   const size_t old_smem = 8 * ((size_t)(m + 1) * s + (size_t)m * s * kSmallLd);
   const size_t back_smem = 8 * (size_t)m * s * s;
-  PINT_CUDA(cudaFuncSetAttribute(k_hess_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)hess_smem));
-  PINT_CUDA(cudaFuncSetAttribute(k_hess_old, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)old_smem));
-  PINT_CUDA(cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)back_smem));
+  smem_attr(k_hess_step, hess_smem);
+  smem_attr(k_hess_old, old_smem);
+  smem_attr(k_backsolve, back_smem);
+  // One Arnoldi step: W = J P^-1 V_j, BCGS2 against V_0..V_j, CholQR2, the
+  // Hessenberg column block and the flags copied to the host.
+  auto arnoldi_step = [&](int j, cudaStream_t sx) {
+    if (ilu) {
+      ilu_apply(op, prec, Vb(j), w->Zt, sx);
+      launch_inner_spmm(op, prec, false, w->Zt, Vb(j + 1), nullptr, sx);
+    } else {
+      launch_inner_spmm(op, prec, jac, Vb(j), Vb(j + 1), nullptr, sx);
+    }
+    launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg1, sx, np);
+    launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg1, Vb(j + 1), 0, sx);
+    launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg2, sx, np);
+    launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg2, Vb(j + 1), 0, sx);
+    cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, sx, np);
+    ProfScope psh(ctx, PF_HESS, 0.0, 4.0 * (j + 1) * s * s * (s + 1), sx);
+    k_hess_old<<<s, 32, 8 * ((size_t)(j + 2) * s + (size_t)j * s * kSmallLd), sx>>>(
+        j, s, ldh, w->Hg1, w->Hg2, w->Rn, w->Hb, w->refl);
+    check_launch("k_hess_old");
+    k_hess_step<<<1, 512, 8 * (size_t)s * (j + 2) * s, sx>>>(j, s, ldh, w->Hb, w->refl, w->Gr,
+                                                            w->target, w->est, w->flag);
+    check_launch("k_hess_step");
+    ctx->launches += 2;
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, sx));
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 2, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                              sx));
+  };
   while (res.its < o->max_inner) {
     res.cycles += 1;
     cholqr2(ctx, vprec, n, s, Vb(0), w->S, w->defl, st, np);
@@ -1098,28 +1121,8 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
     int j = 0;
     bool conv = false;
     for (j = 0; j < m; ++j) {
-      if (ilu) {
-        ilu_apply(op, prec, Vb(j), w->Zt, st);
-        launch_inner_spmm(op, prec, false, w->Zt, Vb(j + 1), nullptr, st);
-      } else {
-        launch_inner_spmm(op, prec, jac, Vb(j), Vb(j + 1), nullptr, st);
-      }
-      launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg1, st, np);
-      launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg1, Vb(j + 1), 0, st);
-      launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg2, st, np);
-      launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg2, Vb(j + 1), 0, st);
-      cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, st, np);
-      ProfScope psh(ctx, PF_HESS, 0.0, 4.0 * (j + 1) * s * s * (s + 1), st);
-      k_hess_old<<<s, 32, 8 * ((size_t)(j + 2) * s + (size_t)j * s * kSmallLd), st>>>(
-          j, s, ldh, w->Hg1, w->Hg2, w->Rn, w->Hb, w->refl);
-      check_launch("k_hess_old");
-      k_hess_step<<<1, 512, 8 * (size_t)s * (j + 2) * s, st>>>(j, s, ldh, w->Hb, w->refl, w->Gr,
-                                                             w->target, w->est, w->flag);
-      check_launch("k_hess_step");
-      ctx->launches += 2;
+      arnoldi_step(j, st);
       res.its += 1;
-      PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-      PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 2, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
       PINT_CUDA(cudaStreamSynchronize(st));
       PINT_REQUIRE(ctx->h_flag[2] == 0, PINT_ERR_TIMEOUT,
                    "bulk-copy wait in the Gram kernel exceeded its time budget");
@@ -1338,7 +1341,7 @@ static void gram_noalloc_t(const NoAllocDevice& d, int64_t n, int s, int nb, con
     constexpr int S = decltype(S_)::value;
     constexpr bool EX = decltype(E_)::value;
     auto launch = [&](auto kern) {
-      PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      smem_attr(kern, smem);
       kern<<<nblk, 256, smem, st>>>(n, s, nb, V, n * s, W, rpc, d.scratch);
     };
     if (npt == 1) launch(k_gram<VT, S, EX, 1>);
