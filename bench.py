@@ -427,6 +427,22 @@ class PipelineCase:
 
 
 # ------------------------------------------------------------------ main
+def max_over_ranks(ms, dist=None, device="cuda"):
+    """The slowest rank's time (every rank gets it); `ms` itself on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, time_steps, cells, ms):
+    """Whole-job time-step*DOF/s of `world` independent replicas, each
+    solving `steps` slabs of `time_steps` steps on `cells` cells in `ms`."""
+    return world * steps * time_steps * cells / (ms / 1e3)
+
+
 def main():
     args = parse()
     if args.oracle_sample:
@@ -497,13 +513,9 @@ def main():
             stats.append(case.step().as_dict(case.s))
         ev1.record(stream)
         barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     launches = P.pint_kernel_launches(ctx) - l0
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * args.steps * case.time_steps * case.n / (elapsed_ms / 1e3)
+    value = replica_throughput(world, args.steps, case.time_steps, case.n, elapsed_ms)
     converged = all(st["status"] == 0 for st in stats)
 
     P.pint_profile_reset(ctx)
@@ -532,12 +544,8 @@ def main():
             case.e2e_step()
         e1.record(stream)
         barrier()
-        e_ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * args.steps * case.time_steps * case.n / (e_ms / 1e3),
+        e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        e2e = {"value": replica_throughput(world, args.steps, case.time_steps, case.n, e_ms),
                "unit": UNIT, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
                "ms_per_step": e_ms / args.steps}
 
