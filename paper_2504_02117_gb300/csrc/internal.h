@@ -328,7 +328,9 @@ void launch_colnorm(pint_ctx ctx, int precision, int64_t n, int s, const void* X
 // Y -= diag(scale) * Dinv? * V  (float64 Y; V float64 or float32)
 void launch_outer_update(int precision, int64_t n, int s, double* Y, const void* V,
                          const double* colscale, const double* rowscale, cudaStream_t st,
-                         pint_ctx ctx);
+                         pint_ctx ctx, int ys = 0, int yoff = 0);
+void launch_gather_cols(int64_t n, int s, int c0, int w, const double* src, double* dst,
+                        cudaStream_t st, pint_ctx ctx);
 // dst(float32) = src(float64) * 1/colscale[k]
 void launch_scale_cast(int64_t n, int s, const double* src, float* dst,
                        const double* inv_colscale, cudaStream_t st, pint_ctx ctx);

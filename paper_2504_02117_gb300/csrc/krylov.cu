@@ -966,6 +966,7 @@ struct KrylovWork {
   void* Xk = nullptr;    // n*s Krylov solution
   void* Rs = nullptr;    // n*s scaled inner right-hand side
   double* R64 = nullptr; // n*s outer residual
+  double* Rsub = nullptr; // n*s trailing columns of R64 (narrowed inner solves)
   double* Hg1 = nullptr;
   double* Hg2 = nullptr;
   double* Rn = nullptr;
@@ -1002,7 +1003,7 @@ void free_work(pint_op op) {
 static KrylovWork* ensure_work(pint_op op, int prec, int m) {
   const int s = op->s;
   KrylovWork* w = op->work;
-  if (w && w->n == op->n && w->s == s && w->m >= m && w->prec == prec) return w;
+  if (w && w->n == op->n && w->s >= s && w->m >= m && w->prec == prec) return w;
   free_work(op);
   w = new KrylovWork();
   op->work = w;
@@ -1025,6 +1026,7 @@ static KrylovWork* ensure_work(pint_op op, int prec, int m) {
     w->Xk = walloc(ctx, w, w->es * ns);
     w->Rs = walloc(ctx, w, w->es * ns);
     w->R64 = (double*)walloc(ctx, w, 8 * ns);
+    w->Rsub = (double*)walloc(ctx, w, 8 * ns);
     const size_t rows = (size_t)(m + 1) * s;
     w->Hg1 = (double*)walloc(ctx, w, 8 * rows * s);
     w->Hg2 = (double*)walloc(ctx, w, 8 * rows * s);
@@ -1073,6 +1075,9 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
     for (int k = 0; k < s; ++k) t[k] = o->inner_tol;
     PINT_CUDA(cudaMemcpyAsync(w->target, t, 8 * s, cudaMemcpyHostToDevice, st));
   }
+  if (s < w->s && np > n)     // narrower than the allocation: rows n..n_pad of a
+    for (int b = 0; b <= m; ++b)  // block now overlap old data; the Gram tiles read them
+      PINT_CUDA(cudaMemsetAsync((char*)Vb(b) + es * (size_t)ns, 0, es * (size_t)(np - n) * s, st));
   PINT_CUDA(cudaMemsetAsync(w->Xk, 0, es * ns, st));
   PINT_CUDA(cudaMemsetAsync(w->defl, 0, 64, st));
   PINT_CUDA(cudaMemcpyAsync(Vb(0), w->Rs, es * ns, cudaMemcpyDeviceToDevice, st));
@@ -1240,6 +1245,10 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
   PINT_CUDA(cudaMemcpyAsync(ctx->h_small, w->fnorm, 8 * s, cudaMemcpyDeviceToHost, st));
   PINT_CUDA(cudaStreamSynchronize(st));
   for (int k = 0; k < s; ++k) fn[k] = ctx->h_small[k];
+  bool lower = true;                 // both coupling matrices lower triangular
+  for (int i = 0; i < s; ++i)
+    for (int k = i + 1; k < s; ++k)
+      if (op->A1[i * kMaxS + k] != 0.0 || op->A2[i * kMaxS + k] != 0.0) lower = false;
   int status = PINT_ERR_NOT_CONVERGED;
   int outer = 0, inner = 0, cycles = 0, defl = 0;
   for (outer = 0; outer <= o->max_outer; ++outer) {
@@ -1265,13 +1274,39 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
       break;
     }
     if (outer == o->max_outer) break;
-    InnerResult ir = inner_solve(op, o, w->R64, w->rnorm, nullptr, st);
+    // With lower-triangular A1, A2 the residual of column k depends on
+    // columns 0..k of Y only, so a converged leading run of columns stays
+    // converged: the inner solve is narrowed to the trailing columns
+    // (power-of-two width, so that the kernels keep their exact-width forms;
+    // the few converged columns it still carries are harmless).
+    int c0 = 0;
+    if (lower) {
+      int lead = 0;
+      while (lead < s && rn[lead] <= (fn[lead] > 0.0 ? o->tol * fn[lead] : o->tol)) ++lead;
+      int wdt = 1;
+      while (wdt < s - lead) wdt <<= 1;
+      if (wdt < s) c0 = s - wdt;
+    }
+    const int sw = s - c0;
+    InnerResult ir;
+    if (c0 == 0) {
+      ir = inner_solve(op, o, w->R64, w->rnorm, nullptr, st);
+    } else {
+      launch_gather_cols(n, s, c0, sw, w->R64, w->Rsub, st, ctx);
+      struct WidthGuard {
+        pint_op op;
+        int s0;
+        ~WidthGuard() { op->s = s0; }
+      } guard{op, s};
+      op->s = sw;
+      ir = inner_solve(op, o, w->Rsub, w->rnorm + c0, nullptr, st);
+    }
     inner += ir.its;
     cycles += ir.cycles;
     defl += ir.deflations;
     const int vprec = w->prec;
-    launch_outer_update(vprec, n, s, Y, w->Xk, w->rnorm,
-                        o->precond == PINT_PC_JACOBI ? op->Jinvdiag : nullptr, st, ctx);
+    launch_outer_update(vprec, n, sw, Y, w->Xk, w->rnorm + c0,
+                        o->precond == PINT_PC_JACOBI ? op->Jinvdiag : nullptr, st, ctx, s, c0);
   }
   PINT_CUDA(cudaStreamSynchronize(st));
   if (stats) {

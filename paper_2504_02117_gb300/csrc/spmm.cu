@@ -385,10 +385,10 @@ void launch_colnorm(pint_ctx ctx, int precision, int64_t n, int s, const void* X
 }
 
 // ---------------------------------------------------- outer update (a10)
-// Y[r][k] -= colscale[k] * rowscale[r] * V[r][k]
+// Y[r][yoff + k] -= colscale[k] * rowscale[r] * V[r][k]  (V: n x s, Y: n x ys)
 template <typename VT>
-__global__ void k_outer_update(int64_t n, int s, double* __restrict__ Y, const VT* __restrict__ V,
-                               const double* __restrict__ colscale,
+__global__ void k_outer_update(int64_t n, int s, double* __restrict__ Y, int ys, int yoff,
+                               const VT* __restrict__ V, const double* __restrict__ colscale,
                                const double* __restrict__ rowscale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * s) return;
@@ -396,20 +396,40 @@ __global__ void k_outer_update(int64_t n, int s, double* __restrict__ Y, const V
   const int k = (int)(i - r * s);
   double v = (double)V[i] * colscale[k];
   if (rowscale) v *= rowscale[r];
-  Y[i] -= v;
+  Y[r * ys + yoff + k] -= v;
 }
 
 void launch_outer_update(int precision, int64_t n, int s, double* Y, const void* V,
                          const double* colscale, const double* rowscale, cudaStream_t st,
-                         pint_ctx ctx) {
+                         pint_ctx ctx, int ys, int yoff) {
   const unsigned g = grid_for(n * s, 256);
+  if (ys <= 0) ys = s;
   ProfScope ps(ctx, PF_VEC, (16.0 + (precision == PINT_FP64 ? 8.0 : 4.0)) * n * s +
                                 (rowscale ? 8.0 * n : 0.0), 3.0 * n * s, st);
   if (precision == PINT_FP64)
-    k_outer_update<double><<<g, 256, 0, st>>>(n, s, Y, (const double*)V, colscale, rowscale);
+    k_outer_update<double><<<g, 256, 0, st>>>(n, s, Y, ys, yoff, (const double*)V, colscale,
+                                              rowscale);
   else
-    k_outer_update<float><<<g, 256, 0, st>>>(n, s, Y, (const float*)V, colscale, rowscale);
+    k_outer_update<float><<<g, 256, 0, st>>>(n, s, Y, ys, yoff, (const float*)V, colscale,
+                                             rowscale);
   check_launch("k_outer_update");
+  ctx->launches += 1;
+}
+
+// dst (n x w) = columns c0 .. c0 + w - 1 of src (n x s), float64
+__global__ void k_gather_cols(int64_t n, int s, int c0, int w, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * w) return;
+  const int64_t r = i / w;
+  dst[i] = src[r * s + c0 + (int)(i - r * w)];
+}
+
+void launch_gather_cols(int64_t n, int s, int c0, int w, const double* src, double* dst,
+                        cudaStream_t st, pint_ctx ctx) {
+  ProfScope ps(ctx, PF_VEC, 16.0 * n * w, 0.0, st);
+  k_gather_cols<<<grid_for(n * w, 256), 256, 0, st>>>(n, s, c0, w, src, dst);
+  check_launch("k_gather_cols");
   ctx->launches += 1;
 }
 

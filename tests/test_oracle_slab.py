@@ -144,3 +144,29 @@ def test_planted_transpose_in_coupling_is_caught(monkeypatch):
     Y, info = slab.slab_solve(K, Md, A1, A2, Bst, B0, tol=1e-12, exact_inner=True,
                               max_outer=30)
     assert not np.allclose(Y, Yseq, rtol=1e-6)
+
+
+def test_narrowed_inner_solves_keep_the_solution_and_iterations():
+    """Leaving converged leading columns out of the inner solve (lower
+    triangular coupling) reaches the same slab solution with fewer
+    column-steps (Arnoldi steps times block width), at most one more outer
+    iteration, and every column meets the tolerance."""
+    rng = np.random.default_rng(21)
+    dims = (10, 9, 1)
+    n, s = 90, 8
+    K = fv.convdiff_matrix(dims, np.exp(rng.standard_normal(dims[::-1])), (1.0, 0.5, 0.0))
+    tau = 1e-2
+    A1 = (np.eye(s) - np.eye(s, k=-1)) / tau
+    A2 = np.eye(s)
+    B = rng.uniform(-1, 1, (n, s))
+    Y0, i0 = slab.slab_solve(K, np.ones(n), A1, A2, B, tol=1e-12, inner_tol=1e-2,
+                             precond="ilu0")
+    Y1, i1 = slab.slab_solve(K, np.ones(n), A1, A2, B, tol=1e-12, inner_tol=1e-2,
+                             precond="ilu0", narrow=True)
+    assert i0["converged"] and i1["converged"]
+    assert i1["outer"] <= i0["outer"] + 1
+    assert i1["column_steps"] < i0["column_steps"]
+    np.testing.assert_allclose(Y1, Y0, rtol=0, atol=1e-9 * np.abs(Y0).max())
+    R = slab.coupled_residual(K, np.ones(n), A1, A2, Y1, B)
+    F = slab.rhs_F(A2, B)
+    assert np.all(np.linalg.norm(R, axis=0) <= 1e-12 * np.linalg.norm(F, axis=0))
