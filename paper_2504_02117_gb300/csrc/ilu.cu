@@ -45,19 +45,6 @@ struct IluState {
   int* d_order_f = nullptr;
   int* d_order_b = nullptr;
   std::map<int, Sched> sched_f, sched_b;   // by rows per chunk
-  // tiled sweeps for natural-order 5/7-point stencils: ts[0] the default
-  // shape, ts[1] (3-D only) 16x16x8 tiles for rows of at most 32 bytes
-  bool tiled = false;
-  struct TileSet {
-    bool valid = false;
-    int TX = 0, TY = 0, TZ = 0, NTX = 0, NTY = 0, NTZ = 0, ntiles = 0, nlev = 0;
-    int* tile_order = nullptr;      // tiles by ascending tile level
-    int* loc_list = nullptr;        // local rows of a full tile by local level
-    int* loc_lvlptr = nullptr;
-    unsigned* tflag_f = nullptr;
-    unsigned* tflag_b = nullptr;
-    unsigned tepoch_f = 0, tepoch_b = 0;
-  } ts[2];
   // row-of-tiles sweeps (stencil operators): tile shape, row order, flags,
   // stencil-format factors L4 / U4 ([n][4], float64 and float32)
   bool rows = false;
@@ -221,326 +208,13 @@ k_ilu_sweep(int s, int sp_log2, const int* __restrict__ rowptr, const int* __res
   }
 }
 
-// ---------------------------------------------------- tiled stencil sweep
+// ------------------------------------------------ stencil (grid) sweeps
 // For the natural-order 7-point (5-point in 2-D) stencil, row (i,j,k) reads
-// only (i-1,j,k), (i,j-1,k), (i,j,k-1) forward and the +1 neighbours backward.
-// A CTA owns a TX x TY x TZ tile: it prefetches the tile's coefficients and
-// right-hand sides, waits (bounded) for the flags of the three upstream
-// tiles, loads their faces into shared memory and sweeps its local levels
-// li+lj+lk with __syncthreads only, then publishes one flag for the tile.
-// Tiles are taken from an atomic ticket in tile-level order, so a CTA only
-// waits for tiles with lower tickets, taken by running CTAs. The arithmetic
-// per row and column is the same as the CSR sweep (same operands, same order).
+// only (i-1,j,k), (i,j-1,k), (i,j,k-1) forward and the +1 neighbours
+// backward; the sweeps below work on tiles of the grid.
 struct TileGeom {
   int nx, ny, nz, NTX, NTY, ntiles;
 };
-
-__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
-
-// TX, TY, TZ: tile shape (powers of two); S: block width when it is a power
-// of two (shifts), 0 for a runtime s (divisions).
-template <typename VT, bool FWD, int TX, int TY, int TZ, int S>
-__global__ void __launch_bounds__(256)
-k_ilu_tile(TileGeom g, int s_rt, const int* __restrict__ rowptr, const int* __restrict__ diagpos,
-           const VT* __restrict__ F, const VT* X, VT* Z, const int* __restrict__ tile_order,
-           const int* __restrict__ loc_list_g, const int* __restrict__ loc_lvlptr_g,
-           unsigned* tflags, unsigned epoch, int* ticket, int* err) {
-  constexpr int TR = TX * TY * TZ;
-  constexpr int NLEV = TX + TY + TZ - 2;
-  constexpr int LX = ilog2c(TX), LXY = ilog2c(TX * TY);
-  constexpr int LS = S > 0 ? ilog2c(S) : 0;
-  const int s = S > 0 ? S : s_rt;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  VT* Ys = reinterpret_cast<VT*>(smem_raw);                 // TR x s
-  VT* Hx = Ys + (size_t)TR * s;                              // TY*TZ x s
-  VT* Hy = Hx + (size_t)TY * TZ * s;                         // TX*TZ x s
-  VT* Hz = Hy + (size_t)TX * TZ * s;                         // TX*TY x s
-  VT* C = Hz + (size_t)TX * TY * s;                          // TR x 4 coefficients
-  __shared__ short loc[TR];
-  __shared__ short lvp[NLEV + 1];
-  __shared__ int tile_sh;
-  for (int i = threadIdx.x; i < TR; i += blockDim.x) loc[i] = (short)loc_list_g[i];
-  for (int i = threadIdx.x; i <= NLEV; i += blockDim.x) lvp[i] = (short)loc_lvlptr_g[i];
-  auto div_s = [&](int e) { return S > 0 ? (e >> LS) : e / s; };
-  auto mod_s = [&](int e) { return S > 0 ? (e & (S - 1)) : e % s; };
-  const unsigned long long deadline = globaltimer() + kWaitBudgetNs;
-  const int64_t sxy = (int64_t)g.nx * g.ny;
-  bool ok = true;
-  while (true) {
-    if (threadIdx.x == 0) {
-      const int t = atomicAdd(ticket, 1);
-      tile_sh = t < g.ntiles ? tile_order[FWD ? t : g.ntiles - 1 - t] : -1;
-    }
-    __syncthreads();
-    const int tile = tile_sh;
-    if (tile < 0) return;
-    const int I = tile % g.NTX, J = (tile / g.NTX) % g.NTY, K = tile / (g.NTX * g.NTY);
-    const int x0 = I * TX, y0 = J * TY, z0 = K * TZ;
-    const int ex = min(TX, g.nx - x0), ey = min(TY, g.ny - y0), ez = min(TZ, g.nz - z0);
-    const int64_t base = x0 + (int64_t)g.nx * y0 + sxy * z0;
-    // prefetch coefficients and right-hand sides (before waiting)
-    for (int l = threadIdx.x; l < TR; l += blockDim.x) {
-      const int li = l & (TX - 1), lj = (l >> LX) & (TY - 1), lk = l >> LXY;
-      if (li >= ex || lj >= ey || lk >= ez) continue;
-      const int gi = x0 + li, gj = y0 + lj, gk = z0 + lk;
-      const int64_t r = base + li + (int64_t)g.nx * lj + sxy * lk;
-      const int d = diagpos[r];
-      VT c0 = VT(0), c1 = VT(0), c2 = VT(0);
-      if (FWD) {
-        int p = rowptr[r];
-        if (gk > 0) c0 = F[p++];      // -z
-        if (gj > 0) c1 = F[p++];      // -y
-        if (gi > 0) c2 = F[p++];      // -x
-      } else {
-        int p = d + 1;
-        if (gi + 1 < g.nx) c0 = F[p++];   // +x
-        if (gj + 1 < g.ny) c1 = F[p++];   // +y
-        if (gk + 1 < g.nz) c2 = F[p++];   // +z
-      }
-      C[4 * l + 0] = c0;
-      C[4 * l + 1] = c1;
-      C[4 * l + 2] = c2;
-      C[4 * l + 3] = F[d];
-    }
-    for (int e = threadIdx.x; e < TR * s; e += blockDim.x) {
-      const int l = div_s(e), c = mod_s(e);
-      const int li = l & (TX - 1), lj = (l >> LX) & (TY - 1), lk = l >> LXY;
-      if (li >= ex || lj >= ey || lk >= ez) continue;
-      const int64_t r = base + li + (int64_t)g.nx * lj + sxy * lk;
-      Ys[e] = FWD ? X[r * s + c] : __ldcg(Z + r * s + c);
-    }
-    // upstream tiles: FWD -x,-y,-z ; BWD +x,+y,+z
-    if (threadIdx.x < 3 && ok) {
-      int nt = -1;
-      if (FWD) {
-        if (threadIdx.x == 0 && I > 0) nt = tile - 1;
-        if (threadIdx.x == 1 && J > 0) nt = tile - g.NTX;
-        if (threadIdx.x == 2 && K > 0) nt = tile - g.NTX * g.NTY;
-      } else {
-        if (threadIdx.x == 0 && x0 + ex < g.nx) nt = tile + 1;
-        if (threadIdx.x == 1 && y0 + ey < g.ny) nt = tile + g.NTX;
-        if (threadIdx.x == 2 && z0 + ez < g.nz) nt = tile + g.NTX * g.NTY;
-      }
-      if (nt >= 0) ok = wait_ready(tflags + nt, epoch, err, deadline);
-    }
-    __syncthreads();
-    // faces of the upstream tiles (zero where the grid ends)
-    const int hx = FWD ? x0 - 1 : x0 + ex, hy = FWD ? y0 - 1 : y0 + ey, hz = FWD ? z0 - 1 : z0 + ez;
-    const bool hxv = hx >= 0 && hx < g.nx, hyv = hy >= 0 && hy < g.ny, hzv = hz >= 0 && hz < g.nz;
-    for (int e = threadIdx.x; e < TY * TZ * s; e += blockDim.x) {
-      const int c = mod_s(e), q = div_s(e), lj = q & (TY - 1), lk = q >> ilog2c(TY);
-      VT v = VT(0);
-      if (hxv && lj < ey && lk < ez)
-        v = __ldcg(Z + (hx + (int64_t)g.nx * (y0 + lj) + sxy * (z0 + lk)) * s + c);
-      Hx[e] = v;
-    }
-    for (int e = threadIdx.x; e < TX * TZ * s; e += blockDim.x) {
-      const int c = mod_s(e), q = div_s(e), li = q & (TX - 1), lk = q >> LX;
-      VT v = VT(0);
-      if (hyv && li < ex && lk < ez)
-        v = __ldcg(Z + (x0 + li + (int64_t)g.nx * hy + sxy * (z0 + lk)) * s + c);
-      Hy[e] = v;
-    }
-    for (int e = threadIdx.x; e < TX * TY * s; e += blockDim.x) {
-      const int c = mod_s(e), q = div_s(e), li = q & (TX - 1), lj = q >> LX;
-      VT v = VT(0);
-      if (hzv && li < ex && lj < ey)
-        v = __ldcg(Z + (x0 + li + (int64_t)g.nx * (y0 + lj) + sxy * hz) * s + c);
-      Hz[e] = v;
-    }
-    __syncthreads();
-    // local wavefront over li + lj + lk
-    for (int it = 0; it < NLEV; ++it) {
-      const int lv = FWD ? it : NLEV - 1 - it;
-      const int b = lvp[lv], cnt = lvp[lv + 1] - b;
-      for (int e = threadIdx.x; e < cnt * s; e += blockDim.x) {
-        const int l = loc[b + div_s(e)], c = mod_s(e);
-        const int li = l & (TX - 1), lj = (l >> LX) & (TY - 1), lk = l >> LXY;
-        if (li >= ex || lj >= ey || lk >= ez) continue;
-        VT acc = Ys[l * s + c];
-        if (FWD) {
-          const VT vz = lk > 0 ? Ys[(l - TX * TY) * s + c] : Hz[(li + TX * lj) * s + c];
-          const VT vy = lj > 0 ? Ys[(l - TX) * s + c] : Hy[(li + TX * lk) * s + c];
-          const VT vx = li > 0 ? Ys[(l - 1) * s + c] : Hx[(lj + TY * lk) * s + c];
-          acc -= C[4 * l + 0] * vz;
-          acc -= C[4 * l + 1] * vy;
-          acc -= C[4 * l + 2] * vx;
-        } else {
-          const VT vx = li + 1 < ex ? Ys[(l + 1) * s + c] : Hx[(lj + TY * lk) * s + c];
-          const VT vy = lj + 1 < ey ? Ys[(l + TX) * s + c] : Hy[(li + TX * lk) * s + c];
-          const VT vz = lk + 1 < ez ? Ys[(l + TX * TY) * s + c] : Hz[(li + TX * lj) * s + c];
-          acc -= C[4 * l + 0] * vx;
-          acc -= C[4 * l + 1] * vy;
-          acc -= C[4 * l + 2] * vz;
-          acc /= C[4 * l + 3];
-        }
-        Ys[l * s + c] = acc;
-      }
-      __syncthreads();
-    }
-    for (int e = threadIdx.x; e < TR * s; e += blockDim.x) {
-      const int l = div_s(e), c = mod_s(e);
-      const int li = l & (TX - 1), lj = (l >> LX) & (TY - 1), lk = l >> LXY;
-      if (li >= ex || lj >= ey || lk >= ez) continue;
-      Z[(base + li + (int64_t)g.nx * lj + sxy * lk) * s + c] = Ys[e];
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) st_release(tflags + tile, epoch);
-  }
-}
-
-// Pencil variant of the tiled sweep (s <= 8): thread (c, lj, lk) owns the
-// x-line of column c at (lj, lk) of the tile and keeps its TX values, their
-// coefficients and its halo values in registers. Step t of the local
-// wavefront handles cell li = t - lj - lk (forward; mirrored backward): the
-// x-neighbour is in the thread's own registers, the y- and z-neighbours are
-// read from the shared tile written one step earlier. Same operands, same
-// order of operations per cell as the CSR sweep.
-template <typename VT, bool FWD, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(512, 1)
-k_ilu_pencil(TileGeom g, int s, const int* __restrict__ rowptr, const int* __restrict__ diagpos,
-             const VT* __restrict__ F, const VT* X, VT* Z, const int* __restrict__ tile_order,
-             unsigned* tflags, unsigned epoch, int* ticket, int* err) {
-  constexpr int NSTEP = TX + TY + TZ - 2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  VT* Ys = reinterpret_cast<VT*>(smem_raw);     // [lk][lj][li][c]
-  __shared__ int tile_sh;
-  const int c = threadIdx.x % s;
-  const int q = threadIdx.x / s;
-  const int lj = q % TY, lk = q / TY;
-  const unsigned long long deadline = globaltimer() + kWaitBudgetNs;
-  const int64_t sxy = (int64_t)g.nx * g.ny;
-  auto sidx = [&](int li_, int lj_, int lk_) { return ((lk_ * TY + lj_) * TX + li_) * s + c; };
-  bool ok = true;
-  while (true) {
-    if (threadIdx.x == 0) {
-      const int t = atomicAdd(ticket, 1);
-      tile_sh = t < g.ntiles ? tile_order[FWD ? t : g.ntiles - 1 - t] : -1;
-    }
-    __syncthreads();
-    const int tile = tile_sh;
-    if (tile < 0) return;
-    const int I = tile % g.NTX, J = (tile / g.NTX) % g.NTY, K = tile / (g.NTX * g.NTY);
-    const int x0 = I * TX, y0 = J * TY, z0 = K * TZ;
-    const int ex = min(TX, g.nx - x0), ey = min(TY, g.ny - y0), ez = min(TZ, g.nz - z0);
-    const bool mine = lj < ey && lk < ez;
-    const int gj = y0 + lj, gk = z0 + lk;
-    const int64_t lbase = x0 + (int64_t)g.nx * gj + sxy * gk;   // row of li = 0
-    VT y[TX], c0[TX], c1[TX], c2[TX], cd[TX];
-    // prefetch the line's coefficients and right-hand side (before waiting)
-#pragma unroll
-    for (int li = 0; li < TX; ++li) {
-      y[li] = c0[li] = c1[li] = c2[li] = VT(0);
-      cd[li] = VT(1);
-      if (mine && li < ex) {
-        const int64_t r = lbase + li;
-        const int gi = x0 + li;
-        const int d = diagpos[r];
-        if (FWD) {
-          int p = rowptr[r];
-          if (gk > 0) c0[li] = F[p++];      // -z
-          if (gj > 0) c1[li] = F[p++];      // -y
-          if (gi > 0) c2[li] = F[p++];      // -x
-          y[li] = X[r * s + c];
-        } else {
-          int p = d + 1;
-          if (gi + 1 < g.nx) c0[li] = F[p++];   // +x
-          if (gj + 1 < g.ny) c1[li] = F[p++];   // +y
-          if (gk + 1 < g.nz) c2[li] = F[p++];   // +z
-          cd[li] = F[d];
-          y[li] = __ldcg(Z + r * s + c);
-        }
-      }
-    }
-    if (threadIdx.x < 3 && ok) {
-      int nt = -1;
-      if (FWD) {
-        if (threadIdx.x == 0 && I > 0) nt = tile - 1;
-        if (threadIdx.x == 1 && J > 0) nt = tile - g.NTX;
-        if (threadIdx.x == 2 && K > 0) nt = tile - g.NTX * g.NTY;
-      } else {
-        if (threadIdx.x == 0 && x0 + ex < g.nx) nt = tile + 1;
-        if (threadIdx.x == 1 && y0 + ey < g.ny) nt = tile + g.NTX;
-        if (threadIdx.x == 2 && z0 + ez < g.nz) nt = tile + g.NTX * g.NTY;
-      }
-      if (nt >= 0) ok = wait_ready(tflags + nt, epoch, err, deadline);
-    }
-    __syncthreads();
-    // halo values from the upstream tiles (zero where the grid ends)
-    VT hx = VT(0), hy[TX], hz[TX];
-#pragma unroll
-    for (int li = 0; li < TX; ++li) hy[li] = hz[li] = VT(0);
-    if (mine) {
-      if (FWD) {
-        if (x0 > 0) hx = __ldcg(Z + (lbase - 1) * s + c);
-        if (lj == 0 && gj > 0) {
-#pragma unroll
-          for (int li = 0; li < TX; ++li)
-            if (li < ex) hy[li] = __ldcg(Z + (lbase + li - g.nx) * s + c);
-        }
-        if (lk == 0 && gk > 0) {
-#pragma unroll
-          for (int li = 0; li < TX; ++li)
-            if (li < ex) hz[li] = __ldcg(Z + (lbase + li - sxy) * s + c);
-        }
-      } else {
-        if (x0 + ex < g.nx) hx = __ldcg(Z + (lbase + ex) * s + c);
-        if (lj == ey - 1 && gj + 1 < g.ny) {
-#pragma unroll
-          for (int li = 0; li < TX; ++li)
-            if (li < ex) hy[li] = __ldcg(Z + (lbase + li + g.nx) * s + c);
-        }
-        if (lk == ez - 1 && gk + 1 < g.nz) {
-#pragma unroll
-          for (int li = 0; li < TX; ++li)
-            if (li < ex) hz[li] = __ldcg(Z + (lbase + li + sxy) * s + c);
-        }
-      }
-    }
-    // local wavefront
-    for (int t = 0; t < NSTEP; ++t) {
-      if (mine) {
-        // forward: li = t - lj - lk ; backward: mirrored coordinates
-        const int d = FWD ? t - lj - lk : t - (ey - 1 - lj) - (ez - 1 - lk);
-#pragma unroll
-        for (int li = 0; li < TX; ++li) {
-          const int want = FWD ? li : ex - 1 - li;
-          if (d == want && li < ex) {
-            VT acc = y[li];
-            if (FWD) {
-              const VT vz = lk > 0 ? Ys[sidx(li, lj, lk - 1)] : hz[li];
-              const VT vy = lj > 0 ? Ys[sidx(li, lj - 1, lk)] : hy[li];
-              const VT vx = li > 0 ? y[li > 0 ? li - 1 : 0] : hx;
-              acc -= c0[li] * vz;
-              acc -= c1[li] * vy;
-              acc -= c2[li] * vx;
-            } else {
-              const VT vx = li + 1 < ex ? y[li + 1 < TX ? li + 1 : li] : hx;
-              const VT vy = lj + 1 < ey ? Ys[sidx(li, lj + 1, lk)] : hy[li];
-              const VT vz = lk + 1 < ez ? Ys[sidx(li, lj, lk + 1)] : hz[li];
-              acc -= c0[li] * vx;
-              acc -= c1[li] * vy;
-              acc -= c2[li] * vz;
-              acc /= cd[li];
-            }
-            y[li] = acc;
-            Ys[sidx(li, lj, lk)] = acc;
-          }
-        }
-      }
-      __syncthreads();
-    }
-    if (mine) {
-#pragma unroll
-      for (int li = 0; li < TX; ++li)
-        if (li < ex) Z[(lbase + li) * s + c] = y[li];
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) st_release(tflags + tile, epoch);
-  }
-}
 
 // Stencil-format copy of the factors: per row four coefficients,
 // FWD (L): (-z, -y, -x, 0); BWD (U): (+x, +y, +z, 1/diag); absent
@@ -848,45 +522,6 @@ static void ensure_state(pint_op op) {
   PINT_CUDA(cudaMemset(S->err, 0, 2 * sizeof(int)));
   if (op->grid_nx > 0) {
     const int nx = op->grid_nx, ny = op->grid_ny, nz = op->grid_nz;
-    auto build = [&](IluState::TileSet& T, int TX, int TY, int TZ) {
-      T.TX = TX;
-      T.TY = TY;
-      T.TZ = TZ;
-      T.NTX = (nx + TX - 1) / TX;
-      T.NTY = (ny + TY - 1) / TY;
-      T.NTZ = (nz + TZ - 1) / TZ;
-      T.ntiles = T.NTX * T.NTY * T.NTZ;
-      T.nlev = TX + TY + TZ - 2;
-      std::vector<int> order(T.ntiles), loc(TX * TY * TZ), ptr(T.nlev + 1, 0);
-      for (int t = 0; t < T.ntiles; ++t) order[t] = t;
-      auto tlev = [&](int t) { return t % T.NTX + (t / T.NTX) % T.NTY + t / (T.NTX * T.NTY); };
-      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tlev(a) < tlev(b); });
-      const int TR = (int)loc.size();
-      auto llev = [&](int l) { return l % TX + (l / TX) % TY + l / (TX * TY); };
-      for (int l = 0; l < TR; ++l) ptr[llev(l) + 1]++;
-      for (int v = 0; v < T.nlev; ++v) ptr[v + 1] += ptr[v];
-      std::vector<int> pos(ptr.begin(), ptr.end() - 1);
-      for (int l = 0; l < TR; ++l) loc[pos[llev(l)]++] = l;
-      T.tile_order = dalloc_n<int>(ctx, T.ntiles);
-      T.loc_list = dalloc_n<int>(ctx, TR);
-      T.loc_lvlptr = dalloc_n<int>(ctx, T.nlev + 1);
-      T.tflag_f = dalloc_n<unsigned>(ctx, T.ntiles);
-      T.tflag_b = dalloc_n<unsigned>(ctx, T.ntiles);
-      PINT_CUDA(cudaMemcpy(T.tile_order, order.data(), sizeof(int) * T.ntiles, cudaMemcpyHostToDevice));
-      PINT_CUDA(cudaMemcpy(T.loc_list, loc.data(), sizeof(int) * TR, cudaMemcpyHostToDevice));
-      PINT_CUDA(cudaMemcpy(T.loc_lvlptr, ptr.data(), sizeof(int) * (T.nlev + 1), cudaMemcpyHostToDevice));
-      PINT_CUDA(cudaMemset(T.tflag_f, 0, sizeof(unsigned) * T.ntiles));
-      PINT_CUDA(cudaMemset(T.tflag_b, 0, sizeof(unsigned) * T.ntiles));
-      T.valid = true;
-    };
-    if (nz > 1) {
-      build(S->ts[0], 8, 8, 8);     // 16x16x8 tiles measured slower at 128^3
-    } else if (ny > 1) {
-      build(S->ts[0], 16, 16, 1);
-    } else {
-      build(S->ts[0], 64, 1, 1);
-    }
-    S->tiled = true;
     // row-of-tiles structures
     S->RX = nz > 1 ? 8 : (ny > 1 ? 16 : 64);
     S->RY = nz > 1 ? 8 : (ny > 1 ? 8 : 1);
@@ -943,14 +578,6 @@ void ilu_destroy(pint_op op) {
     dfree(c, S->L4f, sizeof(float) * 4 * op->n);
     dfree(c, S->U4f, sizeof(float) * 4 * op->n);
   }
-  for (auto& T : S->ts)
-    if (T.valid) {
-      dfree(c, T.tile_order, sizeof(int) * T.ntiles);
-      dfree(c, T.loc_list, sizeof(int) * T.TX * T.TY * T.TZ);
-      dfree(c, T.loc_lvlptr, sizeof(int) * (T.nlev + 1));
-      dfree(c, T.tflag_f, sizeof(unsigned) * T.ntiles);
-      dfree(c, T.tflag_b, sizeof(unsigned) * T.ntiles);
-    }
   delete S;
   op->ilu = nullptr;
 }
@@ -994,87 +621,6 @@ void ilu_setup(pint_op op, cudaStream_t st) {
   PINT_CUDA(cudaStreamSynchronize(st));
   ilu_check(op);
   S->factored = true;
-}
-
-template <typename VT, int TX, int TY, int TZ, int S>
-static void tile_pair(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st, unsigned ef,
-                      unsigned eb, IluState::TileSet& T) {
-  IluState* Sx = op->ilu;
-  const int s = op->s;
-  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, T.NTX, T.NTY, T.ntiles};
-  constexpr int TR = TX * TY * TZ;
-  const size_t smem = sizeof(VT) * ((size_t)TR * s + (size_t)(TY * TZ + TX * TZ + TX * TY) * s +
-                                    4 * (size_t)TR);
-  auto launch = [&](auto kern, const VT* x, unsigned* flags, unsigned ep, int* ticket) {
-    smem_attr(kern, smem);
-    int per_sm = 0;
-    PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
-    const int grid = std::max(1, std::min(T.ntiles, std::max(1, per_sm) * op->ctx->num_sms));
-    kern<<<grid, 256, smem, st>>>(g, s, op->rowptr, op->diagpos, F, x, Z, T.tile_order,
-                                  T.loc_list, T.loc_lvlptr, flags, ep, ticket, Sx->err);
-  };
-  launch(k_ilu_tile<VT, true, TX, TY, TZ, S>, X, T.tflag_f, ef, Sx->ticket);
-  check_launch("k_ilu_tile<fwd>");
-  launch(k_ilu_tile<VT, false, TX, TY, TZ, S>, Z, T.tflag_b, eb, Sx->ticket + 1);
-  check_launch("k_ilu_tile<bwd>");
-}
-
-template <typename VT, int TX, int TY, int TZ>
-static void tile_pair_s(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st, unsigned ef,
-                        unsigned eb, IluState::TileSet& T) {
-  switch (op->s) {
-    case 1: tile_pair<VT, TX, TY, TZ, 1>(op, F, X, Z, st, ef, eb, T); break;
-    case 2: tile_pair<VT, TX, TY, TZ, 2>(op, F, X, Z, st, ef, eb, T); break;
-    case 4: tile_pair<VT, TX, TY, TZ, 4>(op, F, X, Z, st, ef, eb, T); break;
-    case 8: tile_pair<VT, TX, TY, TZ, 8>(op, F, X, Z, st, ef, eb, T); break;
-    case 16: tile_pair<VT, TX, TY, TZ, 16>(op, F, X, Z, st, ef, eb, T); break;
-    default: tile_pair<VT, TX, TY, TZ, 0>(op, F, X, Z, st, ef, eb, T); break;
-  }
-}
-
-template <typename VT, int TX, int TY, int TZ>
-static void pencil_pair(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st, unsigned ef,
-                        unsigned eb, IluState::TileSet& T) {
-  IluState* Sx = op->ilu;
-  const int s = op->s;
-  TileGeom g{op->grid_nx, op->grid_ny, op->grid_nz, T.NTX, T.NTY, T.ntiles};
-  const int threads = TY * TZ * s;
-  const size_t smem = sizeof(VT) * (size_t)TX * TY * TZ * s;
-  auto launch = [&](auto kern, const VT* x, unsigned* flags, unsigned ep, int* ticket) {
-    smem_attr(kern, smem);
-    int per_sm = 0;
-    PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-    const int grid = std::max(1, std::min(T.ntiles, std::max(1, per_sm) * op->ctx->num_sms));
-    kern<<<grid, threads, smem, st>>>(g, s, op->rowptr, op->diagpos, F, x, Z, T.tile_order, flags,
-                                      ep, ticket, Sx->err);
-  };
-  launch(k_ilu_pencil<VT, true, TX, TY, TZ>, X, T.tflag_f, ef, Sx->ticket);
-  check_launch("k_ilu_pencil<fwd>");
-  launch(k_ilu_pencil<VT, false, TX, TY, TZ>, Z, T.tflag_b, eb, Sx->ticket + 1);
-  check_launch("k_ilu_pencil<bwd>");
-}
-
-template <typename VT>
-static void apply_tiled(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st) {
-  IluState* S = op->ilu;
-  // 16x16x8 tiles when a block row (s values) fits in 32 bytes
-  const bool big = S->ts[1].valid && sizeof(VT) * op->s <= 32;
-  IluState::TileSet& T = S->ts[big ? 1 : 0];
-  const unsigned ef = next_epoch(op, T.tepoch_f, T.tflag_f, st, T.ntiles);
-  const unsigned eb = next_epoch(op, T.tepoch_b, T.tflag_b, st, T.ntiles);
-  PINT_CUDA(cudaMemsetAsync(S->ticket, 0, 2 * sizeof(int), st));
-  ProfScope ps(op->ctx, PF_ILU,
-               op->nnz * (sizeof(VT) + 4.0) + 4.0 * (op->n + 1) + 4.0 * op->n +
-                   4.0 * sizeof(VT) * op->n * op->s,
-               2.0 * op->nnz * op->s, st);
-  if (big) tile_pair_s<VT, 16, 16, 8>(op, F, X, Z, st, ef, eb, T);
-  else if (T.TZ == 8 && op->s <= 8) pencil_pair<VT, 8, 8, 8>(op, F, X, Z, st, ef, eb, T);
-  else if (T.TY == 16 && op->s <= 8 && sizeof(VT) == 4)   // float64 16-wide lines spill
-    pencil_pair<VT, 16, 16, 1>(op, F, X, Z, st, ef, eb, T);
-  else if (T.TZ == 8) tile_pair_s<VT, 8, 8, 8>(op, F, X, Z, st, ef, eb, T);
-  else if (T.TY == 16) tile_pair_s<VT, 16, 16, 1>(op, F, X, Z, st, ef, eb, T);
-  else tile_pair_s<VT, 64, 1, 1>(op, F, X, Z, st, ef, eb, T);
-  op->ctx->launches += 2;
 }
 
 // shared memory of k_ilu_rows: the tile (s values per cell), two coefficient
@@ -1131,10 +677,6 @@ static void apply_t(pint_op op, const VT* F, const VT* X, VT* Z, cudaStream_t st
       rows_smem<VT>(S->RX, S->RY, S->RZ, op->s) <= 227 * 1024) {
     if constexpr (sizeof(VT) == 8) apply_rows<double>(op, S->L4d, S->U4d, X, Z, st);
     else apply_rows<float>(op, S->L4f, S->U4f, X, Z, st);
-    return;
-  }
-  if (S->tiled) {
-    apply_tiled<VT>(op, F, X, Z, st);
     return;
   }
   const int s = op->s;
