@@ -84,10 +84,11 @@ def parse(argv=None):
     a.s = a.s or ds
     a.precond = a.precond or dpc
     a.precision = a.precision or dprec
-    # Richards: the workload names no restart length; GMRES(30) stagnates on
-    # its L-scheme systems (67 restarts per solve at 96^3), GMRES(64) needs a
-    # fifth of the Arnoldi steps
-    a.restart = a.restart or (64 if a.workload == "richards" else 30)
+    # the nonlinear workloads name no restart length: GMRES(30) stagnates on
+    # the Richards L-scheme systems (67 restarts per solve at 96^3) and
+    # GMRES(64) needs a fifth of the Arnoldi steps there (and 11 % fewer for
+    # diffusion-reaction); the linear ones are GMRES(30)
+    a.restart = a.restart or (30 if linear(a) else 64)
     return a
 
 
@@ -144,7 +145,7 @@ def oracle_sample(args, n, reps=1):
         for _ in range(reps):
             t = time.perf_counter()
             newton.pipelined_block_newton(prob, A, c, tau, y0, G, s, tol=tol, inner_tol=1e-5,
-                                          precond=args.precond)
+                                          precond=args.precond, restart=args.restart)
             times.append(time.perf_counter() - t)
         return {"n": n * n, "steps": G // 2, "times": times}
     dims = (n, n, n)
