@@ -565,9 +565,11 @@ def main():
         return
 
     # ---------------------------------------- the same workload in pure FP64
-    fp64 = None
+    fp64 = bf16 = None
     if args.precision != "fp64" and not args.no_fp64:
-        fp64 = fp64_variant(P, case, args, stream)
+        fp64 = precision_variant(P, case, args, stream, "fp64")
+        if args.precision == "fp32":
+            bf16 = precision_variant(P, case, args, stream, "bf16")
 
     hbm_peak, peak_kind = measured_peaks()
     total_prof = sum(f["ms"] for f in fams.values()) or 1.0
@@ -599,7 +601,7 @@ def main():
                        "restarts": stats[-1]["restarts"]},
         "converged": converged, "max_col_relres": max(max(st["col_relres"]) for st in stats),
         "setup": {"first_step_s": setup_s, "precond_setup_ms": st0.setup_ms},
-        "fp64": fp64,
+        "fp64": fp64, "bf16": bf16,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(), "impl": "pint",
     }
@@ -612,14 +614,15 @@ def main():
         dist.destroy_process_group()
 
 
-def fp64_variant(P, case, args, stream):
-    """Time the same step with the FP64 inner solve (one warm-up, then up to
-    two timed steps): the "mixed vs FP64" half of the metric."""
+def precision_variant(P, case, args, stream, prec="fp64"):
+    """Time the same step with another inner-solve precision (one warm-up,
+    then up to two timed steps): FP64 is the "mixed vs FP64" half of the
+    metric, BF16 the bfloat16-matrix variant of the mixed path."""
     import torch
     prec0, tol0 = case.o.precision, case.o.inner_tol
-    case.o.precision = P.PINT_FP64
+    case.o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[prec]
     ns = argparse.Namespace(**vars(args))
-    ns.precision = "fp64"
+    ns.precision = prec
     case.o.inner_tol = inner_tol_for(ns, case.s)
     try:
         case.step()
