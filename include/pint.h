@@ -176,6 +176,10 @@ int pint_apply_coupled(pint_op op, const double* Y, const double* B,
  * block GMRES(m) inner solve on J = alpha M + beta K with right Jacobi or
  * ILU(0) preconditioning). Y: in = initial guess, out = solution. Stops when
  * every column satisfies ||R_k|| <= tol ||F_k|| (absolute tol if F_k = 0).
+ * When A1 and A2 are lower triangular, a converged leading run of columns
+ * stays converged (column k's residual depends on columns 0..k only): the
+ * inner solves then take only the trailing columns (a power-of-two count
+ * holding every unconverged one) and the leading ones are left as they are.
  * Synchronous. Returns PINT_ERR_NOT_CONVERGED (stats filled) at max_outer,
  * PINT_ERR_BREAKDOWN on a non-finite residual. */
 int pint_solve_block(pint_op op, const double* B, const double* B0, double* Y,
