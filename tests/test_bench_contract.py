@@ -1,0 +1,72 @@
+"""Host logic of bench.py that the JSON line rests on (CPU only): workload
+defaults, the roofline arithmetic and the DRAM-traffic lookup."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+@pytest.mark.parametrize("wl,n,s,pc,prec,restart", [
+    ("convdiff3d", 128, 8, "ilu0", "fp32", 30),
+    ("convdiff2d", 64, 4, "jacobi", "fp64", 30),
+    ("diffreact", 512, 2, "ilu0", "fp32", 64),
+    ("richards", 96, 8, "ilu0", "fp32", 64),
+])
+def test_workload_defaults(wl, n, s, pc, prec, restart):
+    a = bench.parse(["--workload", wl])
+    assert (a.n, a.s, a.precond, a.precision, a.restart) == (n, s, pc, prec, restart)
+    assert bench.linear(a) == wl.startswith("convdiff")
+    assert a.steps >= 1 and a.warmup >= 3 and a.gpus == 1
+
+
+def test_inner_tolerances_follow_the_paper():
+    a = bench.parse([])
+    assert bench.inner_tol_for(a, 8) == 1e-2            # Sec. 4.1, s > 1
+    a = bench.parse(["--workload", "diffreact", "--precision", "fp64"])
+    assert bench.inner_tol_for(a, 2) == 1e-5            # Sec. 4.2
+    a = bench.parse(["--workload", "richards"])
+    assert bench.inner_tol_for(a, 8) == 1e-2
+
+
+def test_roofline_hbm_and_alu_cases():
+    # 10 launches, 1 GB each, 100 us each -> 10 TB/s against a 5 TB/s peak
+    prof = {"ms": 1.0, "bytes": 10e9, "flops": 1e6, "launches": 10}
+    r = bench.roofline("spmm", prof, 5000.0, "measured", "fp32", "none")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(10000.0) and r["frac"] == pytest.approx(2.0)
+    assert r["algorithmic_bytes_per_launch"] == pytest.approx(1e9)
+    assert r["avg_launch_us"] == pytest.approx(100.0)
+    # float64 with more flop time than byte time: reported against the FP64 rate
+    prof = {"ms": 1.0, "bytes": 1e6, "flops": 1e9, "launches": 1}
+    r = bench.roofline("gram", prof, 5000.0, "measured", "fp64", "none")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(1.0) and r["peak"] == bench.FP64_PEAK_TFLOPS
+    assert bench.roofline("x", {"ms": 0.0, "bytes": 0, "flops": 0, "launches": 0}, 1, "m",
+                          "fp32", "w") is None
+
+
+def test_traffic_lookup_only_for_the_captured_sources():
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    with open(path) as fh:
+        d = json.load(fh)
+    for wl, fams in d.items():
+        for fam, e in fams.items():
+            got = bench.ncu_traffic(fam, wl)
+            if e["source_hash"] == bench.source_hash():
+                assert got == e["dram_bytes_per_launch"] and got > 0
+            else:
+                assert got is None
+    assert bench.ncu_traffic("ilu", "no-such-workload") is None
+
+
+def test_measured_peak_is_read():
+    peak, kind = bench.measured_peaks()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert kind == "measured" and peak > 1000.0
+    else:
+        assert (peak, kind) == (6800.0, "fallback")
