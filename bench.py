@@ -55,6 +55,10 @@ WORKLOADS = {
                  "3-D Richards {n}^3, van Genuchten alpha=1 n=2, K_S=exp(2g) correlated 8 "
                  "cells, implicit Euler tau=1/96 window s=8 pipelined over 8 steps, L-scheme + "
                  "block GMRES(30)+{pc}"),
+    "serve": (128, 16, "ilu0", "fp32",
+              "serving: seeded Poisson stream of slab-solve requests (3-D conv.-diffusion, "
+              "grids 32^3-{n}^3, s in 2..16, FP32 or FP64 inner solves, GMRES(30)+{pc}, "
+              "tol 1e-10), continuous batching over CUDA streams"),
 }
 
 
@@ -77,6 +81,9 @@ def parse(argv=None):
                    help="skip the pure-FP64 run of the same workload")
     p.add_argument("--sweep", action="store_true",
                    help="also time one solve per (s, precision) for s=1..16")
+    p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
+    p.add_argument("--rate", type=float, default=8.0, help="serve: mean arrivals per second")
+    p.add_argument("--slots", type=int, default=4, help="serve: concurrent solves")
     p.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     a = p.parse_args(argv)
     dn, ds, dpc, dprec, _ = WORKLOADS[a.workload]
@@ -93,7 +100,7 @@ def parse(argv=None):
 
 
 def linear(args):
-    return args.workload in ("convdiff3d", "convdiff2d")
+    return args.workload in ("convdiff3d", "convdiff2d", "serve")
 
 
 def inner_tol_for(args, s):
@@ -121,8 +128,10 @@ def oracle_sample(args, n, reps=1):
     from oracle import coupling, fv, newton, slab
     s = args.s
     times = []
-    if args.workload in ("convdiff3d", "convdiff2d"):
-        w = synth.convdiff_3d(n, s) if args.workload == "convdiff3d" else synth.convdiff_2d_64(s)
+    if args.workload in ("convdiff3d", "convdiff2d", "serve"):
+        if args.workload == "serve":
+            s = 4                     # a mid-size request of the stream
+        w = synth.convdiff_3d(n, s) if args.workload != "convdiff2d" else synth.convdiff_2d_64(s)
         if args.workload == "convdiff2d" and n != 64:
             w.dims = (n, n, 1)
         D = synth.diffusion_field(w)
@@ -166,11 +175,13 @@ def oracle_sample(args, n, reps=1):
 
 
 def oracle_sample_size(args):
-    return {"convdiff3d": 48, "convdiff2d": 64, "diffreact": 160, "richards": 20}[args.workload]
+    return {"convdiff3d": 48, "convdiff2d": 64, "diffreact": 160, "richards": 20,
+            "serve": 32}[args.workload]
 
 
 def reference_sample_size(args):
-    return {"convdiff3d": 32, "convdiff2d": 64, "diffreact": 64, "richards": 12}[args.workload]
+    return {"convdiff3d": 32, "convdiff2d": 64, "diffreact": 64, "richards": 12,
+            "serve": 32}[args.workload]
 
 
 def run_oracle_subprocess(args, n, reps):
@@ -483,6 +494,9 @@ def main():
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {e}"[:300]}
 
+    if args.workload == "serve":
+        return serve_main(args, world, rank, local, cpu, desc)
+
     import torch
     import paper_2504_02117_gb300 as P
 
@@ -687,6 +701,81 @@ def sweep(P, ctx, args, w0):
             P.pint_operator_destroy(op)
             del Bd, Y
     return res
+
+
+def serve_main(args, world, rank, local, cpu, desc):
+    """The serving workload: one seeded Poisson stream of slab-solve requests
+    per GPU through the continuous-batching loop; value = time steps x cells
+    of all completed requests / makespan. Every request's latency includes
+    the upload of its inputs and the download of its solution (e2e)."""
+    import torch
+    import synth
+    import paper_2504_02117_gb300 as P
+    from paper_2504_02117_gb300 import serve
+
+    torch.cuda.set_device(local)
+    cache = {}
+
+    def make(spec):
+        key = (spec["n"], spec["s"])
+        if key not in cache:            # the clients' data, seeded per shape
+            w = synth.convdiff_3d(spec["n"], spec["s"])
+            cache[key] = (w, synth.diffusion_field(w), synth.rhs_block(w))
+        w, D, B = cache[key]
+        ns = argparse.Namespace(**vars(args))
+        ns.precision = spec["precision"]
+        return serve.SlabRequest(rid=spec["rid"], arrival=spec["arrival"], dims=w.dims,
+                                 s=spec["s"], precision=spec["precision"], D=D, B=B,
+                                 velocity=w.velocity, tau=w.tau, tol=w.tol,
+                                 inner_tol=inner_tol_for(ns, spec["s"]), restart=args.restart)
+
+    grids = tuple(g for g in (32, 48, 64, 96, 128) if g <= args.n)
+    specs = synth.request_stream(5 + rank, args.requests, args.rate, grids=grids)
+    reqs = [make(sp) for sp in specs]
+    srv = serve.SlabServer(slots=args.slots, device=local, keep_results=True)
+    try:
+        warm = [make({"rid": -1 - i, "arrival": 0.0, "n": grids[0], "s": w, "precision": p})
+                for i, (w, p) in enumerate([(2, "fp32"), (4, "fp64"), (8, "fp32"), (16, "fp64")])]
+        srv.run(warm[:max(1, args.warmup)])
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            summ = srv.run(reqs)
+        launches = sum(int(P.pint_kernel_launches(c)) for c in srv._ctx if c is not None)
+    finally:
+        srv.close()
+    dist = None
+    if world > 1:                       # replicas: one stream per GPU, slowest rank's span
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    span = max_over_ranks(summ["makespan_s"], dist, "cuda")
+    if dist is not None:
+        dist.destroy_process_group()
+    done = [r for r in reqs if r.status == 0]
+    work = sum(r.s * r.cells for r in done)
+    value = world * work / span if span > 0 else None
+    if rank != 0:
+        return
+    h2d = sum(r.B.nbytes + r.D.nbytes for r in done)
+    d2h = sum(r.Y.nbytes for r in done if r.Y is not None)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1,
+        "warmup": args.warmup, "ms_per_step": span * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+fp32/f64", "data": "synthetic",
+        "config": {"workload": f"serve_{args.requests}req_rate{args.rate:g}_slots{args.slots}",
+                   "description": desc.format(n=args.n, pc=args.precond), "grids": list(grids),
+                   "widths": [2, 4, 8, 16], "precisions": ["fp32", "fp64"],
+                   "restart": args.restart, "parallelism": f"replicas x{world}",
+                   "l2": "mixed request sizes, no flush"},
+        "latency": {"p50_ms": 1e3 * summ["p50_latency_s"], "p99_ms": 1e3 * summ["p99_latency_s"],
+                    "p50_queue_ms": 1e3 * summ["p50_queue_s"],
+                    "p99_queue_ms": 1e3 * summ["p99_queue_s"]},
+        "serving": summ, "roofline": None,
+        "roofline_note": "per-kernel rooflines: the convdiff3d workload",
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches, "clocks": clk.summary(), "impl": "pint",
+    }
+    print(json.dumps(out), flush=True)
 
 
 def reference_arm(args, wl_name, desc, world):

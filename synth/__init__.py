@@ -165,3 +165,21 @@ def rhs_block(w: Workload, s: int | None = None) -> np.ndarray:
     iid U[-1,1]; column k of row r is element r*s + k of the stream."""
     s = w.s if s is None else s
     return uniform(w.seed_rhs, w.n * s).reshape(w.n, s)
+
+
+def request_stream(seed: int, count: int, rate: float, grids=(32, 48, 64, 96, 128),
+                   widths=(2, 4, 8, 16), precisions=("fp32", "fp64")) -> list:
+    """Seeded Poisson stream of slab-solve requests: exponential inter-arrival
+    times of mean 1/rate seconds, grid (cells per direction), block width s
+    and inner precision drawn uniformly. Returns a list of dicts
+    {rid, arrival, n, s, precision} in arrival order."""
+    u = 0.5 * (uniform(seed, 4 * count) + 1.0)          # [0, 1)
+    t, out = 0.0, []
+    for i in range(count):
+        t += -np.log1p(-u[4 * i]) / rate
+        out.append({"rid": i, "arrival": t,
+                    "n": int(grids[min(int(u[4 * i + 1] * len(grids)), len(grids) - 1)]),
+                    "s": int(widths[min(int(u[4 * i + 2] * len(widths)), len(widths) - 1)]),
+                    "precision": precisions[min(int(u[4 * i + 3] * len(precisions)),
+                                                len(precisions) - 1)]})
+    return out

@@ -35,3 +35,17 @@ def test_workloads_shapes():
     w3 = synth.convdiff_3d(16, 3)
     D = synth.diffusion_field(w3)
     assert D.shape == (16, 16, 16) and np.all(D > 0)
+
+
+def test_request_stream_is_seeded_and_poisson():
+    a = synth.request_stream(5, 2000, rate=40.0)
+    b = synth.request_stream(5, 2000, rate=40.0)
+    assert a == b
+    t = np.array([r["arrival"] for r in a])
+    assert np.all(np.diff(t) >= 0.0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / 40.0) < 0.1 / 40.0          # exponential mean 1/rate
+    assert abs(np.median(gaps) - np.log(2) / 40.0) < 0.15 / 40.0
+    assert {r["n"] for r in a} == {32, 48, 64, 96, 128}
+    assert {r["s"] for r in a} == {2, 4, 8, 16}
+    assert {r["precision"] for r in a} == {"fp32", "fp64"}
