@@ -70,6 +70,8 @@ enum {
   PINT_BF16 = 2    /* as PINT_FP32 but the SpMM matrix values are bfloat16    */
 };
 
+enum { PINT_SOLVER_GMRES = 0, PINT_SOLVER_CG = 1 };
+
 typedef struct pint_ctx_s* pint_ctx;
 typedef struct pint_op_s* pint_op;
 typedef struct pint_problem_s* pint_problem;
@@ -92,7 +94,12 @@ typedef struct {
   int max_inner;     /* block Arnoldi steps per inner solve                 */
   int precond;       /* PINT_PC_*                                           */
   int precision;     /* PINT_FP64 / PINT_FP32 / PINT_BF16                   */
-  int reserved[3];
+  int solver;        /* inner solver: PINT_SOLVER_GMRES (block GMRES(restart),
+                        right preconditioning) or PINT_SOLVER_CG (breakdown-
+                        free block CG, the paper's solver for symmetric
+                        systems: J and the preconditioner must be symmetric
+                        positive definite; uses 4 basis blocks, restart >= 3) */
+  int reserved[2];
 } pint_opts;
 
 typedef struct {

@@ -304,3 +304,61 @@ def ilu0_stencil_apply(dims, fac, X):
             Z[rows[has]] -= u[has][:, None] * Z[j]
         Z[rows] /= d[rows][:, None]
     return Z
+
+
+# --------------------------------------------------------------------------
+# Block conjugate gradients (the paper's solver for symmetric systems)
+# --------------------------------------------------------------------------
+def _spd_pinv_apply(G, rhs, defl):
+    """(G)^+ rhs for a symmetric positive semi-definite s x s G through the
+    deflating Cholesky factor: columns whose pivot is deflated get zero rows
+    (the inverse restricted to the active columns)."""
+    Rf, dead = cholesky_deflating(G, defl)
+    s = G.shape[0]
+    Rinv = np.zeros_like(Rf)
+    for t in range(s):                    # rows of R^-1, as the device computes them
+        row = np.zeros(s)
+        for k in range(s):
+            if dead[k]:
+                continue
+            v = (1.0 if t == k else 0.0) - np.dot(row[:k], Rf[:k, k])
+            row[k] = v / Rf[k, k]
+        Rinv[t] = row
+    # G^+ = R^-1 R^-T on the active columns
+    return Rinv @ (Rinv.T @ rhs)
+
+
+def block_cg(apply_J, apply_Minv, R, tol, maxit=1000, defl=1e-14):
+    """Preconditioned block CG for symmetric positive definite J and M,
+    breakdown-free form: the search block is orthonormalised (CholQR2 with
+    deflation) every iteration, so dependent or converged columns drop out
+    instead of making P^T J P singular:
+        Z = M^-1 R;  P = orth(Z)
+        repeat: Q = J P;  a = (P^T Q)^+ P^T R;  X += P a;  R -= Q a
+                Z = M^-1 R;  b = -(P^T Q)^+ Q^T Z;  P = orth(Z + P b)
+    until every column satisfies ||R_k|| <= tol ||R0_k||. X0 = 0.
+    Returns (X, info) with info = {iters, est, converged}."""
+    N, s = R.shape
+    X = np.zeros_like(R)
+    r0 = np.linalg.norm(R, axis=0)
+    target = tol * r0
+    Rc = R.copy()
+    est = r0.copy()
+    if np.all(r0 == 0.0):
+        return X, {"iters": 0, "est": est, "converged": True}
+    P, _ = cholqr2(apply_Minv(Rc), defl)
+    its = 0
+    while its < maxit:
+        Q = apply_J(P)
+        G = P.T @ Q
+        a = _spd_pinv_apply(G, P.T @ Rc, defl)
+        X = X + P @ a
+        Rc = Rc - Q @ a
+        its += 1
+        est = np.linalg.norm(Rc, axis=0)
+        if np.all(est <= target):
+            break
+        Z = apply_Minv(Rc)
+        b = -_spd_pinv_apply(G, Q.T @ Z, defl)
+        P, _ = cholqr2(Z + P @ b, defl)
+    return X, {"iters": its, "est": est, "converged": bool(np.all(est <= target))}

@@ -98,7 +98,7 @@ def sequential_dirk_linear(K, Mdiag, A, tau, y0, Bstages):
 
 def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
                precond="jacobi", restart=30, max_outer=200, inner_maxit=2000,
-               exact_inner=False, Y0=None, narrow=False):
+               exact_inner=False, Y0=None, narrow=False, solver="gmres"):
     """The method for a linear slab: defect correction around the splitting
     (Eq. matrix-splitting, Eq. matrix-fixed-point-equation) with a block GMRES
     inner solve on J = alpha M + beta K. Returns (Y, info).
@@ -107,7 +107,10 @@ def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
     depends on columns 0..k of Y only, so converged leading columns stay
     converged; the inner solve then takes only the trailing columns, the
     smallest power-of-two count that holds every unconverged one (the slab
-    counterpart of dropping converged stages in Algorithm 1)."""
+    counterpart of dropping converged stages in Algorithm 1).
+
+    solver: "gmres" (block GMRES(restart)) or "cg" (block CG, symmetric
+    positive definite J and preconditioner)."""
     n, s = K.shape[0], A1.shape[0]
     alpha, beta, _, _ = _split(A1, A2)
     J = sp.csr_matrix(sp.diags(alpha * Mdiag) + beta * K)
@@ -136,6 +139,8 @@ def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
             c0 = s - width if width < s else 0
         if exact_inner:
             V = lu.solve(R[:, c0:])
+        elif solver == "cg":
+            V, info = krylov.block_cg(lambda X: J @ X, Pinv, R[:, c0:], inner_tol, inner_maxit)
         else:
             V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R[:, c0:], inner_tol, restart,
                                          inner_maxit)

@@ -25,6 +25,7 @@ PINT_MAX_S = 16
 PINT_MEM_HOST, PINT_MEM_DEVICE = 0, 1
 PINT_PC_NONE, PINT_PC_JACOBI, PINT_PC_ILU0 = 0, 1, 2
 PINT_FP64, PINT_FP32, PINT_BF16 = 0, 1, 2
+PINT_SOLVER_GMRES, PINT_SOLVER_CG = 0, 1
 PINT_PROBLEM_DIFFREACT, PINT_PROBLEM_RICHARDS = 1, 2
 KERNEL_FAMILIES = ["coupled", "spmm", "gram", "update", "cholqr", "hess", "ilu", "norm", "vec",
                    "nl"]
@@ -43,7 +44,7 @@ class pint_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("max_step", C.c_double),
                 ("lscheme_L", C.c_double), ("restart", C.c_int),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("precond", C.c_int),
-                ("precision", C.c_int), ("reserved", C.c_int * 3)]
+                ("precision", C.c_int), ("solver", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class pint_stats(C.Structure):

@@ -1175,6 +1175,140 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
   return res;
 }
 
+// ------------------------------------------------------ block CG (inner)
+// out = scale * Rinv Rinv^T Y for the deflating Cholesky factor of G = R^T R
+// (Rinv from k_chol, zero rows for deflated pivots): the inverse of a
+// symmetric positive semi-definite s x s G on its active columns.
+__global__ void k_spd_apply(int s, const double* __restrict__ Rinv, const double* __restrict__ Y,
+                            double scale, double* __restrict__ out) {
+  __shared__ double T[kMaxS][kMaxS + 1];
+  const int t = threadIdx.x, i = t / kMaxS, k = t % kMaxS;
+  if (i < s && k < s) {                         // T = Rinv^T Y
+    double v = 0.0;
+    for (int c = 0; c < s; ++c) v += Rinv[c * s + i] * Y[c * s + k];
+    T[i][k] = v;
+  }
+  __syncthreads();
+  if (i < s && k < s) {                         // out = scale Rinv T
+    double v = 0.0;
+    for (int c = 0; c < s; ++c) v += Rinv[i * s + c] * T[c][k];
+    out[i * s + k] = scale * v;
+  }
+}
+
+// Z = D^-1 R (Jacobi) in the vector precision
+template <typename VT>
+__global__ void k_rowscale_v(int64_t n, int s, const VT* __restrict__ R,
+                             const double* __restrict__ dinv, VT* __restrict__ Z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n * s) Z[i] = (VT)((double)R[i] * dinv[i / s]);
+}
+
+// Breakdown-free preconditioned block CG on the unit-column right-hand side
+// Rs (symmetric positive definite J and M): the search block is
+// orthonormalised by CholQR2 with deflation every iteration, so dependent or
+// converged columns leave it instead of making P^T J P singular.
+//   Z = M^-1 R, P = orth(Z);  repeat: Q = J P, a = (P^T Q)^+ P^T R,
+//   X += P a, R -= Q a, Z = M^-1 R, b = -(P^T Q)^+ Q^T Z, P = orth(Z + P b)
+// Blocks 0..3 of the basis hold P, Q, Z, R; the solution goes to Xk.
+static InnerResult block_cg(pint_op op, const pint_opts* o, KrylovWork* w, cudaStream_t st) {
+  pint_ctx ctx = op->ctx;
+  const int64_t n = op->n;
+  const int s = op->s, prec = o->precision;
+  const int vprec = prec == PINT_FP64 ? PINT_FP64 : PINT_FP32;
+  const bool ilu = o->precond == PINT_PC_ILU0;
+  const int64_t bs = w->bs, np = w->n_pad, ns = n * s;
+  const size_t es = w->es;
+  PINT_REQUIRE(w->m >= 3, PINT_ERR_INVALID, "block CG needs restart >= 3 (work blocks)");
+  auto Vb = [&](int b) { return (void*)((char*)w->V + (size_t)b * bs * es); };
+  void* Pb = Vb(0);
+  void* Qb = Vb(1);
+  void* Zb = Vb(2);
+  void* Rb = Vb(3);
+  const double defl = vprec == PINT_FP64 ? 1e-14 : 1e-8;
+  auto precond = [&](const void* X, void* Z) {
+    if (ilu) {
+      ilu_apply(op, prec, X, Z, st);
+    } else if (o->precond == PINT_PC_JACOBI) {
+      ProfScope ps(ctx, PF_VEC, (2.0 * es + 8.0) * ns, 1.0 * ns, st);
+      if (vprec == PINT_FP64)
+        k_rowscale_v<double><<<grid_for(ns, 256), 256, 0, st>>>(n, s, (const double*)X,
+                                                                op->Jinvdiag, (double*)Z);
+      else
+        k_rowscale_v<float><<<grid_for(ns, 256), 256, 0, st>>>(n, s, (const float*)X,
+                                                               op->Jinvdiag, (float*)Z);
+      check_launch("k_rowscale_v");
+      ctx->launches += 1;
+    } else {
+      PINT_CUDA(cudaMemcpyAsync(Z, X, es * ns, cudaMemcpyDeviceToDevice, st));
+    }
+  };
+  auto spd_apply = [&](const double* Y, double scale, double* out) {
+    ProfScope ps(ctx, PF_CHOLQR, 0.0, 4.0 * s * s * s, st);
+    k_spd_apply<<<1, 256, 0, st>>>(s, w->S, Y, scale, out);
+    check_launch("k_spd_apply");
+    ctx->launches += 1;
+  };
+  {
+    double t[kMaxS];
+    for (int k = 0; k < s; ++k) t[k] = o->inner_tol;
+    PINT_CUDA(cudaMemcpyAsync(w->target, t, 8 * s, cudaMemcpyHostToDevice, st));
+  }
+  PINT_CUDA(cudaMemsetAsync(w->Xk, 0, es * ns, st));
+  PINT_CUDA(cudaMemsetAsync(w->defl, 0, 64, st));
+  PINT_CUDA(cudaMemcpyAsync(Rb, w->Rs, es * ns, cudaMemcpyDeviceToDevice, st));
+  if (s < w->s && np > n)          // narrower than the allocation: clear the padded rows
+    for (int b = 0; b < 4; ++b)
+      PINT_CUDA(cudaMemsetAsync((char*)Vb(b) + es * (size_t)ns, 0, es * (size_t)(np - n) * s, st));
+  precond(Rb, Zb);
+  PINT_CUDA(cudaMemcpyAsync(Pb, Zb, es * ns, cudaMemcpyDeviceToDevice, st));
+  cholqr2(ctx, vprec, n, s, Pb, w->Rn, w->defl, st, np);
+  InnerResult res{0, 1, false, 0};
+  while (res.its < o->max_inner) {
+    launch_inner_spmm(op, prec, false, Pb, Qb, nullptr, st);              // Q = J P
+    launch_gram(ctx, vprec, n, s, 1, Pb, bs, Qb, w->Hg1, st, np);           // G = P^T Q
+    {
+      ProfScope ps(ctx, PF_CHOLQR, 0.0, 1.0 * s * s * s, st);
+      k_chol<<<1, 256, 0, st>>>(s, w->Hg1, defl, w->Rn, w->S, w->defl);
+      check_launch("k_chol");
+      ctx->launches += 1;
+    }
+    launch_gram(ctx, vprec, n, s, 1, Pb, bs, Rb, w->Hg2, st, np);           // P^T R
+    spd_apply(w->Hg2, 1.0, w->Yls);                                         // a
+    launch_update(ctx, vprec, n, s, 1, Pb, bs, w->Yls, w->Xk, 2, st);       // X += P a
+    launch_update(ctx, vprec, n, s, 1, Qb, bs, w->Yls, Rb, 0, st);          // R -= Q a
+    launch_colnorm(ctx, vprec, n, s, Rb, w->est, st);
+    res.its += 1;
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_small, w->est, 8 * s, cudaMemcpyDeviceToHost, st));
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 2, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                              st));
+    PINT_CUDA(cudaStreamSynchronize(st));
+    PINT_REQUIRE(ctx->h_flag[2] == 0, PINT_ERR_TIMEOUT,
+                 "bulk-copy wait in the Gram kernel exceeded its time budget");
+    if (ilu) ilu_check(op);
+    bool conv = true;
+    for (int k = 0; k < s; ++k) {
+      PINT_REQUIRE(std::isfinite(ctx->h_small[k]), PINT_ERR_BREAKDOWN,
+                   "non-finite residual in block CG");
+      if (!(ctx->h_small[k] <= o->inner_tol)) conv = false;   // columns of Rs are unit
+    }
+    if (conv) {
+      res.converged = true;
+      break;
+    }
+    precond(Rb, Zb);                                                        // Z = M^-1 R
+    launch_gram(ctx, vprec, n, s, 1, Qb, bs, Zb, w->Hg2, st, np);           // Q^T Z
+    spd_apply(w->Hg2, -1.0, w->Yls);                                        // b
+    launch_update(ctx, vprec, n, s, 1, Pb, bs, w->Yls, Zb, 2, st);          // Z += P b
+    cholqr2(ctx, vprec, n, s, Zb, w->Rn, w->defl, st, np);                  // P = orth(Z)
+    std::swap(Pb, Zb);
+  }
+  PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->defl, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PINT_CUDA(cudaStreamSynchronize(st));
+  res.deflations = ctx->h_flag[0];
+  return res;
+}
+
 InnerResult inner_solve(pint_op op, const pint_opts* o, const double* R, const double* rnorm_dev,
                         double* /*unused*/, cudaStream_t st) {
   KrylovWork* w = ensure_work(op, o->precision == PINT_FP64 ? PINT_FP64 : PINT_FP32, o->restart);
@@ -1185,6 +1319,7 @@ InnerResult inner_solve(pint_op op, const pint_opts* o, const double* R, const d
   } else {
     launch_scale_cast(n, s, R, (float*)w->Rs, rnorm_dev, st, op->ctx);
   }
+  if (o->solver == PINT_SOLVER_CG) return block_cg(op, o, w, st);
   return gmres(op, o, w, st);
 }
 

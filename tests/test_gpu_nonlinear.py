@@ -223,3 +223,30 @@ def test_pipeline_richards_lscheme_equals_sequential(P, ctx, prec):
         np.testing.assert_allclose(out.cpu().numpy(), Yseq, rtol=0, atol=2e-7)
     finally:
         P.pint_problem_destroy(prob)
+
+
+def test_pipeline_richards_lscheme_block_cg(P, ctx):
+    """The L-scheme matrix is symmetric positive definite (one conductivity
+    per face): Algorithm 1 with block CG inner solves reaches the stages of
+    sequential Newton stepping on 8^3 cells."""
+    import torch
+    dims = (8, 8, 8)
+    prob, oprob, n = _make(P, ctx, "richards", dims)
+    try:
+        A, _, c = coupling.implicit_euler()
+        tau, G, s = 1.0 / 96.0, 6, 4
+        z, _ = fv.richards_cells(dims)
+        out = torch.zeros(n, G, device="cuda", dtype=torch.float64)
+        o = P.pint_opts_default()
+        o.tol = 1e-10
+        o.inner_tol = 1e-8
+        o.precond = P.PINT_PC_ILU0
+        o.max_outer = 150
+        o.max_step = 1.0
+        o.lscheme_L = -1.0
+        o.solver = P.PINT_SOLVER_CG
+        P.pint_pipeline_run(ctx, prob, A, c, tau, s, _dev(-z), G, out, o)
+        Yseq, _ = newton.sequential_dirk_newton(oprob, A, c, tau, -z, G)
+        np.testing.assert_allclose(out.cpu().numpy(), Yseq, rtol=0, atol=2e-7)
+    finally:
+        P.pint_problem_destroy(prob)

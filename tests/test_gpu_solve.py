@@ -215,3 +215,33 @@ def test_budget_exceeded_is_nomem(P):
         assert P.pint_bytes_in_use(c) <= 1 << 20
     finally:
         P.pint_destroy(c)
+
+
+@pytest.mark.parametrize("prec,pc", [("fp64", "ilu0"), ("fp64", "jacobi"), ("fp32", "ilu0"),
+                                     ("fp32", "jacobi")])
+@pytest.mark.parametrize("s", [1, 3, 8])
+def test_slab_block_cg_symmetric_operator(P, ctx, prec, pc, s):
+    """Pure diffusion (symmetric J = M/tau + K): the slab with block CG inner
+    solves equals sequential stepping, with an effort close to the oracle's
+    block CG."""
+    import torch
+    dims = (12, 10, 9)
+    op, K, n, A, A1, A2, B = _setup(P, ctx, dims, s, 1e-3, v=(0.0, 0.0, 0.0))
+    try:
+        Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
+        o = P.pint_opts_default()
+        o.tol = 1e-12
+        o.inner_tol = 1e-2 if s > 1 else 1e-6
+        o.precond = P.PINT_PC_ILU0 if pc == "ilu0" else P.PINT_PC_JACOBI
+        o.precision = P.PINT_FP64 if prec == "fp64" else P.PINT_FP32
+        o.solver = P.PINT_SOLVER_CG
+        st = P.pint_solve_block(ctx, op, _dev(B), None, Y, o, raise_on_nonconvergence=True)
+        Yref = slab.sequential_dirk_linear(K, np.ones(n), A, 1e-3, np.zeros(n), B)
+        err = _colerr(Y.cpu().numpy(), Yref)
+        assert np.all(err < 1e-9), err
+        Yo, info = slab.slab_solve(K, np.ones(n), A1, A2, B, None, tol=1e-12,
+                                   inner_tol=o.inner_tol, precond=pc, solver="cg")
+        assert abs(st.outer_its - info["outer"]) <= 2
+        assert st.inner_its <= 1.5 * info["inner"] + 5
+    finally:
+        P.pint_operator_destroy(op)

@@ -182,3 +182,45 @@ def test_ilu0_stencil_tridiagonal_is_exact_solve():
     b = rng.standard_normal((40, 2))
     Z = krylov.ilu0_stencil_apply(dims, krylov.ilu0_stencil(dims, J), b)
     np.testing.assert_allclose(J @ Z, b, rtol=1e-12, atol=1e-12)
+
+
+def _spd(n=7, seed=5):
+    """SPD 5-point diffusion matrix plus a mass term on an n x n grid."""
+    dims = (n, n, 1)
+    rng = np.random.default_rng(seed)
+    K = fv.convdiff_matrix(dims, np.exp(rng.standard_normal(dims[::-1])), (0.0, 0.0, 0.0))
+    J = sp.csr_matrix(K + 50.0 * sp.identity(n * n))
+    J.sort_indices()
+    return J, rng
+
+
+def test_block_cg_single_column_is_textbook_pcg():
+    J, rng = _spd()
+    b = rng.standard_normal((J.shape[0], 1))
+    d = J.diagonal()
+    X, info = krylov.block_cg(lambda V: J @ V, lambda V: V / d[:, None], b, 1e-12)
+    # textbook PCG, written out
+    x = np.zeros_like(b[:, 0]); r = b[:, 0].copy(); z = r / d; p = z.copy(); it = 0
+    while np.linalg.norm(r) > 1e-12 * np.linalg.norm(b):
+        q = J @ p; al = (r @ z) / (p @ q); x += al * p; rn = r - al * q
+        zn = rn / d; be = (rn @ zn) / (r @ z); p = zn + be * p; r, z = rn, zn; it += 1
+    assert info["converged"] and abs(info["iters"] - it) <= 1
+    np.testing.assert_allclose(X[:, 0], x, rtol=1e-9, atol=1e-12)
+
+
+def test_block_cg_solves_spd_blocks_and_survives_dependent_columns():
+    J, rng = _spd(9, 6)
+    n = J.shape[0]
+    B = rng.standard_normal((n, 5))
+    B[:, 3] = 2.0 * B[:, 0]                       # dependent column: rank 4
+    B[:, 4] = 0.0                                 # zero column
+    L, U = krylov.ilu0(J)
+    Minv = krylov.ilu0_apply(L, U)
+    X, info = krylov.block_cg(lambda V: J @ V, Minv, B, 1e-11)
+    assert info["converged"] and np.all(np.isfinite(X))
+    Xd = np.linalg.solve(J.toarray(), B)
+    np.testing.assert_allclose(X, Xd, rtol=1e-8, atol=1e-12)
+    # the block needs no more iterations than its hardest single column
+    its1 = max(krylov.block_cg(lambda V: J @ V, Minv, B[:, [k]], 1e-11)[1]["iters"]
+               for k in range(3))
+    assert info["iters"] <= its1

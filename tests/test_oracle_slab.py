@@ -170,3 +170,20 @@ def test_narrowed_inner_solves_keep_the_solution_and_iterations():
     R = slab.coupled_residual(K, np.ones(n), A1, A2, Y1, B)
     F = slab.rhs_F(A2, B)
     assert np.all(np.linalg.norm(R, axis=0) <= 1e-12 * np.linalg.norm(F, axis=0))
+
+
+def test_slab_with_block_cg_equals_sequential_stepping():
+    """Pure diffusion (symmetric J): the slab solved with block CG inner
+    solves equals s sequential implicit-Euler steps."""
+    rng = np.random.default_rng(23)
+    dims = (8, 7, 3)
+    n, s, tau = 168, 4, 1e-2
+    K = fv.convdiff_matrix(dims, np.exp(rng.standard_normal(dims[::-1])), (0.0, 0.0, 0.0))
+    A, _, _ = coupling.implicit_euler()
+    A1, A2, _ = coupling.multistep_matrices(A, s, tau)
+    B = rng.uniform(-1, 1, (n, s))
+    Y, info = slab.slab_solve(K, np.ones(n), A1, A2, B, tol=1e-12, inner_tol=1e-2,
+                              precond="ilu0", solver="cg")
+    Ys = slab.sequential_dirk_linear(K, np.ones(n), A, tau, np.zeros(n), B)
+    assert info["converged"]
+    np.testing.assert_allclose(Y, Ys, rtol=1e-9, atol=1e-12)
