@@ -75,6 +75,8 @@ def parse(argv=None):
     p.add_argument("--precond", default=None, choices=["ilu0", "jacobi"])
     p.add_argument("--inner-tol", type=float, default=None)
     p.add_argument("--restart", type=int, default=None, help="GMRES restart length (30)")
+    p.add_argument("--solver", default="gmres", choices=["gmres", "cg"],
+                   help="inner solver (cg: symmetric systems, e.g. the Richards L-scheme)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true",
@@ -335,6 +337,7 @@ class LinearCase:
         o.precond = P.PINT_PC_ILU0 if args.precond == "ilu0" else P.PINT_PC_JACOBI
         o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[args.precision]
         o.restart = args.restart
+        o.solver = P.PINT_SOLVER_CG if args.solver == "cg" else P.PINT_SOLVER_GMRES
         self.o = o
         self.Bd = torch.tensor(self.B, device="cuda", dtype=torch.float64)
         self.Y = torch.zeros(self.n, s, device="cuda", dtype=torch.float64)
@@ -415,6 +418,7 @@ class PipelineCase:
         o.precond = P.PINT_PC_ILU0 if args.precond == "ilu0" else P.PINT_PC_JACOBI
         o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[args.precision]
         o.restart = args.restart
+        o.solver = P.PINT_SOLVER_CG if args.solver == "cg" else P.PINT_SOLVER_GMRES
         self.o = o
         self.nnz = int(P.pint_operator_nnz(P.pint_problem_operator(self.prob)))
 
@@ -439,7 +443,7 @@ class PipelineCase:
                 "tol": self.tol, "inner_tol": self.o.inner_tol, "restart": self.o.restart,
                 "max_step": self.max_step,
                 "linearisation": "L-scheme (L = Lipschitz constant of theta)" if self.lscheme
-                else "simplified Newton"}
+                else "simplified Newton", "solver": self.args.solver}
 
     def close(self):
         self.P.pint_problem_destroy(self.prob)

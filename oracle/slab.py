@@ -139,11 +139,13 @@ def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
             c0 = s - width if width < s else 0
         if exact_inner:
             V = lu.solve(R[:, c0:])
-        elif solver == "cg":
-            V, info = krylov.block_cg(lambda X: J @ X, Pinv, R[:, c0:], inner_tol, inner_maxit)
         else:
-            V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R[:, c0:], inner_tol, restart,
-                                         inner_maxit)
+            if solver == "cg":
+                V, info = krylov.block_cg(lambda X: J @ X, Pinv, R[:, c0:], inner_tol,
+                                          inner_maxit)
+            else:
+                V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R[:, c0:], inner_tol,
+                                             restart, inner_maxit)
             inner_its += info["iters"]
             col_steps += info["iters"] * (s - c0)
         Y[:, c0:] = Y[:, c0:] - V

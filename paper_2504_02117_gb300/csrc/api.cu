@@ -216,6 +216,7 @@ int pint_create(pint_ctx* out, int device, size_t budget) {
     ctx->d_small = dalloc_n<double>(ctx, kSmallDoubles);
     ctx->d_flag = dalloc_n<int>(ctx, 64);
     PINT_CUDA(cudaMemset(ctx->d_small, 0, sizeof(double) * kSmallDoubles));
+    PINT_CUDA(cudaMemset(ctx->d_flag, 0, 64 * sizeof(int)));    // device error words
     return PINT_OK;
   });
   if (rc != PINT_OK) {

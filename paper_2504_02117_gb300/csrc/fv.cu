@@ -555,7 +555,9 @@ static void newton_step(pint_problem p, const double* times, double* Y, const do
     stats->restarts += ir.cycles;
     stats->deflations += ir.deflations;
   }
-  const double* rs = o->precond == PINT_PC_JACOBI ? op->Jinvdiag : nullptr;
+  // block GMRES with Jacobi solves for D V (see solve_block_impl); CG for V
+  const double* rs =
+      o->precond == PINT_PC_JACOBI && o->solver != PINT_SOLVER_CG ? op->Jinvdiag : nullptr;
   const double* cs = rnorm;
   if (o->max_step > 0.0) {
     double* bounded = ctx->d_small + kSmallScratch + 128;

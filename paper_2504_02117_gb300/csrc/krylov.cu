@@ -1312,6 +1312,8 @@ static InnerResult block_cg(pint_op op, const pint_opts* o, KrylovWork* w, cudaS
 InnerResult inner_solve(pint_op op, const pint_opts* o, const double* R, const double* rnorm_dev,
                         double* /*unused*/, cudaStream_t st) {
   KrylovWork* w = ensure_work(op, o->precision == PINT_FP64 ? PINT_FP64 : PINT_FP32, o->restart);
+  // the error word that bounded waits raise belongs to this solve only
+  PINT_CUDA(cudaMemsetAsync(op->ctx->d_flag, 0, sizeof(int), st));
   const int64_t n = op->n;
   const int s = op->s;
   if (w->prec == PINT_FP64) {
@@ -1440,8 +1442,11 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
     cycles += ir.cycles;
     defl += ir.deflations;
     const int vprec = w->prec;
-    launch_outer_update(vprec, n, sw, Y, w->Xk, w->rnorm + c0,
-                        o->precond == PINT_PC_JACOBI ? op->Jinvdiag : nullptr, st, ctx, s, c0);
+    // block GMRES with Jacobi solves for the scaled variable D X (right
+    // preconditioning fused into the SpMM); block CG solves for X itself
+    const bool scaled = o->precond == PINT_PC_JACOBI && o->solver != PINT_SOLVER_CG;
+    launch_outer_update(vprec, n, sw, Y, w->Xk, w->rnorm + c0, scaled ? op->Jinvdiag : nullptr,
+                        st, ctx, s, c0);
   }
   PINT_CUDA(cudaStreamSynchronize(st));
   if (stats) {
