@@ -15,7 +15,10 @@ the device are:
     reflectors of length s+1, one per column; the per-column residual
     estimates are the norms of the last s rows of the rotated right-hand side;
   * Jacobi: P^{-1} = diag(J)^{-1}; ILU(0): incomplete LU in natural order on
-    the pattern of J (IKJ variant), applied by forward / backward substitution.
+    the pattern of J (IKJ variant), applied by forward / backward substitution;
+  * block CG (symmetric systems) re-orthonormalises its search block every
+    iteration; block BiCGStab (nonsymmetric systems) deflates the right-hand
+    side block once, by CholQR2, before it starts.
 """
 from __future__ import annotations
 
@@ -362,3 +365,79 @@ def block_cg(apply_J, apply_Minv, R, tol, maxit=1000, defl=1e-14):
         b = -_spd_pinv_apply(G, Q.T @ Z, defl)
         P, _ = cholqr2(Z + P @ b, defl)
     return X, {"iters": its, "est": est, "converged": bool(np.all(est <= target))}
+
+
+# --------------------------------------------------------------------------
+# Block BiCGStab (the paper's solver for the linear convection-diffusion
+# problem, Sec. 4.1)
+# --------------------------------------------------------------------------
+def _solve_active(G, rhs, active):
+    """G^{-1} rhs on the active rows and columns of the s x s G; the rows of
+    inactive (deflated) columns are zero."""
+    out = np.zeros((G.shape[0], rhs.shape[1]))
+    a = np.flatnonzero(active)
+    if a.size:
+        out[a] = np.linalg.solve(G[np.ix_(a, a)], rhs[a])
+    return out
+
+
+def block_bicgstab(apply_J, apply_Minv, R, tol, maxit=1000, defl=1e-14, record=None):
+    """Right-preconditioned block BiCGStab (Guennouni, Jbilou and Sadok, "A
+    block version of BiCGSTAB for linear systems with multiple right-hand
+    sides", ETNA 16, 2003) for a nonsymmetric J, X0 = 0.
+
+    The published method has no treatment of dependent right-hand sides, for
+    which the s x s matrices Rt^T V are singular from the start. The reading
+    here deflates once, up front: R = Q0 C by CholQR2 with deflation, the
+    iteration solves J Xh = Q0 with the shadow block Rt = Q0 (deflated
+    columns of Q0 are zero and stay zero; the s x s solves act on the active
+    columns only), and X = Xh C:
+        Rh = P = Q0
+        repeat: Ph = M^-1 P;  V = J Ph;  alpha = (Rt^T V)^-1 Rt^T Rh
+                S = Rh - V alpha;  Sh = M^-1 S;  T = J Sh
+                omega = <T, S>_F / <T, T>_F
+                Xh += Ph alpha + omega Sh;  Rh = S - omega T
+                stop when every column of Rh C is <= tol ||R_k||
+                beta = -(Rt^T V)^-1 Rt^T T;  P = Rh + (P - omega V) beta
+    `record`, a list, receives per iteration the quantities that define
+    alpha, omega and beta (Rt^T S, <T, S - omega T>_F, Rt^T (T + V beta)),
+    all zero in exact arithmetic. Returns (X, info) with info = {iters, est,
+    converged}."""
+    N, s = R.shape
+    r0 = np.linalg.norm(R, axis=0)
+    target = tol * r0
+    if np.all(r0 == 0.0):
+        return np.zeros_like(R), {"iters": 0, "est": r0, "converged": True}
+    Q0, C = cholqr2(R, defl)
+    active = np.diag(C) != 0.0
+    Rt = Q0
+    Rh = Q0.copy()
+    P = Q0.copy()
+    Xh = np.zeros_like(R)
+    est = r0.copy()
+    its = 0
+    while its < maxit:
+        Ph = apply_Minv(P)
+        V = apply_J(Ph)
+        G = Rt.T @ V
+        alpha = _solve_active(G, Rt.T @ Rh, active)
+        S = Rh - V @ alpha
+        Sh = apply_Minv(S)
+        T = apply_J(Sh)
+        tt = float(np.sum(T * T))
+        omega = float(np.sum(T * S)) / tt if tt > 0.0 else 0.0
+        Xh = Xh + Ph @ alpha + omega * Sh
+        Rh = S - omega * T
+        its += 1
+        est = np.linalg.norm(Rh @ C, axis=0)
+        if not np.all(np.isfinite(est)) or np.all(est <= target):
+            if record is not None:
+                record.append({"RtS": Rt.T @ S, "omega_orth": float(np.sum(T * Rh))})
+            break
+        beta = -_solve_active(G, Rt.T @ T, active)
+        if record is not None:
+            record.append({"RtS": Rt.T @ S, "omega_orth": float(np.sum(T * Rh)),
+                           "RtTVb": Rt.T @ (T + V @ beta)})
+        P = Rh + (P - omega * V) @ beta
+    return Xh @ C, {"iters": its, "est": est,
+                    "converged": bool(np.all(est <= target))}

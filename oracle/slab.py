@@ -109,8 +109,9 @@ def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
     smallest power-of-two count that holds every unconverged one (the slab
     counterpart of dropping converged stages in Algorithm 1).
 
-    solver: "gmres" (block GMRES(restart)) or "cg" (block CG, symmetric
-    positive definite J and preconditioner)."""
+    solver: "gmres" (block GMRES(restart)), "cg" (block CG, symmetric
+    positive definite J and preconditioner) or "bicgstab" (block BiCGStab,
+    the paper's solver for the nonsymmetric linear problem)."""
     n, s = K.shape[0], A1.shape[0]
     alpha, beta, _, _ = _split(A1, A2)
     J = sp.csr_matrix(sp.diags(alpha * Mdiag) + beta * K)
@@ -143,6 +144,9 @@ def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
             if solver == "cg":
                 V, info = krylov.block_cg(lambda X: J @ X, Pinv, R[:, c0:], inner_tol,
                                           inner_maxit)
+            elif solver == "bicgstab":
+                V, info = krylov.block_bicgstab(lambda X: J @ X, Pinv, R[:, c0:], inner_tol,
+                                                inner_maxit)
             else:
                 V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R[:, c0:], inner_tol,
                                              restart, inner_maxit)

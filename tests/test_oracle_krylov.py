@@ -224,3 +224,65 @@ def test_block_cg_solves_spd_blocks_and_survives_dependent_columns():
     its1 = max(krylov.block_cg(lambda V: J @ V, Minv, B[:, [k]], 1e-11)[1]["iters"]
                for k in range(3))
     assert info["iters"] <= its1
+
+
+def _nonsym(n=9, seed=8, vel=(40.0, 20.0, 0.0)):
+    """Nonsymmetric convection-diffusion matrix (upwind, strong convection)
+    plus a mass term on an n x (n-1) grid."""
+    dims = (n, n - 1, 1)
+    rng = np.random.default_rng(seed)
+    K = fv.convdiff_matrix(dims, np.exp(0.5 * rng.standard_normal(dims[::-1])), vel)
+    J = sp.csr_matrix(sp.identity(K.shape[0]) / 1e-2 + K)
+    J.sort_indices()
+    return J, rng
+
+
+def test_block_bicgstab_single_column_is_library_bicgstab():
+    """s = 1 reduces to textbook BiCGStab: the iterates after k = 1, 2, 3, 6
+    steps equal scipy's right-preconditioned BiCGStab (an independent
+    implementation) to rounding."""
+    from scipy.sparse.linalg import LinearOperator, bicgstab
+    J, rng = _nonsym()
+    b = rng.standard_normal((J.shape[0], 1))
+    L, U = krylov.ilu0(J)
+    Minv = krylov.ilu0_apply(L, U)
+    M = LinearOperator(J.shape, matvec=lambda v: Minv(v.reshape(-1, 1)).ravel())
+    for k in (1, 2, 3, 6):
+        X, info = krylov.block_bicgstab(lambda V: J @ V, Minv, b, 1e-30, maxit=k)
+        x, _ = bicgstab(J, b[:, 0], rtol=1e-30, atol=0.0, maxiter=k, M=M)
+        assert info["iters"] == k
+        np.testing.assert_allclose(X[:, 0], x, rtol=1e-11, atol=1e-13 * np.abs(x).max())
+
+
+def test_block_bicgstab_coefficients_satisfy_their_defining_equations():
+    """alpha makes S orthogonal to the shadow block (Rt^T S = 0), omega
+    minimises ||S - omega T||_F (<T, Rh>_F = 0) and beta makes
+    Rt^T (T + V beta) = 0: each fails for a transposed s x s solve or a
+    flipped sign."""
+    J, rng = _nonsym(10, 9)
+    B = rng.standard_normal((J.shape[0], 4))
+    rec = []
+    krylov.block_bicgstab(lambda V: J @ V, lambda V: V / J.diagonal()[:, None], B, 1e-10,
+                          record=rec)
+    assert len(rec) >= 3
+    for r in rec:
+        assert np.abs(r["RtS"]).max() <= 1e-10
+        assert abs(r["omega_orth"]) <= 1e-10
+        if "RtTVb" in r:
+            assert np.abs(r["RtTVb"]).max() <= 1e-10
+
+
+def test_block_bicgstab_solves_and_survives_dependent_columns():
+    J, rng = _nonsym(9, 10)
+    n = J.shape[0]
+    B = rng.standard_normal((n, 6))
+    B[:, 3] = -3.0 * B[:, 1]                      # dependent column
+    B[:, 4] = 0.0                                 # zero column
+    B[:, 5] = B[:, 0]                             # duplicate column
+    L, U = krylov.ilu0(J)
+    X, info = krylov.block_bicgstab(lambda V: J @ V, krylov.ilu0_apply(L, U), B, 1e-11)
+    assert info["converged"] and np.all(np.isfinite(X))
+    Xd = np.linalg.solve(J.toarray(), B)
+    np.testing.assert_allclose(X, Xd, rtol=1e-8, atol=1e-12)
+    np.testing.assert_array_equal(X[:, 4], 0.0)
+    np.testing.assert_allclose(X[:, 5], X[:, 0], rtol=1e-12, atol=1e-15)

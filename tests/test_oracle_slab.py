@@ -187,3 +187,23 @@ def test_slab_with_block_cg_equals_sequential_stepping():
     Ys = slab.sequential_dirk_linear(K, np.ones(n), A, tau, np.zeros(n), B)
     assert info["converged"] and info["inner"] > 0
     np.testing.assert_allclose(Y, Ys, rtol=1e-9, atol=1e-12)
+
+
+def test_slab_with_block_bicgstab_equals_sequential_stepping():
+    """Convection-diffusion (nonsymmetric J): the slab solved with block
+    BiCGStab inner solves (Sec. 4.1's solver for this problem) equals s
+    sequential implicit-Euler steps, with and without narrowed inner solves."""
+    rng = np.random.default_rng(29)
+    dims = (8, 7, 3)
+    n, s, tau = 168, 4, 1e-2
+    K = fv.convdiff_matrix(dims, np.exp(rng.standard_normal(dims[::-1])), (30.0, 15.0, 5.0))
+    A, _, _ = coupling.implicit_euler()
+    A1, A2, _ = coupling.multistep_matrices(A, s, tau)
+    B = rng.uniform(-1, 1, (n, s))
+    Ys = slab.sequential_dirk_linear(K, np.ones(n), A, tau, np.zeros(n), B)
+    for pc in ("ilu0", "jacobi"):
+        for narrow in (False, True):
+            Y, info = slab.slab_solve(K, np.ones(n), A1, A2, B, tol=1e-12, inner_tol=1e-2,
+                                      precond=pc, solver="bicgstab", narrow=narrow)
+            assert info["converged"] and info["inner"] > 0
+            np.testing.assert_allclose(Y, Ys, rtol=1e-9, atol=1e-12)
