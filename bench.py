@@ -75,8 +75,10 @@ def parse(argv=None):
     p.add_argument("--precond", default=None, choices=["ilu0", "jacobi"])
     p.add_argument("--inner-tol", type=float, default=None)
     p.add_argument("--restart", type=int, default=None, help="GMRES restart length (30)")
-    p.add_argument("--solver", default="gmres", choices=["gmres", "cg"],
-                   help="inner solver (cg: symmetric systems, e.g. the Richards L-scheme)")
+    p.add_argument("--solver", default="gmres", choices=["gmres", "cg", "bicgstab"],
+                   help="inner solver (cg: symmetric systems, e.g. the Richards L-scheme; "
+                        "bicgstab: the paper's solver for the linear convection-diffusion "
+                        "problem)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true",
@@ -144,7 +146,8 @@ def oracle_sample(args, n, reps=1):
         for _ in range(reps):
             t = time.perf_counter()
             slab.slab_solve(K, np.ones(w.n), A1, A2, B, None, tol=w.tol,
-                            inner_tol=1e-2 if s > 1 else 1e-10, precond=args.precond)
+                            inner_tol=1e-2 if s > 1 else 1e-10, precond=args.precond,
+                            restart=args.restart, solver=args.solver)
             times.append(time.perf_counter() - t)
         return {"n": w.n, "steps": s, "times": times}
     if args.workload == "diffreact":
@@ -190,7 +193,8 @@ def run_oracle_subprocess(args, n, reps):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n), "--s", str(args.s),
-           "--steps", str(reps), "--workload", args.workload, "--precond", args.precond]
+           "--steps", str(reps), "--workload", args.workload, "--precond", args.precond,
+           "--solver", args.solver, "--restart", str(args.restart)]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
@@ -262,11 +266,27 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def source_hash():
+def solver_code(P, name):
+    return {"gmres": P.PINT_SOLVER_GMRES, "cg": P.PINT_SOLVER_CG,
+            "bicgstab": P.PINT_SOLVER_BICGSTAB}[name]
+
+
+# Files whose content fixes a kernel family's device code and launch shape:
+# its translation unit, the shared internal header and the build (flags).
+KERNEL_SOURCES = {
+    "ilu": ("paper_2504_02117_gb300/csrc/ilu.cu", "paper_2504_02117_gb300/csrc/internal.h",
+            "paper_2504_02117_gb300/build.py"),
+    "spmm": ("paper_2504_02117_gb300/csrc/spmm.cu", "paper_2504_02117_gb300/csrc/internal.h",
+             "paper_2504_02117_gb300/build.py"),
+}
+
+
+def source_hash(family):
+    """Hash of the sources of one kernel family (KERNEL_SOURCES): a captured
+    DRAM traffic figure is reported only while they are unchanged."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2504_02117_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    for rel in KERNEL_SOURCES[family]:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -280,7 +300,7 @@ def ncu_traffic(family, workload):
     with open(path) as fh:
         d = json.load(fh)
     e = d.get(workload, {}).get(family)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or family not in KERNEL_SOURCES or e.get("source_hash") != source_hash(family):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -337,7 +357,7 @@ class LinearCase:
         o.precond = P.PINT_PC_ILU0 if args.precond == "ilu0" else P.PINT_PC_JACOBI
         o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[args.precision]
         o.restart = args.restart
-        o.solver = P.PINT_SOLVER_CG if args.solver == "cg" else P.PINT_SOLVER_GMRES
+        o.solver = solver_code(P, args.solver)
         self.o = o
         self.Bd = torch.tensor(self.B, device="cuda", dtype=torch.float64)
         self.Y = torch.zeros(self.n, s, device="cuda", dtype=torch.float64)
@@ -361,7 +381,8 @@ class LinearCase:
 
     def describe(self):
         return {"cells": self.n, "s": self.s, "nnz": self.nnz, "tau": self.w.tau,
-                "tol": self.w.tol, "inner_tol": self.o.inner_tol, "restart": self.o.restart}
+                "tol": self.w.tol, "inner_tol": self.o.inner_tol, "restart": self.o.restart,
+                "solver": self.args.solver}
 
     def close(self):
         self.P.pint_operator_destroy(self.op)
@@ -418,7 +439,7 @@ class PipelineCase:
         o.precond = P.PINT_PC_ILU0 if args.precond == "ilu0" else P.PINT_PC_JACOBI
         o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[args.precision]
         o.restart = args.restart
-        o.solver = P.PINT_SOLVER_CG if args.solver == "cg" else P.PINT_SOLVER_GMRES
+        o.solver = solver_code(P, args.solver)
         self.o = o
         self.nnz = int(P.pint_operator_nnz(P.pint_problem_operator(self.prob)))
 

@@ -70,7 +70,7 @@ enum {
   PINT_BF16 = 2    /* as PINT_FP32 but the SpMM matrix values are bfloat16    */
 };
 
-enum { PINT_SOLVER_GMRES = 0, PINT_SOLVER_CG = 1 };
+enum { PINT_SOLVER_GMRES = 0, PINT_SOLVER_CG = 1, PINT_SOLVER_BICGSTAB = 2 };
 
 typedef struct pint_ctx_s* pint_ctx;
 typedef struct pint_op_s* pint_op;
@@ -95,10 +95,18 @@ typedef struct {
   int precond;       /* PINT_PC_*                                           */
   int precision;     /* PINT_FP64 / PINT_FP32 / PINT_BF16                   */
   int solver;        /* inner solver: PINT_SOLVER_GMRES (block GMRES(restart),
-                        right preconditioning) or PINT_SOLVER_CG (breakdown-
+                        right preconditioning), PINT_SOLVER_CG (breakdown-
                         free block CG, the paper's solver for symmetric
                         systems: J and the preconditioner must be symmetric
-                        positive definite; uses 4 basis blocks, restart >= 3) */
+                        positive definite; uses 4 basis blocks, restart >= 3)
+                        or PINT_SOLVER_BICGSTAB (block BiCGStab, the paper's
+                        solver for the nonsymmetric linear problem, Sec. 4.1:
+                        right preconditioning, the right-hand side block
+                        deflated once by CholQR2; uses 9 basis blocks,
+                        restart >= 8; a singular s x s system Rt^T V returns
+                        PINT_ERR_BREAKDOWN). max_inner counts its iterations
+                        (two operator and preconditioner applications each).
+                        Other values: PINT_ERR_INVALID                       */
   int reserved[2];
 } pint_opts;
 

@@ -512,6 +512,8 @@ static void newton_step(pint_problem p, const double* times, double* Y, const do
   PINT_REQUIRE(std::isfinite(o->lscheme_L) &&
                    (o->lscheme_L == 0.0 || p->kind == PINT_PROBLEM_RICHARDS),
                PINT_ERR_INVALID, "the L-scheme (lscheme_L != 0) applies to Richards problems");
+  PINT_REQUIRE(o->solver >= PINT_SOLVER_GMRES && o->solver <= PINT_SOLVER_BICGSTAB,
+               PINT_ERR_INVALID, "solver");
   pint_op op = p->op;
   pint_ctx ctx = p->ctx;
   const int s = op->s;

@@ -1309,6 +1309,210 @@ static InnerResult block_cg(pint_op op, const pint_opts* o, KrylovWork* w, cudaS
   return res;
 }
 
+// ------------------------------------------------ block BiCGStab (inner)
+// Coefficients of one block BiCGStab iteration from the Gram blocks
+//   H1 = [V Rh]^T Rt (2s x s)  and  H2 = [S T Rt]^T T (3s x s):
+// G = Rt^T V is the transpose of the top block of H1. Stage 0 solves
+// G alpha = Rt^T Rh; stage 1 forms omega = <T, S>_F / <T, T>_F and solves
+// G beta = -Rt^T T. Columns deflated at the start (zero diagonal of the
+// CholQR factor C) are inactive: identity rows and columns of G, zero rows
+// of the right-hand side. Gaussian elimination with partial pivoting on
+// [G | rhs] in one CTA; a zero or non-finite pivot sets flag[1].
+// Co holds four row-major s x s blocks: alpha, omega I, beta, -omega beta.
+__global__ void __launch_bounds__(256)
+k_bicg_coef(int s, int stage, const double* __restrict__ H1, const double* __restrict__ H2,
+            const double* __restrict__ C, double* __restrict__ Co, int* __restrict__ flag) {
+  __shared__ double A[kMaxS][2 * kMaxS + 1];
+  __shared__ double mult[kMaxS];
+  __shared__ int act[kMaxS];
+  __shared__ double om;
+  __shared__ int bad, piv;
+  const int t = threadIdx.x, w2 = 2 * s;
+  if (t < s) act[t] = C[t * s + t] != 0.0 ? 1 : 0;
+  if (t == 0) {
+    bad = 0;
+    om = 0.0;
+    if (stage == 1) {
+      double ts = 0.0, tt = 0.0;
+      for (int i = 0; i < s; ++i) {
+        ts += H2[i * s + i];
+        tt += H2[(s + i) * s + i];
+      }
+      om = tt > 0.0 ? ts / tt : 0.0;
+      if (!isfinite(om)) bad = 1;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < s * w2; e += blockDim.x) {
+    const int k = e / w2, c = e - k * w2;
+    double v;
+    if (c < s) {
+      v = (act[k] && act[c]) ? H1[c * s + k] : (k == c ? 1.0 : 0.0);
+    } else {
+      const int j = c - s;
+      v = !act[k] ? 0.0 : (stage == 0 ? H1[(s + j) * s + k] : -H2[(2 * s + k) * s + j]);
+    }
+    A[k][c] = v;
+  }
+  __syncthreads();
+  for (int k = 0; k < s; ++k) {
+    if (t == 0) {
+      int p = k;
+      double best = fabs(A[k][k]);
+      for (int i = k + 1; i < s; ++i)
+        if (fabs(A[i][k]) > best) {
+          best = fabs(A[i][k]);
+          p = i;
+        }
+      piv = p;
+      if (!(best > 0.0) || !isfinite(best)) bad = 1;
+    }
+    __syncthreads();
+    if (bad) break;                     // read after the barrier: uniform
+    if (piv != k && t < w2) {
+      const double x = A[k][t];
+      A[k][t] = A[piv][t];
+      A[piv][t] = x;
+    }
+    __syncthreads();
+    if (t > k && t < s) mult[t] = A[t][k] / A[k][k];
+    __syncthreads();
+    const int wc = w2 - k - 1;          // columns k+1 .. 2s-1
+    for (int e = t; e < (s - k - 1) * wc; e += blockDim.x) {
+      const int i = k + 1 + e / wc, c = k + 1 + e % wc;
+      A[i][c] -= mult[i] * A[k][c];
+    }
+    __syncthreads();
+  }
+  if (t < s && !bad) {                  // back substitution, one right-hand side per thread
+    for (int k = s - 1; k >= 0; --k) {
+      double v = A[k][s + t];
+      for (int c = k + 1; c < s; ++c) v -= A[k][c] * A[c][s + t];
+      A[k][s + t] = v / A[k][k];
+    }
+  }
+  __syncthreads();
+  if (bad && t == 0) flag[1] = 1;
+  for (int e = t; e < s * s; e += blockDim.x) {
+    const int i = e / s, j = e - i * s;
+    const double x = bad ? 0.0 : A[i][s + j];
+    if (stage == 0) {
+      Co[e] = x;
+    } else {
+      Co[s * s + e] = i == j ? om : 0.0;
+      Co[2 * s * s + e] = x;
+      Co[3 * s * s + e] = -om * x;
+    }
+  }
+}
+
+// Block BiCGStab with right preconditioning (Guennouni, Jbilou and Sadok,
+// ETNA 16, 2003) on the unit-column right-hand side Rs of a nonsymmetric J.
+// Rs = Q0 C by CholQR2 with deflation, so dependent or zero columns leave the
+// block before it starts; the iteration solves J Xh = Q0 with the shadow
+// block Rt = Q0 and returns Xk = Xh C:
+//   Rh = P = Q0;  repeat: Ph = M^-1 P, V = J Ph, alpha = (Rt^T V)^-1 Rt^T Rh,
+//   S = Rh - V alpha, Sh = M^-1 S, T = J Sh, omega = <T, S>_F / <T, T>_F,
+//   Xh += Ph alpha + omega Sh, Rh = S - omega T (converged when every column
+//   of Rh C is <= inner_tol), beta = -(Rt^T V)^-1 Rt^T T,
+//   P = Rh + (P - omega V) beta.
+// With Jacobi the matrix is the column-scaled J D^-1, as in block GMRES.
+// Basis blocks: 0 P, 1 V, 2 Rh (S), 3 T, 4 Rt, 5 Ph (then the new P), 6 Sh,
+// 7 Xh, 8 Rh C. The runs (V, Rh), (S, T, Rt), (Ph, Sh) and (P, V) are
+// adjacent, so each Gram product and block update is a single launch.
+static InnerResult block_bicgstab(pint_op op, const pint_opts* o, KrylovWork* w,
+                                  cudaStream_t st) {
+  pint_ctx ctx = op->ctx;
+  const int64_t n = op->n;
+  const int s = op->s, prec = o->precision;
+  const int vprec = prec == PINT_FP64 ? PINT_FP64 : PINT_FP32;
+  const bool jac = o->precond == PINT_PC_JACOBI;
+  const bool ilu = o->precond == PINT_PC_ILU0;
+  const int64_t bs = w->bs, np = w->n_pad, ns = n * s;
+  const size_t es = w->es;
+  PINT_REQUIRE(w->m >= 8, PINT_ERR_INVALID, "block BiCGStab needs restart >= 8 (work blocks)");
+  auto Vb = [&](int b) { return (void*)((char*)w->V + (size_t)b * bs * es); };
+  void* Pb = Vb(0);
+  void* Vv = Vb(1);
+  void* Rh = Vb(2);
+  void* Tb = Vb(3);
+  void* Rt = Vb(4);
+  void* Ph = Vb(5);
+  void* Sh = Vb(6);
+  void* Xh = Vb(7);
+  void* Rc = Vb(8);
+  double* Co = w->Yls;
+  auto copy = [&](void* dst, const void* src) {
+    PINT_CUDA(cudaMemcpyAsync(dst, src, es * ns, cudaMemcpyDeviceToDevice, st));
+  };
+  auto coef = [&](int stage) {
+    ProfScope ps(ctx, PF_HESS, 0.0, 2.0 * s * s * s, st);
+    k_bicg_coef<<<1, 256, 0, st>>>(s, stage, w->Hg1, w->Hg2, w->S, Co, w->flag);
+    check_launch("k_bicg_coef");
+    ctx->launches += 1;
+  };
+  if (s < w->s && np > n)          // narrower than the allocation: clear the padded rows
+    for (int b = 0; b < 9; ++b)
+      PINT_CUDA(cudaMemsetAsync((char*)Vb(b) + es * (size_t)ns, 0, es * (size_t)(np - n) * s, st));
+  PINT_CUDA(cudaMemsetAsync(w->flag, 0, 64, st));
+  PINT_CUDA(cudaMemsetAsync(w->defl, 0, 64, st));
+  PINT_CUDA(cudaMemsetAsync(Xh, 0, es * ns, st));
+  copy(Rt, w->Rs);
+  cholqr2(ctx, vprec, n, s, Rt, w->S, w->defl, st, np);                     // Rs = Q0 C
+  copy(Rh, Rt);
+  copy(Pb, Rt);
+  InnerResult res{0, 1, false, 0};
+  while (res.its < o->max_inner) {
+    if (ilu) ilu_apply(op, prec, Pb, Ph, st);                                // Ph = M^-1 P
+    launch_inner_spmm(op, prec, jac, ilu ? Ph : Pb, Vv, nullptr, st);         // V = J Ph
+    launch_gram(ctx, vprec, n, s, 2, Vv, bs, Rt, w->Hg1, st, np);             // [V Rh]^T Rt
+    coef(0);                                                                  // alpha
+    launch_update(ctx, vprec, n, s, 1, Vv, bs, Co, Rh, 0, st);                // S = Rh - V alpha
+    if (ilu) ilu_apply(op, prec, Rh, Sh, st);                                // Sh = M^-1 S
+    launch_inner_spmm(op, prec, jac, ilu ? Sh : Rh, Tb, nullptr, st);         // T = J Sh
+    launch_gram(ctx, vprec, n, s, 3, Rh, bs, Tb, w->Hg2, st, np);             // [S T Rt]^T T
+    coef(1);                                                                  // omega, beta
+    if (ilu) {
+      launch_update(ctx, vprec, n, s, 2, Ph, bs, Co, Xh, 2, st);              // Xh += [Ph Sh] [alpha; omega I]
+    } else {
+      launch_update(ctx, vprec, n, s, 1, Pb, bs, Co, Xh, 2, st);              // Xh += P alpha
+      launch_update(ctx, vprec, n, s, 1, Rh, bs, Co + s * s, Xh, 2, st);      // Xh += omega S
+    }
+    launch_update(ctx, vprec, n, s, 1, Tb, bs, Co + s * s, Rh, 0, st);        // Rh = S - omega T
+    launch_update(ctx, vprec, n, s, 1, Rh, bs, w->S, Rc, 1, st);              // Rh C
+    launch_colnorm(ctx, vprec, n, s, Rc, w->est, st);
+    res.its += 1;
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_small, w->est, 8 * s, cudaMemcpyDeviceToHost, st));
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 2, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                              st));
+    PINT_CUDA(cudaStreamSynchronize(st));
+    PINT_REQUIRE(ctx->h_flag[2] == 0, PINT_ERR_TIMEOUT,
+                 "bulk-copy wait in the Gram kernel exceeded its time budget");
+    if (ilu) ilu_check(op);
+    PINT_REQUIRE(ctx->h_flag[1] == 0, PINT_ERR_BREAKDOWN,
+                 "singular s x s system (Rt^T V) in block BiCGStab");
+    bool conv = true;
+    for (int k = 0; k < s; ++k) {
+      PINT_REQUIRE(std::isfinite(ctx->h_small[k]), PINT_ERR_BREAKDOWN,
+                   "non-finite residual in block BiCGStab");
+      if (!(ctx->h_small[k] <= o->inner_tol)) conv = false;   // columns of Rs are unit
+    }
+    if (conv) {
+      res.converged = true;
+      break;
+    }
+    copy(Ph, Rh);
+    launch_update(ctx, vprec, n, s, 2, Pb, bs, Co + 2 * s * s, Ph, 2, st);   // Rh + [P V][beta; -omega beta]
+    copy(Pb, Ph);
+  }
+  launch_update(ctx, vprec, n, s, 1, Xh, bs, w->S, w->Xk, 1, st);            // Xk = Xh C
+  PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->defl, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PINT_CUDA(cudaStreamSynchronize(st));
+  res.deflations = ctx->h_flag[0];
+  return res;
+}
+
 InnerResult inner_solve(pint_op op, const pint_opts* o, const double* R, const double* rnorm_dev,
                         double* /*unused*/, cudaStream_t st) {
   KrylovWork* w = ensure_work(op, o->precision == PINT_FP64 ? PINT_FP64 : PINT_FP32, o->restart);
@@ -1322,6 +1526,7 @@ InnerResult inner_solve(pint_op op, const pint_opts* o, const double* R, const d
     launch_scale_cast(n, s, R, (float*)w->Rs, rnorm_dev, st, op->ctx);
   }
   if (o->solver == PINT_SOLVER_CG) return block_cg(op, o, w, st);
+  if (o->solver == PINT_SOLVER_BICGSTAB) return block_bicgstab(op, o, w, st);
   return gmres(op, o, w, st);
 }
 
@@ -1357,6 +1562,8 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
                "precision");
   PINT_REQUIRE(o->precond >= PINT_PC_NONE && o->precond <= PINT_PC_ILU0, PINT_ERR_INVALID,
                "precond");
+  PINT_REQUIRE(o->solver >= PINT_SOLVER_GMRES && o->solver <= PINT_SOLVER_BICGSTAB,
+               PINT_ERR_INVALID, "solver");
   const int64_t n = op->n;
   const int s = op->s;
   if (!op->j_valid) build_inner(op, st);
@@ -1442,8 +1649,9 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
     cycles += ir.cycles;
     defl += ir.deflations;
     const int vprec = w->prec;
-    // block GMRES with Jacobi solves for the scaled variable D X (right
-    // preconditioning fused into the SpMM); block CG solves for X itself
+    // block GMRES and block BiCGStab with Jacobi solve for the scaled
+    // variable D X (right preconditioning fused into the SpMM); block CG
+    // solves for X itself
     const bool scaled = o->precond == PINT_PC_JACOBI && o->solver != PINT_SOLVER_CG;
     launch_outer_update(vprec, n, sw, Y, w->Xk, w->rnorm + c0, scaled ? op->Jinvdiag : nullptr,
                         st, ctx, s, c0);

@@ -57,11 +57,31 @@ def test_traffic_lookup_only_for_the_captured_sources():
     for wl, fams in d.items():
         for fam, e in fams.items():
             got = bench.ncu_traffic(fam, wl)
-            if e["source_hash"] == bench.source_hash():
+            if e["source_hash"] == bench.source_hash(fam):
                 assert got == e["dram_bytes_per_launch"] and got > 0
             else:
                 assert got is None
     assert bench.ncu_traffic("ilu", "no-such-workload") is None
+    assert bench.ncu_traffic("gram", "convdiff3d_n128_s8_ilu0") is None
+
+
+def test_source_hash_follows_only_the_family_sources(tmp_path, monkeypatch):
+    """A change in another translation unit leaves a family's hash alone; a
+    change in one of its own sources changes it."""
+    import shutil
+    for fam, files in bench.KERNEL_SOURCES.items():
+        for rel in files:
+            dst = tmp_path / rel
+            dst.parent.mkdir(parents=True, exist_ok=True)
+            shutil.copy(os.path.join(ROOT, rel), dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    before = {f: bench.source_hash(f) for f in bench.KERNEL_SOURCES}
+    (tmp_path / "paper_2504_02117_gb300/csrc/krylov.cu").write_text("// another unit\n")
+    assert {f: bench.source_hash(f) for f in bench.KERNEL_SOURCES} == before
+    with open(tmp_path / "paper_2504_02117_gb300/csrc/ilu.cu", "a") as fh:
+        fh.write("// changed\n")
+    assert bench.source_hash("ilu") != before["ilu"]
+    assert bench.source_hash("spmm") == before["spmm"]
 
 
 def test_measured_peak_is_read():

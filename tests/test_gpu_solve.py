@@ -245,3 +245,82 @@ def test_slab_block_cg_symmetric_operator(P, ctx, prec, pc, s):
         assert st.inner_its <= 1.5 * info["inner"] + 5
     finally:
         P.pint_operator_destroy(op)
+
+
+@pytest.mark.parametrize("prec,pc", [("fp64", "ilu0"), ("fp64", "jacobi"), ("fp32", "ilu0"),
+                                     ("fp32", "jacobi"), ("fp64", "none")])
+@pytest.mark.parametrize("s", [1, 3, 8])
+def test_slab_block_bicgstab_nonsymmetric_operator(P, ctx, prec, pc, s):
+    """Convection-dominated J (upwind, nonsymmetric): the slab with block
+    BiCGStab inner solves (the paper's solver for this problem, Sec. 4.1)
+    equals sequential stepping, with an effort close to the oracle's block
+    BiCGStab."""
+    import torch
+    dims = (12, 10, 9)
+    op, K, n, A, A1, A2, B = _setup(P, ctx, dims, s, 1e-3, v=(20.0, 10.0, 5.0))
+    try:
+        Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
+        o = P.pint_opts_default()
+        o.tol = 1e-12
+        o.inner_tol = 1e-2 if s > 1 else 1e-6
+        o.precond = {"ilu0": P.PINT_PC_ILU0, "jacobi": P.PINT_PC_JACOBI,
+                     "none": P.PINT_PC_NONE}[pc]
+        o.precision = P.PINT_FP64 if prec == "fp64" else P.PINT_FP32
+        o.solver = P.PINT_SOLVER_BICGSTAB
+        st = P.pint_solve_block(ctx, op, _dev(B), None, Y, o, raise_on_nonconvergence=True)
+        Yref = slab.sequential_dirk_linear(K, np.ones(n), A, 1e-3, np.zeros(n), B)
+        err = _colerr(Y.cpu().numpy(), Yref)
+        assert np.all(err < 1e-9), err
+        Yo, info = slab.slab_solve(K, np.ones(n), A1, A2, B, None, tol=1e-12,
+                                   inner_tol=o.inner_tol, precond=pc, solver="bicgstab")
+        assert abs(st.outer_its - info["outer"]) <= 2
+        assert st.inner_its <= 1.5 * info["inner"] + 5
+    finally:
+        P.pint_operator_destroy(op)
+
+
+def test_block_bicgstab_dependent_and_zero_columns(P, ctx):
+    """Dependent and zero right-hand sides leave the block BiCGStab block at
+    the start (CholQR2 deflation) instead of making Rt^T V singular."""
+    import torch
+    dims = (12, 12, 1)
+    n = 144
+    D = np.ones(dims[::-1])
+    K = fv.convdiff_matrix(dims, D, (20.0, 10.0, 0.0))
+    op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), (20.0, 10.0, 0.0))
+    try:
+        s, tau = 4, 1e-2
+        P.pint_set_coupling(ctx, op, np.eye(s) / tau, np.eye(s))
+        b = synth.uniform(9, n)
+        B = np.column_stack([b, 2 * b, np.zeros(n), -b])
+        Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
+        o = P.pint_opts_default()
+        o.tol = 1e-12
+        o.precond = P.PINT_PC_ILU0
+        o.solver = P.PINT_SOLVER_BICGSTAB
+        st = P.pint_solve_block(ctx, op, _dev(B), None, Y, o, raise_on_nonconvergence=True)
+        assert st.deflations > 0
+        y = sp.linalg.spsolve((sp.identity(n) / tau + K).tocsc(), b)
+        np.testing.assert_allclose(Y.cpu().numpy(), np.column_stack([y, 2 * y, 0 * y, -y]),
+                                   rtol=1e-9, atol=1e-12)
+    finally:
+        P.pint_operator_destroy(op)
+
+
+def test_solver_option_is_validated(P, ctx):
+    import torch
+    op, K, n, A, A1, A2, B = _setup(P, ctx, (6, 5, 1), 2, 1e-2)
+    try:
+        Y = torch.zeros(n, 2, device="cuda", dtype=torch.float64)
+        o = P.pint_opts_default()
+        o.solver = 7
+        with pytest.raises(P.PintError) as ei:
+            P.pint_solve_block(ctx, op, _dev(B), None, Y, o)
+        assert ei.value.code == P.PINT_ERR_INVALID
+        o.solver = P.PINT_SOLVER_BICGSTAB
+        o.restart = 4                          # nine work blocks need restart >= 8
+        with pytest.raises(P.PintError) as ei:
+            P.pint_solve_block(ctx, op, _dev(B), None, Y, o)
+        assert ei.value.code == P.PINT_ERR_INVALID
+    finally:
+        P.pint_operator_destroy(op)
