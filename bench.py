@@ -44,20 +44,20 @@ WORKLOADS = {
     # name: (cells per direction, s, precond, precision, description)
     "convdiff3d": (128, 8, "ilu0", "fp32",
                    "3-D conv.-diffusion {n}^3, log-normal D (sigma 1), implicit Euler tau=1e-3, "
-                   "slab of s steps, block GMRES(30)+{pc}, tol 1e-10"),
+                   "slab of s steps, {solver}+{pc}, tol 1e-10"),
     "convdiff2d": (64, 4, "jacobi", "fp64",
                    "2-D conv.-diffusion {n}^2, D=1, v=(1,0.5), implicit Euler tau=1e-3, slab of "
-                   "s steps, block GMRES(30)+{pc}, tol 1e-10"),
+                   "s steps, {solver}+{pc}, tol 1e-10"),
     "diffreact": (512, 2, "ilu0", "fp32",
                   "2-D diffusion-reaction {n}^2, SDIRK2 window of s=2 stages pipelined over 4 "
-                  "steps (Algorithm 1), Newton + block GMRES(30)+{pc}"),
+                  "steps (Algorithm 1), Newton + {solver}+{pc}"),
     "richards": (96, 8, "ilu0", "fp32",
                  "3-D Richards {n}^3, van Genuchten alpha=1 n=2, K_S=exp(2g) correlated 8 "
                  "cells, implicit Euler tau=1/96 window s=8 pipelined over 8 steps, L-scheme + "
-                 "block GMRES(30)+{pc}"),
+                 "{solver}+{pc}"),
     "serve": (128, 16, "ilu0", "fp32",
               "serving: seeded Poisson stream of slab-solve requests (3-D conv.-diffusion, "
-              "grids 32^3-{n}^3, s in 2..16, FP32 or FP64 inner solves, GMRES(30)+{pc}, "
+              "grids 32^3-{n}^3, s in 2..16, FP32 or FP64 inner solves, {solver}+{pc}, "
               "tol 1e-10), continuous batching over CUDA streams"),
 }
 
@@ -264,6 +264,11 @@ def measured_peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def solver_label(args):
+    return {"gmres": f"block GMRES({args.restart})", "cg": "block CG",
+            "bicgstab": "block BiCGStab"}[args.solver]
 
 
 def solver_code(P, name):
@@ -497,7 +502,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    desc = WORKLOADS[args.workload][4].format(n=args.n, pc=args.precond)
+    desc = WORKLOADS[args.workload][4].format(n=args.n, pc=args.precond,
+                                             solver=solver_label(args))
     wl_name = f"{args.workload}_n{args.n}_s{args.s}_{args.precond}"
 
     if args.impl == "reference":
@@ -706,6 +712,8 @@ def sweep(P, ctx, args, w0):
             o.inner_tol = inner_tol_for(ns, s)
             o.precond = P.PINT_PC_ILU0
             o.precision = P.PINT_FP64 if prec_name == "fp64" else P.PINT_FP32
+            o.restart = args.restart
+            o.solver = solver_code(P, args.solver)
             Bd = torch.tensor(synth.rhs_block(w), device="cuda", dtype=torch.float64)
             Y = torch.zeros(w.n, s, device="cuda", dtype=torch.float64)
             P.pint_solve_block(ctx, op, Bd, None, Y, o)
@@ -752,7 +760,8 @@ def serve_main(args, world, rank, local, cpu, desc):
         return serve.SlabRequest(rid=spec["rid"], arrival=spec["arrival"], dims=w.dims,
                                  s=spec["s"], precision=spec["precision"], D=D, B=B,
                                  velocity=w.velocity, tau=w.tau, tol=w.tol,
-                                 inner_tol=inner_tol_for(ns, spec["s"]), restart=args.restart)
+                                 inner_tol=inner_tol_for(ns, spec["s"]), restart=args.restart,
+                                 solver=args.solver)
 
     grids = tuple(g for g in (32, 48, 64, 96, 128) if g <= args.n)
     specs = synth.request_stream(5 + rank, args.requests, args.rate, grids=grids)
@@ -786,7 +795,7 @@ def serve_main(args, world, rank, local, cpu, desc):
         "warmup": args.warmup, "ms_per_step": span * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+fp32/f64", "data": "synthetic",
         "config": {"workload": f"serve_{args.requests}req_rate{args.rate:g}_slots{args.slots}",
-                   "description": desc.format(n=args.n, pc=args.precond), "grids": list(grids),
+                   "description": desc, "grids": list(grids),
                    "widths": [2, 4, 8, 16], "precisions": ["fp32", "fp64"],
                    "restart": args.restart, "parallelism": f"replicas x{world}",
                    "l2": "mixed request sizes, no flush"},

@@ -35,6 +35,7 @@ class SlabRequest:
     tol: float = 1e-10
     inner_tol: float = 1e-2
     restart: int = 30
+    solver: str = "gmres"          # inner solver: "gmres", "cg" or "bicgstab"
     # filled by the server
     admitted: Optional[float] = None
     finished: Optional[float] = None
@@ -101,6 +102,8 @@ class SlabServer:
                 o.restart = r.restart
                 o.precond = P.PINT_PC_ILU0
                 o.precision = P.PINT_FP64 if r.precision == "fp64" else P.PINT_FP32
+                o.solver = {"gmres": P.PINT_SOLVER_GMRES, "cg": P.PINT_SOLVER_CG,
+                            "bicgstab": P.PINT_SOLVER_BICGSTAB}[r.solver]
                 res = P.pint_solve_block(ctx, op, Bd, None, Y, o, stream=st)
                 out = {"status": res.status, "outer": res.outer_its, "inner": res.inner_its}
                 if self.keep:
