@@ -257,6 +257,31 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- helpers
+NOMINAL_HBM_GBS = 7900.0      # GB300 HBM3e, nominal (context for the measured peak)
+
+
+def spbop_bytes(nnz, n, k, val_bytes=8, vec_bytes=8, idx_bytes=4, vector_reuse=True,
+                write_result=True):
+    """Bytes one sparse block operator product Z = A X with k columns moves
+    (CSR): values and column indices once, the row pointer, X and Z. The
+    defaults are the library's algorithmic count for its inner SpMM (X read
+    once, Z written once). With vector_reuse=False every nonzero loads its k
+    entries of X, and with no index bytes and no result writes this is the
+    count of the paper's performance analysis (Sec. Performance analysis:
+    one matrix entry and k block-vector entries per nonzero)."""
+    b = nnz * (val_bytes + idx_bytes) + (n + 1) * idx_bytes
+    b += (n if vector_reuse else nnz) * k * vec_bytes
+    if write_result:
+        b += n * k * vec_bytes
+    return b
+
+
+def spbop_ai(nnz, n, k, **kw):
+    """Arithmetic intensity (flop per byte) of the sparse block product:
+    2 k flops per nonzero over spbop_bytes."""
+    return 2.0 * nnz * k / spbop_bytes(nnz, n, k, **kw)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -330,6 +355,7 @@ def roofline(fam, prof, hbm_peak, peak_kind, precision, workload):
                 "avg_launch_us": per_launch_s * 1e6}
     return {"kernel": fam, "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
             "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+            "frac_of_nominal": round(gbs / NOMINAL_HBM_GBS, 4),
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
             else "fallback 6.8 TB/s",
             "traffic": ncu_traffic(fam, workload), "algorithmic_bytes_per_launch": bytes_pl,
@@ -693,11 +719,14 @@ def precision_variant(P, case, args, stream, prec="fp64"):
 
 def sweep(P, ctx, args, w0):
     """One timed solve per (precision, s) on the same grid (after one warm-up
-    solve each): time-step*DOF/s and SpMM GB/s."""
+    solve each): time-step*DOF/s, SpMM GB/s and the SpMM's s-dependent
+    arithmetic-intensity roofline (flop per byte, achieved and attainable
+    GFLOP/s against the measured HBM peak, and the FP64 rate in FP64)."""
     import numpy as np
     import torch
     import synth
     res = []
+    hbm_peak, _ = measured_peaks()
     D = synth.diffusion_field(w0).ravel()
     for prec_name in ("fp64", "fp32"):
         for s in (1, 2, 4, 8, 16):
@@ -727,10 +756,21 @@ def sweep(P, ctx, args, w0):
             dt = time.perf_counter() - t
             P.pint_profile_enable(ctx, False)
             sp = P.pint_profile_read(ctx, 1)
+            gbs = sp["bytes"] / max(sp["ms"], 1e-9) / 1e6
+            eb = 8 if prec_name == "fp64" else 4
+            nnz = int(P.pint_operator_nnz(op))
+            # over all SpMM launches of the solve (narrowed inner solves launch
+            # narrower, lower-intensity products) and for a full-width launch
+            ai = sp["flops"] / max(sp["bytes"], 1.0)
+            ai_full = spbop_ai(nnz, w.n, s, val_bytes=eb, vec_bytes=eb)
+            roof = hbm_peak * ai
             res.append({"precision": prec_name, "s": s, "value": s * w.n / dt,
                         "solve_s": dt, "outer": st.outer_its, "inner": st.inner_its,
-                        "status": st.status,
-                        "spmm_GBs": sp["bytes"] / max(sp["ms"], 1e-9) / 1e6})
+                        "status": st.status, "spmm_GBs": gbs,
+                        "spmm_ai_flop_per_byte": ai, "spmm_ai_full_width": ai_full,
+                        "spmm_gflops": sp["flops"] / max(sp["ms"], 1e-9) / 1e6,
+                        "spmm_roof_gflops": min(roof, 1e3 * FP64_PEAK_TFLOPS)
+                        if prec_name == "fp64" else roof})
             P.pint_operator_destroy(op)
             del Bd, Y
     return res

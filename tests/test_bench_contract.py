@@ -90,3 +90,23 @@ def test_measured_peak_is_read():
         assert kind == "measured" and peak > 1000.0
     else:
         assert (peak, kind) == (6800.0, "fallback")
+
+
+def test_spbop_byte_model_reduces_to_the_papers_count():
+    """Without vector reuse, index bytes or result writes the byte count is
+    the paper's (one matrix entry and k vector entries per nonzero, Sec.
+    Performance analysis): AI 1/8 for the single vector (the spMV figure of
+    Sec. 1) and a gain of about 1.8 at k = 16; the library's own count for
+    the 128^3 inner SpMM at s = 8 in float32 is the 259 260 420 bytes its
+    profiler recorded for a full-width launch."""
+    paper = dict(idx_bytes=0, vector_reuse=False, write_result=False)
+    nnz, n = 14_581_760, 128 ** 3
+    assert bench.spbop_ai(nnz, n, 1, **paper) == 0.125
+    gain = bench.spbop_ai(nnz, n, 16, **paper) / bench.spbop_ai(nnz, n, 1, **paper)
+    assert 1.8 <= gain < 1.9
+    assert abs(bench.spbop_ai(nnz, n, 16, **paper) - 0.2353) < 1e-4
+    assert bench.spbop_bytes(nnz, n, 8, val_bytes=4, vec_bytes=4) == 259_260_420
+    # with X read once per row the intensity grows with k towards nnz / (n * vec_bytes)
+    ai = [bench.spbop_ai(nnz, n, k) for k in (1, 2, 4, 8, 16)]
+    assert all(a < b for a, b in zip(ai, ai[1:]))
+    assert ai[-1] < 2.0 * nnz / n / (2 * 8)
