@@ -159,7 +159,8 @@ def oracle_sample(args, n, reps=1):
         for _ in range(reps):
             t = time.perf_counter()
             newton.pipelined_block_newton(prob, A, c, tau, y0, G, s, tol=tol, inner_tol=1e-5,
-                                          precond=args.precond, restart=args.restart)
+                                          precond=args.precond, restart=args.restart,
+                                          solver=args.solver)
             times.append(time.perf_counter() - t)
         return {"n": n * n, "steps": G // 2, "times": times}
     dims = (n, n, n)
@@ -174,7 +175,8 @@ def oracle_sample(args, n, reps=1):
         t = time.perf_counter()
         newton.pipelined_block_newton(prob, A, c, 1.0 / 96.0, -z, G, s, tol=1e-5, inner_tol=1e-2,
                                       precond=args.precond, max_step=1.0, max_newton=150,
-                                      lscheme_L=vg.lipschitz(), restart=args.restart)
+                                      lscheme_L=vg.lipschitz(), restart=args.restart,
+                                      solver=args.solver)
         times.append(time.perf_counter() - t)
     return {"n": n ** 3, "steps": G, "times": times}
 

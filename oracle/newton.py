@@ -160,9 +160,13 @@ def linearisation(prob, alpha, beta, t, y, lscheme_L=None):
 
 def pipelined_block_newton(prob, A, c, tau, y0, nstages, s, tol=1e-8, inner_tol=1e-5,
                            precond="ilu0", restart=30, max_newton=50, inner_maxit=1000,
-                           max_step=None, lscheme_L=None):
+                           max_step=None, lscheme_L=None, solver="gmres"):
     """Algorithm 1 over `nstages` global stages with a window of s stages.
     Returns (stages N x nstages, stats dict).
+
+    solver: the inner block solver, "gmres" (block GMRES(restart)), "cg"
+    (block CG: the L-scheme matrix of Richards' equation and its ILU(0) are
+    symmetric positive definite) or "bicgstab" (block BiCGStab).
 
     max_step (reading, the paper gives no globalisation): when set, column k
     of each Newton update V is scaled by min(1, max_step / max_r |V_rk|). The
@@ -186,8 +190,14 @@ def pipelined_block_newton(prob, A, c, tau, y0, nstages, s, tol=1e-8, inner_tol=
                 break
             J = linearisation(prob, alpha, beta, times[0], Y[:, 0], lscheme_L)
             Pinv = krylov.make_preconditioner(J, precond)
-            V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R, inner_tol, restart,
-                                         inner_maxit)
+            if solver == "cg":
+                V, info = krylov.block_cg(lambda X: J @ X, Pinv, R, inner_tol, inner_maxit)
+            elif solver == "bicgstab":
+                V, info = krylov.block_bicgstab(lambda X: J @ X, Pinv, R, inner_tol,
+                                                inner_maxit)
+            else:
+                V, info = krylov.block_gmres(lambda X: J @ X, Pinv, R, inner_tol, restart,
+                                             inner_maxit)
             inner_its += info["iters"]
             if max_step:
                 vmax = np.max(np.abs(V), axis=0)

@@ -156,3 +156,35 @@ def test_pipelined_richards_lscheme_equals_sequential():
     # ||R_0|| <= 1e-10 ||B0_0|| ~ 4e-8 and ||J^-1|| <= 1 here (diag J >= alpha
     # theta' >= 1 on these heads): stage errors below 1e-7
     np.testing.assert_allclose(Ypl, Yseq, rtol=0, atol=1e-7)
+
+
+def test_pipelined_with_block_cg_and_bicgstab_equals_sequential():
+    """Algorithm 1 with the paper's other block solvers as inner solves:
+    block BiCGStab on the nonsymmetric diffusion-reaction Jacobian (the
+    window's identical trailing columns are deflated at the start of each
+    inner solve) and block CG on the symmetric positive definite L-scheme
+    matrix of Richards' equation; both reach the stages of sequential Newton
+    stepping."""
+    import synth
+    dims = (8, 8, 1)
+    prob = newton.DiffReactProblem(dims)
+    A, _, c = coupling.sdirk2()
+    y0 = np.full(64, 0.5)
+    Yseq, _ = newton.sequential_dirk_newton(prob, A, c, 0.01, y0, 6)
+    Ypl, st = newton.pipelined_block_newton(prob, A, c, 0.01, y0, 6, 2, tol=1e-12,
+                                            inner_tol=1e-6, solver="bicgstab")
+    assert st["inner"] > 0
+    np.testing.assert_allclose(Ypl, Yseq, rtol=1e-10, atol=1e-11)
+
+    dims = (6, 6, 6)
+    Ks = np.exp(2.0 * synth.correlated_field(4, dims[::-1], 2.0))
+    vg = fv.VanGenuchten(1.0, 2.0, 0.05, 0.4)
+    z, _ = fv.richards_cells(dims)
+    rprob = newton.RichardsProblem(dims, Ks, vg, 1 / 16)
+    A, _, c = coupling.implicit_euler()
+    Yseq, _ = newton.sequential_dirk_newton(rprob, A, c, 1 / 96, -z, 5)
+    Ypl, st = newton.pipelined_block_newton(rprob, A, c, 1 / 96, -z, 5, 4, tol=1e-10,
+                                            inner_tol=1e-8, max_newton=120, max_step=1.0,
+                                            lscheme_L=vg.lipschitz(), solver="cg")
+    assert max(st["newton"]) < 120
+    np.testing.assert_allclose(Ypl, Yseq, rtol=0, atol=1e-7)
