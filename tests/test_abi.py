@@ -79,3 +79,34 @@ def test_vg_lipschitz_host_call_matches_oracle():
         assert abs(L - fv.VanGenuchten(*prm).lipschitz()) <= 1e-12 * L
     with pytest.raises(P.PintError):
         P.pint_vg_lipschitz((1.0, 1.0, 0.05, 0.4))
+
+
+def test_struct_layout_matches_the_header(tmp_path):
+    """pint_opts and pint_stats as the binding declares them have the C
+    compiler's sizes and field offsets (a C program compiled against
+    include/pint.h prints them)."""
+    import shutil
+    import subprocess
+    import paper_2504_02117_gb300 as P
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {"pint_opts": [f[0] for f in P.pint_opts._fields_],
+              "pint_stats": [f[0] for f in P.pint_stats._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pint.h"', "int main(void) {"]
+    for st, names in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for n in names:
+            lines.append(f'  printf("{st} {n} %zu\\n", offsetof({st}, {n}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out.splitlines()}
+    for st, cls in (("pint_opts", P.pint_opts), ("pint_stats", P.pint_stats)):
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for n in fields[st]:
+            assert got[(st, n)] == getattr(cls, n).offset, (st, n)
