@@ -188,8 +188,9 @@ int pint_apply_coupled(pint_op op, const double* Y, const double* B,
                        const double* B0, double* R, void* stream);
 
 /* Linear slab solve (Eq. matrix-fixed-point-equation as defect correction,
- * block GMRES(m) inner solve on J = alpha M + beta K with right Jacobi or
- * ILU(0) preconditioning). Y: in = initial guess, out = solution. Stops when
+ * inner solves on J = alpha M + beta K by the block solver opts->solver:
+ * block GMRES(m) by default, block BiCGStab or block CG; Jacobi or ILU(0)
+ * preconditioning). Y: in = initial guess, out = solution. Stops when
  * every column satisfies ||R_k|| <= tol ||F_k|| (absolute tol if F_k = 0).
  * When A1 and A2 are lower triangular, a converged leading run of columns
  * stays converged (column k's residual depends on columns 0..k only): the

@@ -110,3 +110,30 @@ def test_struct_layout_matches_the_header(tmp_path):
         assert got[(st, "size")] == ctypes.sizeof(cls), st
         for n in fields[st]:
             assert got[(st, n)] == getattr(cls, n).offset, (st, n)
+
+
+def test_plain_c_client_compiles_and_links(tmp_path):
+    """The boundary is usable from C alone: tests/c/slab_client.c (a slab
+    solve through the C ABI, device buffers from the CUDA runtime) compiles
+    with a C compiler against include/pint.h and links against libpint.so."""
+    import shutil
+    import subprocess
+    import __graft_entry__
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if cc is None or not os.path.isdir(os.path.join(cuda, "include")):
+        pytest.skip("no C compiler or CUDA toolkit")
+    lib_path = __graft_entry__._build_module().build()
+    libdir = os.path.dirname(lib_path)
+    cudalib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                    if os.path.isdir(d)), None)
+    if cudalib is None:
+        pytest.skip("no CUDA runtime library directory")
+    exe = tmp_path / "slab_client"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-I", os.path.join(cuda, "include"),
+                        os.path.join(ROOT, "tests", "c", "slab_client.c"), "-o", str(exe),
+                        "-L", libdir, "-lpint", "-L", cudalib, "-lcudart", "-lm",
+                        f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert exe.exists()
