@@ -31,7 +31,8 @@ import numpy as np
 # Butcher tableaux
 # --------------------------------------------------------------------------
 def implicit_euler():
-    """Implicit Euler as a 1-stage stiffly accurate DIRK: A=[[1]], c=[1]."""
+    """Implicit Euler as a 1-stage stiffly accurate DIRK (Eq. stiffly-accurate-DIRK):
+    A=[[1]], c=[1]."""
     return np.array([[1.0]]), np.array([1.0]), np.array([1.0])
 
 
@@ -43,7 +44,9 @@ def theta_method(theta: float):
 
 
 def sdirk2():
-    """Two-stage L-stable SDIRK, gamma = 1 - 1/sqrt(2), stiffly accurate."""
+    """Two-stage L-stable SDIRK, gamma = 1 - 1/sqrt(2), stiffly accurate in the
+    sense of Eq. stiffly-accurate-DIRK (the diffusion-reaction workload's
+    integrator, standing in for Sec. 4.2's Crank-Nicolson)."""
     g = 1.0 - 1.0 / math.sqrt(2.0)
     A = np.array([[g, 0.0], [1.0 - g, g]])
     return A, A[-1].copy(), np.array([g, 1.0])
@@ -58,14 +61,16 @@ def is_stiffly_accurate(A, b) -> bool:
 # One step, all stages (Eq. general-system-time-steps)
 # --------------------------------------------------------------------------
 def single_step_matrices(A, tau: float):
-    """A1 = I_m / tau and A2 = A for the m stages of one step."""
+    """A1 = I_m / tau and A2 = A for the m stages of one step (Eq.
+    general-system-time-steps with a single step)."""
     A = np.asarray(A, dtype=np.float64)
     m = A.shape[0]
     return np.eye(m) / tau, A.copy()
 
 
 def eliminate_explicit_first_stage(A):
-    """Split A with a_11 = 0 into (A_impl, e) with e_i = a_{i+1,1}, i=1..m-1.
+    """Split A with a_11 = 0 into (A_impl, e) with e_i = a_{i+1,1}, i=1..m-1
+    (the elimination of the explicit first stage, Sec. 2.1).
 
     After the elimination the stage system has one stage less, operator
     (I/tau (x) M + A_impl (x) K), and B0 gains a_{i1}(b^n - K y^n) in row i.
@@ -80,7 +85,8 @@ def eliminate_explicit_first_stage(A):
 # s consecutive steps (Eq. time-stepping-matrices-multiple-parallel-time-steps)
 # --------------------------------------------------------------------------
 def multistep_matrices(A, s: int, tau: float, eliminate_first: bool = False):
-    """Return (A1, A2, e) for s consecutive steps of the DIRK method A.
+    """Return (A1, A2, e) for s consecutive steps of the DIRK method A
+    (Eq. time-stepping-matrices-multiple-parallel-time-steps).
 
     Block (n, n) of A1 is I_m'/tau, block (n, n-1) holds -1/tau in every row of
     its last column (y^{n} = y^{(n-1,m)} for stiffly accurate methods). A2 is
@@ -118,7 +124,8 @@ def theta_example_matrices(theta: float, s: int, tau: float):
 
 
 def theta_example_B0(theta, tau, Mdiag, K, yn, bn, s):
-    """B0 = ((1/tau) M y^n - (1-theta)(K y^n - b^n), 0, ..., 0)."""
+    """B0 = ((1/tau) M y^n - (1-theta)(K y^n - b^n), 0, ..., 0) of Example
+    ex:time-stepping-matrices."""
     B0 = np.zeros((len(yn), s))
     B0[:, 0] = Mdiag * yn / tau - (1.0 - theta) * (K @ yn - bn)
     return B0
@@ -147,7 +154,8 @@ def stage_of(g: int, m: int):
 
 
 def window_matrices(A, c, tau: float, g0: int, s: int):
-    """A1, A2 (s x s) and the B0 recipe of the window of s consecutive stages
+    """A1, A2 (s x s) and the B0 recipe (Eq. matrix-equation-pipelining,
+    Algorithm 1) of the window of s consecutive stages
     starting at global stage g0 (0-based) of the stiffly accurate DIRK (A, c).
 
     Stage (n, k) reads (1/tau)(M(y^{(n,k)}) - M(y^n)) + sum_{j<=k} a_kj

@@ -27,6 +27,8 @@ import scipy.sparse as sp
 
 
 def grid_index(dims):
+    """Natural x-fastest cell numbering of an nx x ny x nz grid, as an array
+    of shape (nz, ny, nx) (the matrix-based FV setting of Sec. 1)."""
     nx, ny, nz = dims
     return np.arange(nx * ny * nz).reshape(nz, ny, nx)
 
@@ -67,7 +69,8 @@ def _csr(rows, cols, vals, n):
 
 
 def pattern(dims):
-    """Sparsity pattern of the 5- / 7-point stencil (all ones)."""
+    """Sparsity pattern of the 5- / 7-point stencil (all ones): the pattern K
+    shares with every Jacobian of Sec. 2.2."""
     n = int(np.prod(dims))
     rows, cols, vals = [np.arange(n)], [np.arange(n)], [np.ones(n)]
     for _, P, Q in _faces(dims):
@@ -81,7 +84,9 @@ def pattern(dims):
 # Linear convection-diffusion: K u = -div(D grad u) + div(v u)
 # --------------------------------------------------------------------------
 def convdiff_matrix(dims, D, velocity):
-    """Stiffness matrix K of -div(D grad u) + div(v u) on [0,1]^d.
+    """Stiffness matrix K of -div(D grad u) + div(v u) on [0,1]^d (the linear
+    problem of Sec. 4.1; the paper gives no FV details, so the cell-centred
+    scheme below is this module's reading).
 
     D has shape (nz, ny, nx); velocity is (vx, vy, vz), constant. Homogeneous
     Dirichlet on every boundary face for diffusion, upwind convection with zero
@@ -135,7 +140,8 @@ def circle_source(dims, t):
 
 
 def diffreact_f(dims, t, u):
-    """f(t,u) with M u' + f(t,u) = 0, M = I:
+    """f(t,u) with M u' + f(t,u) = 0, M = I, for the diffusion-reaction problem
+    of Sec. 4.2:
     f_P = -sum_Q a_PQ (u_Q - u_P)/h^2 - u_P (1 - u_P) - src_P(t),
     a_PQ = 1 + (u_P^2 + u_Q^2)/2, zero-flux boundary."""
     h = 1.0 / dims[0]
@@ -149,7 +155,8 @@ def diffreact_f(dims, t, u):
 
 
 def diffreact_jacobian(dims, t, u):
-    """Df(t,u) (CSR) of diffreact_f."""
+    """Df(t,u) (CSR) of diffreact_f: the Jacobian of Algorithm 1's simplified
+    Newton step (Sec. 2.2), in K's pattern."""
     h = 1.0 / dims[0]
     n = int(np.prod(dims))
     rows, cols, vals = [np.arange(n)], [np.arange(n)], [-(1.0 - 2.0 * u)]
@@ -241,7 +248,8 @@ def richards_dirichlet_head(t, dt_D):
 
 
 def richards_cells(dims):
-    """Cell-centre heights z and the top-patch mask (top layer, x < 1/2, y < 1/2)."""
+    """Cell-centre heights z and the top-patch mask (top layer, x < 1/2,
+    y < 1/2): the inflow boundary of the trench problem of Sec. 4.3."""
     nx, ny, nz = dims
     h = 1.0 / nx
     idx = grid_index(dims)
@@ -260,7 +268,8 @@ def _upwind_is_Q(HP, HQ, P, Q):
 
 
 def richards_f(dims, t, psi, Ks, vg: VanGenuchten, dt_D):
-    """f(t,psi) with d/dt theta(psi) + f = 0:
+    """f(t,psi) with d/dt theta(psi) + f = 0 (Richards' equation, Sec. 4.3,
+    Eq. RelationshipsThetaK for theta and K):
     f_P = -sum_Q K_PQ (H_Q - H_P)/h^2 - [top patch] 2 K_S,P kr_up (H_D - H_P)/h^2,
     H = psi + z, K_PQ = harmonic(K_S) kr(upwind)."""
     h = 1.0 / dims[0]

@@ -31,7 +31,9 @@ from scipy.sparse.linalg import spsolve_triangular
 # CholQR with deflation
 # --------------------------------------------------------------------------
 def cholesky_deflating(G, defl):
-    """Upper R with G = R^T R (natural order). Deflated rows are zero.
+    """Upper R with G = R^T R (natural order; the paper is silent on
+    orthogonalisation, this is the module's CholQR reading). Deflated rows
+    are zero.
     Returns (R, deflated mask)."""
     s = G.shape[0]
     R = np.zeros_like(G)
@@ -48,7 +50,7 @@ def cholesky_deflating(G, defl):
 
 
 def cholqr(W, defl=1e-14):
-    """One CholQR pass: W = Q R, Q = W R^{-1} column by column."""
+    """One CholQR pass (module reading): W = Q R, Q = W R^{-1} column by column."""
     G = W.T @ W
     R, dead = cholesky_deflating(G, defl)
     s = W.shape[1]
@@ -61,14 +63,15 @@ def cholqr(W, defl=1e-14):
 
 
 def cholqr2(W, defl=1e-14):
-    """CholQR applied twice; R = R2 R1."""
+    """CholQR applied twice (module reading); R = R2 R1."""
     Q1, R1 = cholqr(W, defl)
     Q, R2 = cholqr(Q1, defl)
     return Q, R2 @ R1
 
 
 def bcgs2(Vs, W):
-    """Two passes of block classical Gram-Schmidt of W against the blocks Vs.
+    """Two passes of block classical Gram-Schmidt (module reading) of W against
+    the blocks Vs.
     Returns (W_orth, H) with W = W_orth + [V] H."""
     Vm = np.hstack(Vs)
     H = np.zeros((Vm.shape[1], W.shape[1]))
@@ -83,7 +86,9 @@ def bcgs2(Vs, W):
 # Householder reduction of the block Hessenberg matrix
 # --------------------------------------------------------------------------
 def householder(x):
-    """Unit v and beta with (I - 2 v v^T) x = beta e_1; v = 0 if x = 0."""
+    """Householder reflector (textbook; module reading for the block
+    Hessenberg least squares): unit v and beta with (I - 2 v v^T) x =
+    beta e_1; v = 0 if x = 0."""
     nx = np.linalg.norm(x)
     if nx == 0.0:
         return np.zeros_like(x), 0.0
@@ -95,7 +100,7 @@ def householder(x):
 
 
 def apply_reflector(v, Yblk):
-    """Yblk <- (I - 2 v v^T) Yblk (rows of Yblk match v)."""
+    """Yblk <- (I - 2 v v^T) Yblk (rows of Yblk match v); textbook."""
     Yblk -= 2.0 * np.outer(v, v @ Yblk)
 
 
@@ -103,7 +108,9 @@ def apply_reflector(v, Yblk):
 # Block GMRES(m), right preconditioned
 # --------------------------------------------------------------------------
 def block_gmres(apply_J, apply_Pinv, R, tol, restart=30, maxit=1000, defl=1e-14):
-    """Solve J X = R for X (N x s) to per-column relative residual `tol`.
+    """Block GMRES(restart) (the block Krylov solve of Eq.
+    matrix-fixed-point-equation, Sec. 2.1, with the module's readings):
+    solve J X = R for X (N x s) to per-column relative residual `tol`.
 
     apply_J(X) and apply_Pinv(X) act on N x s blocks. Returns (X, info) with
     info = {iters, restarts, est (final per-column estimates), converged}.
@@ -171,13 +178,15 @@ def block_gmres(apply_J, apply_Pinv, R, tol, restart=30, maxit=1000, defl=1e-14)
 # Preconditioners
 # --------------------------------------------------------------------------
 def jacobi(J):
-    """P^{-1} X = diag(J)^{-1} X."""
+    """Jacobi preconditioner (the workloads' choice for the 2-D linear slab):
+    P^{-1} X = diag(J)^{-1} X."""
     d = J.diagonal().copy()
     return lambda X: X / d[:, None]
 
 
 def ilu0(J):
-    """ILU(0) of CSR J in natural order (IKJ): for each row i and each k < i in
+    """ILU(0) (the workloads' preconditioner; the paper uses AMG, out of
+    scope) of CSR J in natural order (IKJ): for each row i and each k < i in
     its pattern, l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for j > k in both
     rows' patterns. Returns (L unit lower, U upper) as CSR."""
     J = sp.csr_matrix(J, dtype=np.float64, copy=True)
@@ -210,7 +219,8 @@ def ilu0(J):
 
 
 def ilu0_apply(L, U):
-    """P^{-1} X = U^{-1} L^{-1} X."""
+    """P^{-1} X = U^{-1} L^{-1} X for the ILU(0) factors (forward, then
+    backward substitution; textbook)."""
     def f(X):
         Y = spsolve_triangular(L, X, lower=True, unit_diagonal=True)
         return spsolve_triangular(U, Y, lower=False)
@@ -218,6 +228,8 @@ def ilu0_apply(L, U):
 
 
 def make_preconditioner(J, kind):
+    """P^{-1} as a function of a block X: "none", "jacobi" or "ilu0" (the
+    module's preconditioner readings)."""
     if kind == "none":
         return lambda X: X.copy()
     if kind == "jacobi":
@@ -332,7 +344,8 @@ def _spd_pinv_apply(G, rhs, defl):
 
 
 def block_cg(apply_J, apply_Minv, R, tol, maxit=1000, defl=1e-14):
-    """Preconditioned block CG for symmetric positive definite J and M,
+    """Preconditioned block CG (Sec. 4.2 and 4.3 solve with a block CG) for
+    symmetric positive definite J and M,
     breakdown-free form: the search block is orthonormalised (CholQR2 with
     deflation) every iteration, so dependent or converged columns drop out
     instead of making P^T J P singular:

@@ -30,7 +30,7 @@ from . import coupling, fv, krylov
 
 
 class LinearProblem:
-    """M y' + K y - b(t) = 0 with diagonal M."""
+    """M y' + K y - b(t) = 0 with diagonal M: Eq. problem with f linear."""
 
     def __init__(self, K, Mdiag, b):
         self.K, self.Mdiag, self.b = K, np.asarray(Mdiag, dtype=np.float64), b
@@ -49,7 +49,8 @@ class LinearProblem:
 
 
 class DiffReactProblem:
-    """u_t = div((1+u^2) grad u) + u(1-u) + src(t), M = I (oracle.fv)."""
+    """u_t = div((1+u^2) grad u) + u(1-u) + src(t), M = I (oracle.fv): the
+    diffusion-reaction problem of Sec. 4.2."""
 
     def __init__(self, dims):
         self.dims = dims
@@ -68,7 +69,8 @@ class DiffReactProblem:
 
 
 class RichardsProblem:
-    """d/dt theta(psi) - div(K(psi) grad(psi + z)) = 0 (oracle.fv)."""
+    """d/dt theta(psi) - div(K(psi) grad(psi + z)) = 0 (oracle.fv): Richards'
+    equation of Sec. 4.3 (mass term M(y) of Sec. 2.2)."""
 
     def __init__(self, dims, Ks, vg, dt_D):
         self.dims, self.Ks, self.vg, self.dt_D = dims, Ks, vg, dt_D
@@ -124,7 +126,8 @@ def sequential_dirk_newton(prob, A, c, tau, y0, nstages, tol=1e-13, maxit=50):
 
 
 def window_B0(prob, terms, stages, fvals, y0, s):
-    """B0 of a window from the recipe of coupling.window_matrices."""
+    """B0 of a window (Eq. matrix-equation-pipelining) from the recipe of
+    coupling.window_matrices."""
     n = len(y0)
     B0 = np.zeros((n, s))
     for i, kind, g, coef in terms:

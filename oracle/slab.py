@@ -24,7 +24,8 @@ from . import krylov
 
 
 def coupled_residual(K, Mdiag, A1, A2, Y, B=None, B0=None):
-    """R = M Y A1^T + (K Y - B) A2^T - B0 (B, B0 may be None = 0)."""
+    """R = M Y A1^T + (K Y - B) A2^T - B0 (B, B0 may be None = 0): the defect
+    of Eq. general-system-time-steps in matrix form (column-stacking vec)."""
     KY = K @ Y
     if B is not None:
         KY = KY - B
@@ -35,7 +36,8 @@ def coupled_residual(K, Mdiag, A1, A2, Y, B=None, B0=None):
 
 
 def rhs_F(A2, B=None, B0=None, shape=None):
-    """F = B A2^T + B0."""
+    """F = B A2^T + B0, the right-hand side of Eq. general-system-time-steps
+    in matrix form."""
     F = np.zeros(shape) if B is None else B @ A2.T
     if B0 is not None:
         F = F + B0
@@ -48,11 +50,14 @@ def vec(X):
 
 
 def unvec(x, n, s):
+    """Inverse of the column-stacking vec of Eq. general-system-time-steps:
+    x (N s) -> Y (N x s)."""
     return np.asarray(x).reshape(n, s, order="F")
 
 
 def kron_operator(K, Mdiag, A1, A2):
-    """Dense A1 (x) M + A2 (x) K (tiny grids only)."""
+    """Dense A1 (x) M + A2 (x) K (tiny grids only): the all-at-once operator
+    of Eq. general-system-time-steps with column-stacking vec."""
     Kd = K.toarray() if sp.issparse(K) else np.asarray(K)
     return np.kron(A1, np.diag(Mdiag)) + np.kron(A2, Kd)
 
