@@ -141,12 +141,24 @@ def test_richards_hydrostatic_is_steady_without_boundary_flux():
     assert np.all(f[top] > 0.0)      # psi_D = -2 below hydrostatic: water leaves
 
 
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
 def test_vg_lipschitz_matches_paper_silt_loam():
     """Sec. 4.3 chooses L as the Lipschitz constant of Theta for the silt loam
-    of its parameter table (alpha 0.423, n 2.06, theta_R 0.131, theta_S 0.396)
-    and prints L = 4.501e-2."""
-    vg = fv.VanGenuchten(0.423, 2.06, 0.131, 0.396)
-    assert abs(vg.lipschitz() - 4.501e-2) < 0.0005e-2
+    of its parameter table and prints L = 4.501e-2 (golden file
+    silt_loam_lscheme.txt)."""
+    g = _golden("silt_loam_lscheme.txt")
+    vg = fv.VanGenuchten(g["alpha"], g["n"], g["theta_R"], g["theta_S"])
+    assert abs(vg.lipschitz() - g["L"]) < 0.0005e-2
 
 
 def test_vg_lipschitz_is_the_supremum():
