@@ -286,3 +286,23 @@ def test_block_bicgstab_solves_and_survives_dependent_columns():
     np.testing.assert_allclose(X, Xd, rtol=1e-8, atol=1e-12)
     np.testing.assert_array_equal(X[:, 4], 0.0)
     np.testing.assert_allclose(X[:, 5], X[:, 0], rtol=1e-12, atol=1e-15)
+
+
+def test_block_gmres_never_worse_than_its_columns_alone():
+    """The block Krylov space of k steps contains every column's own Krylov
+    space of k steps, so after k block steps each column's residual is at
+    most that of GMRES run on the column alone (the motivation of block
+    Krylov methods, Sec. 1); with right preconditioning the same holds for
+    the preconditioned spaces."""
+    J, rng = _J(6, 12)
+    R = rng.standard_normal((J.shape[0], 4))
+    ilu = krylov.make_preconditioner(J, "ilu0")
+    for P in (lambda X: X.copy(), ilu):
+        for k in (1, 3, 6):
+            X, _ = krylov.block_gmres(lambda X: J @ X, P, R, tol=0.0, restart=30, maxit=k)
+            blk = np.linalg.norm(R - J @ X, axis=0)
+            for i in range(R.shape[1]):
+                x1, _ = krylov.block_gmres(lambda X: J @ X, P, R[:, [i]], tol=0.0, restart=30,
+                                           maxit=k)
+                one = np.linalg.norm(R[:, i] - J @ x1[:, 0])
+                assert blk[i] <= one * (1.0 + 1e-9) + 1e-13
