@@ -325,22 +325,17 @@ def ilu0_stencil_apply(dims, fac, X):
 # Block conjugate gradients (the paper's solver for symmetric systems)
 # --------------------------------------------------------------------------
 def _spd_pinv_apply(G, rhs, defl):
-    """(G)^+ rhs for a symmetric positive semi-definite s x s G through the
-    deflating Cholesky factor: columns whose pivot is deflated get zero rows
-    (the inverse restricted to the active columns)."""
-    Rf, dead = cholesky_deflating(G, defl)
-    s = G.shape[0]
-    Rinv = np.zeros_like(Rf)
-    for t in range(s):                    # rows of R^-1, as the device computes them
-        row = np.zeros(s)
-        for k in range(s):
-            if dead[k]:
-                continue
-            v = (1.0 if t == k else 0.0) - np.dot(row[:k], Rf[:k, k])
-            row[k] = v / Rf[k, k]
-        Rinv[t] = row
-    # G^+ = R^-1 R^-T on the active columns
-    return Rinv @ (Rinv.T @ rhs)
+    """(G)^+ rhs for a symmetric positive semi-definite s x s G, read as the
+    inverse of G on its active columns (reading of the breakdown-free block
+    CG): the deflating Cholesky test decides which columns are dependent; the
+    result solves G[a, a] x_a = rhs[a] on the active set a and is zero on the
+    deflated rows."""
+    _, dead = cholesky_deflating(G, defl)
+    act = np.flatnonzero(~np.asarray(dead, dtype=bool))
+    out = np.zeros((G.shape[0],) + rhs.shape[1:])
+    if act.size:
+        out[act] = np.linalg.solve(G[np.ix_(act, act)], rhs[act])
+    return out
 
 
 def block_cg(apply_J, apply_Minv, R, tol, maxit=1000, defl=1e-14):

@@ -115,6 +115,34 @@ def test_van_genuchten_limits():
     np.testing.assert_allclose(vg.dkr(psi)[sel], dk[sel], rtol=1e-4, atol=1e-8)
 
 
+def test_van_genuchten_kr_closed_form():
+    """kr of Eq. RelationshipsThetaK, K/K_S = x^(1/2) [1 - (1 - x^(n/(n-1)))^((n-1)/n)]^2
+    with x = theta/theta_S, against values worked out independently:
+     * n = 2 (exponents 2 and 1/2): theta = tr + (ts - tr)/sqrt(1 + psi^2) and
+       kr = sqrt(x) (1 - sqrt(1 - x^2))^2, written out here;
+     * the same and an n = 3 case (exponents 3/2 and 2/3) evaluated in exact
+       rational arithmetic beforehand (25 digits, literals below).
+    Swapping the two exponents keeps kr(0) = 1 and monotonicity but changes
+    every interior value (at n = 2, psi = -1: 0.830 instead of 0.0948)."""
+    vg = fv.VanGenuchten(1.0, 2.0, 0.05, 0.4)
+    psi = np.array([-0.5, -1.0, -3.0])
+    x = (0.05 + 0.35 / np.sqrt(1.0 + psi ** 2)) / 0.4
+    np.testing.assert_allclose(vg.kr(psi), np.sqrt(x) * (1.0 - np.sqrt(1.0 - x ** 2)) ** 2,
+                               rtol=1e-12)
+    exact_n2 = [0.3207240617325334723442305, 0.09477410205668127813004689,
+                0.004496424850521366630713021]
+    np.testing.assert_allclose(vg.kr(psi), exact_n2, rtol=1e-12)
+    # n = 3, alpha = 1, psi = -1: theta = tr + (ts - tr) 2^(-2/3)
+    vg3 = fv.VanGenuchten(1.0, 3.0, 0.05, 0.4)
+    assert vg3.theta(np.array([-1.0]))[0] / 0.4 == pytest.approx(0.6762154593290070095856546,
+                                                                 rel=1e-13)
+    assert vg3.kr(np.array([-1.0]))[0] == pytest.approx(0.1437211805412071599323933, rel=1e-12)
+    # n = 3, alpha = 2, psi = -0.75 (alpha |psi| = 3/2)
+    vg3b = fv.VanGenuchten(2.0, 3.0, 0.05, 0.4)
+    assert vg3b.kr(np.array([-0.75]))[0] == pytest.approx(0.03097319362505719719299625,
+                                                           rel=1e-12)
+
+
 def test_richards_jacobian_matches_finite_differences():
     dims = (4, 4, 4)
     rng = np.random.default_rng(3)
