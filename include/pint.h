@@ -302,7 +302,9 @@ int pint_precond_apply(pint_op op, int precond, const double* X, double* Z,
  * and bf16 inner solves use (X, Z: float32 N x s, device, must not alias).
  * Factors J on first use like pint_precond_apply. */
 int pint_ilu0_apply_f32(pint_op op, const float* X, float* Z, void* stream);
-/* H[(b*s+i)*s + k] = sum_r V_b[r][i] W[r][k]  ((nb*s) x s, float64, device). */
+/* H[(b*s+i)*s + k] = sum_r V_b[r][i] W[r][k]  ((nb*s) x s, float64, device).
+ * nb*s <= 1024. Synchronous: it reads the device error word of the bulk-copy
+ * pipeline afterwards (PINT_ERR_TIMEOUT when one of its waits ran out). */
 int pint_block_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb,
                     const void* V, const void* W, double* H, void* stream);
 /* W[r][k] -= sum_{b,i} V_b[r][i] H[(b*s+i)*s + k]. */
@@ -322,10 +324,14 @@ int pint_cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W,
  *    cross-CTA partial sums live in a fixed 4 MiB float64 array in the
  *    library's device memory, held on every device that loads the library
  *    until the process exits.
- *  - Limit: nb * s * s <= 4096 (otherwise PINT_ERR_INVALID with a message
- *    from pint_last_error(NULL)); 1 <= s <= 16; V, W 16-byte aligned.
+ *  - Limits: nb * s * s <= 4096 (the scratch) and nb * s <= 1024 (basis
+ *    columns one Gram CTA covers); otherwise PINT_ERR_INVALID with a message
+ *    from pint_last_error(NULL). 1 <= s <= 16; V, W 16-byte aligned.
  *  - The first call on a device (with that device current) looks up the
- *    array's device address; make that first call before any stream capture.
+ *    array's device address and keeps it for the life of the process; make
+ *    that first call before any stream capture. A cudaDeviceReset of that
+ *    device invalidates the kept address: do not call this entry point on a
+ *    device after resetting it.
  *  - All calls share the array, which keeps the last call's contents; every
  *    call overwrites the part it reads. Calls that overlap on the GPU (other
  *    streams, other host threads) race on it and must be serialised by the
@@ -334,6 +340,16 @@ int pint_cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W,
 int pint_block_gram_noalloc(int precision, int64_t n, int s, int nb,
                             const void* V, const void* W, double* H,
                             void* stream);
+/* Test access to the bounded device waits (no paper counterpart). which = 0:
+ * one thread waits, through the same bounded wait as the ILU(0) sweeps, for a
+ * device flag that nothing sets; which = 1: one CTA waits, through the same
+ * bounded mbarrier wait as the Gram kernel's bulk-copy ring, for a
+ * transaction count that no copy delivers. The deadline is limit_ms
+ * (0 < limit_ms <= 1000) after the wait starts; the wait then gives up,
+ * raises its error word and the kernel returns (no trap, no copy in flight),
+ * so the context stays usable. Synchronous. Returns PINT_ERR_TIMEOUT when
+ * the wait ran out, as it must. */
+int pint_test_wait_timeout(pint_ctx ctx, int which, double limit_ms, void* stream);
 /* norms[k] = ||X_k||_2 (host array of s doubles). Synchronous. */
 int pint_colnorms(pint_ctx ctx, int precision, int64_t n, int s,
                   const void* X, double* norms, void* stream);

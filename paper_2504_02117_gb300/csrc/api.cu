@@ -470,8 +470,16 @@ int pint_block_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb, const
     PINT_REQUIRE(precision == PINT_FP64 || precision == PINT_FP32, PINT_ERR_INVALID, "precision");
     require_aligned(V, "V");
     require_aligned(W, "W");
+    cudaStream_t st = as_stream(stream);
+    // the bulk-copy pipeline raises the context's error word when a wait runs
+    // out: clear it first, read it after the product
+    PINT_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
     // n a multiple of 64 needs no padding rows: use the bulk-copy pipeline
-    launch_gram(ctx, precision, n, s, nb, V, n * s, W, H, as_stream(stream), n % 64 == 0 ? n : 0);
+    launch_gram(ctx, precision, n, s, nb, V, n * s, W, H, st, n % 64 == 0 ? n : 0);
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 2, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PINT_CUDA(cudaStreamSynchronize(st));
+    PINT_REQUIRE(ctx->h_flag[2] == 0, PINT_ERR_TIMEOUT,
+                 "bulk-copy wait in the Gram kernel exceeded its time budget");
     return PINT_OK;
   });
 }
@@ -498,6 +506,31 @@ int pint_cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W, double*
     PINT_REQUIRE(precision == PINT_FP64 || precision == PINT_FP32, PINT_ERR_INVALID, "precision");
     require_aligned(W, "W");
     cholqr2(ctx, precision, n, s, W, R, nullptr, as_stream(stream));
+    return PINT_OK;
+  });
+}
+
+int pint_test_wait_timeout(pint_ctx ctx, int which, double limit_ms, void* stream) {
+  if (!ctx) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    PINT_REQUIRE(which == 0 || which == 1, PINT_ERR_INVALID, "which must be 0 or 1");
+    PINT_REQUIRE(limit_ms > 0.0 && limit_ms <= 1000.0, PINT_ERR_INVALID,
+                 "limit_ms must be in (0, 1000]");
+    cudaStream_t st = as_stream(stream);
+    // words 8 (a flag nothing sets) and 9 (the error word) of the context's
+    // flag array, which no solve uses
+    unsigned* flag = reinterpret_cast<unsigned*>(ctx->d_flag + 8);
+    int* err = ctx->d_flag + 9;
+    PINT_CUDA(cudaMemsetAsync(ctx->d_flag + 8, 0, 2 * sizeof(int), st));
+    if (which == 0) test_wait_timeout(limit_ms, flag, err, st);
+    else test_mbar_timeout(limit_ms, err, st);
+    ctx->launches += 1;
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 3, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PINT_CUDA(cudaStreamSynchronize(st));
+    const int e = ctx->h_flag[3];
+    PINT_REQUIRE(e == 0, PINT_ERR_TIMEOUT,
+                 which == 0 ? "ILU(0) dependency wait exceeded its time budget"
+                            : "bulk-copy (mbarrier) wait exceeded its time budget");
     return PINT_OK;
   });
 }

@@ -144,6 +144,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return done != 0;
 }
 
+// Bounded wait for phase `parity` of an mbarrier. Returns true when the phase
+// completed; false when *aborted was raised by another thread of the CTA or
+// when `deadline` (globaltimer) passed, in which case it raises *aborted and
+// stores `code` into the error word *err. Never traps.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  unsigned long long deadline,
+                                                  volatile int* aborted, int* err, int code) {
+  while (!mbar_try_wait(bar, parity)) {
+    if (*aborted) return false;
+    if (gtimer() > deadline) {
+      *aborted = 1;
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+
 // Thread work unit: Q consecutive basis columns (b, i0..i0+Q-1) x all S
 // columns of W, kept in Q*S register accumulators; per row one Q-wide and
 // S/4 four-wide shared loads feed Q*S FMAs. Each block's stage region is
@@ -201,15 +219,15 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // Copies of one stage are issued by threads 0..nb (one block each); thread
-  // 0 also posts the expected byte count. A copy may complete before the
-  // expect_tx is posted: the phase still needs thread 0's arrival.
+  // Copies of one stage: thread t issues the blocks b = t, t + NT, ... <= nb
+  // (one copy each, so every one of the nb + 1 blocks is issued whatever nb);
+  // thread 0 also posts the expected byte count. A copy may complete before
+  // the expect_tx is posted: the phase still needs thread 0's arrival.
   auto issue = [&](int stage, int tile) {
     unsigned char* dst = smem_raw + (size_t)stage * stage_bytes;
     if (threadIdx.x == 0) mbar_expect_tx(&bars[stage], blk_bytes * (nb + 1));
-    const int b = threadIdx.x;
-    if (b <= nb) {
-      const int64_t row = r0 + (int64_t)tile * TR;
+    const int64_t row = r0 + (int64_t)tile * TR;
+    for (int b = threadIdx.x; b <= nb; b += NT) {
       const VT* src = (b < nb ? V + (int64_t)b * bstride : W) + row * s;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_g2s(dst + (size_t)b * blk_pitch, src, blk_bytes, &bars[stage]);
@@ -247,15 +265,7 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
     const int stage = t % kStages;
     const unsigned parity = (unsigned)((t / kStages) & 1);
     if (!*(volatile int*)&aborted) {
-      bool done = false;
-      while (!(done = mbar_try_wait(&bars[stage], parity))) {
-        if (*(volatile int*)&aborted) break;
-        if (gtimer() > deadline) {
-          aborted = 1;
-          atomicExch(err, 3);
-          break;
-        }
-      }
+      const bool done = mbar_wait_bounded(&bars[stage], parity, deadline, &aborted, err, 3);
       if (done && threadIdx.x == 0) pending[stage] = -1;
     }
     const VT* T = reinterpret_cast<const VT*>(smem_raw + (size_t)stage * stage_bytes);
@@ -349,6 +359,29 @@ __global__ void k_gram_reduce(int nblk, int E, const double* __restrict__ partia
   double v = 0.0;
   for (int b = 0; b < nblk; ++b) v += partial[(int64_t)b * E + e];
   H[e] = v;
+}
+
+// Test of the bounded mbarrier wait: one CTA posts an expected transaction
+// count of 16 bytes that no copy ever delivers, then waits for the phase
+// through mbar_wait_bounded with a deadline `budget_ns` from now. No copy is
+// in flight, so the CTA returns as soon as the wait gives up.
+__global__ void k_test_mbar_timeout(unsigned long long budget_ns, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int aborted;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    aborted = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, 16);
+  }
+  __syncthreads();
+  const unsigned long long deadline = gtimer() + budget_ns;
+  mbar_wait_bounded(&bar, 0, deadline, &aborted, err, 3);
+}
+
+void test_mbar_timeout(double limit_ms, int* err, cudaStream_t st) {
+  k_test_mbar_timeout<<<1, 32, 0, st>>>((unsigned long long)(limit_ms * 1e6), err);
+  check_launch("k_test_mbar_timeout");
 }
 
 static void ensure_partial(pint_ctx ctx, size_t bytes) {
@@ -1748,6 +1781,10 @@ extern "C" int pint_block_gram_noalloc(int precision, int64_t n, int s, int nb, 
                  "pint_block_gram_noalloc: nb*s*s = " + std::to_string((int64_t)nb * s * s) +
                      " exceeds the maximum of " + std::to_string(kNoAllocMaxEntries) +
                      " (fixed scratch of 4 MiB)");
+    // the Gram kernel covers at most 4 x 256 basis columns per CTA
+    PINT_REQUIRE((int64_t)nb * s <= 1024, PINT_ERR_INVALID,
+                 "pint_block_gram_noalloc: nb*s = " + std::to_string((int64_t)nb * s) +
+                     " exceeds the maximum of 1024 basis columns");
     PINT_REQUIRE(precision == PINT_FP64 || precision == PINT_FP32, PINT_ERR_INVALID,
                  "pint_block_gram_noalloc: precision must be PINT_FP64 or PINT_FP32");
     PINT_REQUIRE(V && W && H, PINT_ERR_INVALID, "pint_block_gram_noalloc: NULL pointer");

@@ -160,6 +160,26 @@ def test_gram_update_colnorms(P, ctx, prec, s, nb, n):
                                rtol=1e-12 if prec == "fp64" else 1e-6)
 
 
+@pytest.mark.parametrize("prec,s,nb", [("fp32", 1, 300), ("fp64", 2, 300), ("fp32", 1, 700)])
+def test_gram_many_blocks_bulk_pipeline(P, ctx, prec, s, nb):
+    """More basis blocks than the Gram CTA has threads (nb + 1 > 256): every
+    block must still be copied into each stage of the bulk-copy ring (n a
+    multiple of 64 takes that pipeline). Checked against V^T W in float64."""
+    import torch
+    n = 65536
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    code = P.PINT_FP64 if prec == "fp64" else P.PINT_FP32
+    Vd = torch.tensor(synth.uniform(17, nb * n * s).reshape(nb, n, s), device="cuda", dtype=dt)
+    Wd = torch.tensor(synth.uniform(18, n * s).reshape(n, s), device="cuda", dtype=dt)
+    H = torch.full((nb * s, s), float("nan"), device="cuda", dtype=torch.float64)
+    P.pint_block_gram(ctx, code, n, s, nb, Vd, Wd, H)
+    Vm = Vd.double().cpu().numpy().transpose(0, 2, 1).reshape(nb * s, n)
+    Wm = Wd.double().cpu().numpy()
+    scale = np.abs(Vm) @ np.abs(Wm)
+    err = np.abs(H.cpu().numpy() - Vm @ Wm)
+    assert np.all(err <= (1e-13 if prec == "fp64" else 1e-5) * scale)
+
+
 @pytest.mark.parametrize("s", [1, 2, 5, 8, 16])
 def test_cholqr2_matches_oracle(P, ctx, s):
     import torch
