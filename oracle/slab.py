@@ -70,11 +70,27 @@ def solve_all_at_once_dense(K, Mdiag, A1, A2, B=None, B0=None):
     return unvec(y, n, s)
 
 
-def sequential_dirk_linear(K, Mdiag, A, tau, y0, Bstages):
+def _gmres_solve(J, rhs, rtol):
+    """x with ||J x - rhs|| <= rtol ||rhs|| by scipy's GMRES(200) with a
+    Jacobi preconditioner; raises when it does not get there."""
+    from scipy.sparse.linalg import LinearOperator, gmres
+    d = J.diagonal()
+    M = LinearOperator(J.shape, matvec=lambda x: x / d)
+    x, info = gmres(J, rhs, rtol=rtol, atol=0.0, restart=200, maxiter=100, M=M)
+    res = np.linalg.norm(J @ x - rhs)
+    if info != 0 or res > 2.0 * rtol * np.linalg.norm(rhs):
+        raise RuntimeError(f"stage solve did not reach rtol {rtol}: info {info}")
+    return x
+
+
+def sequential_dirk_linear(K, Mdiag, A, tau, y0, Bstages, rtol=None):
     """Step the stiffly accurate DIRK (Eq. stiffly-accurate-DIRK) one stage at
     a time. Bstages[:, g] is b(t) at global stage g (0-based, step-major).
     Returns the stage values (N x #stages); stages with a_kk = 0 are the
-    explicit y^{(n,1)} = y^n."""
+    explicit y^{(n,1)} = y^n.
+    rtol None: each stage equation is solved by sparse LU (scipy splu). A
+    float: by Jacobi-preconditioned GMRES (scipy) to that relative residual
+    instead, for 3-D grids whose LU fill makes splu take minutes."""
     A = np.asarray(A, dtype=np.float64)
     m = A.shape[0]
     N, G = Bstages.shape
@@ -92,10 +108,12 @@ def sequential_dirk_linear(K, Mdiag, A, tau, y0, Bstages):
             rhs -= A[k - 1, j - 1] * (K @ Y[:, gj] - Bstages[:, gj])
         if akk == 0.0:
             Y[:, g] = yn
-        else:
+        elif rtol is None:
             if akk not in cache:
                 cache[akk] = splu(sp.csc_matrix(Mdg / tau + akk * K))
             Y[:, g] = cache[akk].solve(rhs)
+        else:
+            Y[:, g] = _gmres_solve(sp.csr_matrix(Mdg / tau + akk * K), rhs, rtol)
         if k == m:
             yn = Y[:, g].copy()
     return Y

@@ -105,6 +105,7 @@ _SIGS = {
     "pint_block_gram_noalloc": (_i, [_i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
     "pint_cholqr2": (_i, [_vp, _i, _i64, _i, _vp, _vp, _vp]),
     "pint_colnorms": (_i, [_vp, _i, _i64, _i, _vp, _vp, _vp]),
+    "pint_test_wait_timeout": (_i, [_vp, _i, _d, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -334,6 +335,12 @@ def pint_colnorms(ctx, precision, n, s, X, stream=None):
     out = np.zeros(s)
     _check(lib.pint_colnorms(ctx, precision, n, s, _ptr(X), _ptr(out), _stream(stream)), ctx)
     return out
+
+
+def pint_test_wait_timeout(ctx, which, limit_ms, stream=None):
+    """Run one bounded device wait that must run out (0: the ILU(0) flag
+    wait, 1: the bulk-copy mbarrier wait); returns the status code."""
+    return lib.pint_test_wait_timeout(ctx, which, limit_ms, _stream(stream))
 
 
 def pint_profile_enable(ctx, on=True):

@@ -109,6 +109,18 @@ __device__ __forceinline__ bool wait_ready(const unsigned* flag, unsigned epoch,
   }
 }
 
+// Test of the bounded dependency wait: one thread waits through wait_ready
+// for `flag` to reach epoch 1, which nothing stores, with a deadline
+// `budget_ns` from now; it raises *err (1) and returns.
+__global__ void k_test_wait_timeout(const unsigned* flag, unsigned long long budget_ns, int* err) {
+  if (threadIdx.x == 0) wait_ready(flag, 1u, err, globaltimer() + budget_ns);
+}
+
+void test_wait_timeout(double limit_ms, unsigned* flag, int* err, cudaStream_t st) {
+  k_test_wait_timeout<<<1, 32, 0, st>>>(flag, (unsigned long long)(limit_ms * 1e6), err);
+  check_launch("k_test_wait_timeout");
+}
+
 // ------------------------------------------------------------ factor
 // Lane = row. Chunk rows never depend on each other (same level).
 __global__ void __launch_bounds__(256)

@@ -375,6 +375,11 @@ void ilu_setup(pint_op op, cudaStream_t st);          // factor J (float64 + flo
 void ilu_apply(pint_op op, int precision, const void* X, void* Z, cudaStream_t st);
 void ilu_destroy(pint_op op);
 void ilu_check(pint_op op);                            // throws PINT_ERR_TIMEOUT
+// Bounded waits made to run out (test access): the ILU(0) dependency wait on
+// a flag nothing sets, and the Gram ring's mbarrier wait on a transaction
+// count no copy delivers. Each raises its error word and returns.
+void test_wait_timeout(double limit_ms, unsigned* flag, int* err, cudaStream_t st);
+void test_mbar_timeout(double limit_ms, int* err, cudaStream_t st);
 
 }  // namespace pint
 

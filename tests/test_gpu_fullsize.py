@@ -182,3 +182,44 @@ def test_pipeline_full_size_stage_equations(P, ctx, workload):
         assert worst <= case.tol * 1.01, worst
     finally:
         case.close()
+
+
+@pytest.fixture(scope="module")
+def seq48():
+    """The 48^3 convection-diffusion workload (bench's recipe: log-normal D,
+    v = (1, 0.5, 0), tau = 1e-3) stepped sequentially by the oracle over 16
+    implicit-Euler steps, each stage equation solved to a relative residual
+    of 1e-15."""
+    w = synth.convdiff_3d(48, 16)
+    D = synth.diffusion_field(w)
+    K = fv.convdiff_matrix(w.dims, D, w.velocity)
+    B = synth.rhs_block(w)
+    A, _, _ = coupling.implicit_euler()
+    Y = slab.sequential_dirk_linear(K, np.ones(w.n), A, w.tau, np.zeros(w.n), B, rtol=1e-15)
+    return B, Y
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("s", [8, 16])
+def test_slab_elementwise_equals_sequential_48cube(P, ctx, seq48, s, prec):
+    """bench's slab configuration (ILU(0) row-of-tiles sweeps, block
+    GMRES(30), default inner tolerances, narrowed inner solves; the Gram
+    products on 2 x 152 CTAs) at 48^3 with s = 8 and s = 16, solved to
+    tol 1e-13: every column equals sequential stepping (the first s steps of
+    the same right-hand sides) to 1e-10 relative in FP64 and 1e-8 with FP32
+    inner solves under FP64 refinement."""
+    import torch
+    B16, Yseq = seq48
+    case = bench.LinearCase(P, ctx, bench.parse(["--n", "48", "--s", str(s),
+                                                 "--precision", prec]))
+    try:
+        case.o.tol = 1e-13
+        case.Bd.copy_(torch.tensor(np.ascontiguousarray(B16[:, :s]), device="cuda"))
+        st = case.step()
+        assert st.status == P.PINT_OK
+        Yg = case.Y.cpu().numpy()
+        ref = Yseq[:, :s]
+        err = np.linalg.norm(Yg - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert np.all(err <= (1e-10 if prec == "fp64" else 1e-8)), err
+    finally:
+        case.close()

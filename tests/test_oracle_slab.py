@@ -207,3 +207,22 @@ def test_slab_with_block_bicgstab_equals_sequential_stepping():
                                       precond=pc, solver="bicgstab", narrow=narrow)
             assert info["converged"] and info["inner"] > 0
             np.testing.assert_allclose(Y, Ys, rtol=1e-9, atol=1e-12)
+
+
+def test_sequential_stepping_iterative_stage_solves_equal_lu():
+    """The GMRES option of sequential_dirk_linear (for grids where sparse LU
+    is too slow) gives the LU result: 3-D convection-diffusion with a
+    log-normal coefficient, 12^3 cells, 6 implicit-Euler steps and 3 steps of
+    the theta example (explicit first stage)."""
+    import synth
+    dims = (12, 12, 12)
+    n = 12 ** 3
+    D = np.exp(synth.normal(5, n)).reshape(12, 12, 12)
+    K = fv.convdiff_matrix(dims, D, (1.0, 0.5, 0.0))
+    B = synth.uniform(6, n * 6).reshape(n, 6)
+    y0 = synth.uniform(7, n)
+    for A in (coupling.implicit_euler()[0], coupling.theta_method(0.5)[0]):
+        lu = slab.sequential_dirk_linear(K, np.ones(n), A, 1e-3, y0, B)
+        it = slab.sequential_dirk_linear(K, np.ones(n), A, 1e-3, y0, B, rtol=1e-15)
+        rel = np.linalg.norm(it - lu, axis=0) / np.linalg.norm(lu, axis=0)
+        assert np.all(rel < 1e-12), rel
