@@ -253,7 +253,9 @@ namespace pint {
 // than was set before (per kernel and device): the attribute call is a host
 // round trip on every launch otherwise.
 inline void smem_attr_raw(const void* kern, size_t bytes) {
-  if (bytes <= 48 * 1024) return;                 // the default limit
+  // the default limit (48 KB) covers static plus dynamic shared memory; the
+  // library's kernels declare at most 2 KB statically
+  if (bytes + 2048 <= 48 * 1024) return;
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, size_t> set;
   int dev = 0;
