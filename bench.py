@@ -678,6 +678,8 @@ def main():
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(), "impl": "pint",
     }
+    if linear(args):
+        out["spmm_full_width"] = spmm_full_width(P, ctx, case, args.precision, hbm_peak)
     if args.sweep and linear(args):
         out["sweep"] = sweep(P, ctx, args, case.w)
     print(json.dumps(out), flush=True)
@@ -685,6 +687,55 @@ def main():
     P.pint_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def spmm_full_width(P, ctx, case, prec, hbm_peak, reps=20):
+    """The inner SpMM (Z = J X) alone at the workload's full block width, in
+    the inner-solve precision: `reps` launches alternating between two input /
+    output pairs (together far larger than L2), timed by the library's
+    CUDA-event profiler on the launching stream; bytes are the kernel's own
+    algorithmic bytes (the library's count). The in-solve figure
+    (`spmm_roofline`) averages over narrowed widths as well."""
+    import torch
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    code = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[prec]
+    g = torch.Generator(device="cuda").manual_seed(7)
+    bufs = [(torch.rand(case.n, case.s, device="cuda", dtype=dt, generator=g),
+             torch.empty(case.n, case.s, device="cuda", dtype=dt)) for _ in range(2)]
+
+    def apply(i):
+        X, Z = bufs[i % 2]
+        if prec == "fp64":
+            P.pint_inner_apply(ctx, case.op, X, Z)
+        else:
+            P.pint_inner_apply_lowp(ctx, case.op, code, X, Z)
+    for i in range(3):
+        apply(i)
+    torch.cuda.synchronize()
+    P.pint_profile_reset(ctx)
+    P.pint_profile_enable(ctx, True)
+    for i in range(reps):
+        apply(i)
+    P.pint_profile_enable(ctx, False)
+    r = P.pint_profile_read(ctx, 1)
+    per_s = r["ms"] / 1e3 / r["launches"]
+    b = r["bytes"] / r["launches"]
+    gbs = b / per_s / 1e9
+    vb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+    xb = 8 if prec == "fp64" else 4
+    # the format the kernel reads: 8 stencil coefficients per row for grid
+    # operators (SELL-32 values and indices otherwise), X read, Z written once
+    fmt = 8 * vb * case.n + 2 * xb * case.n * case.s
+    return {"s": case.s, "precision": prec, "bound": "hbm", "achieved": round(gbs, 1),
+            "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+            "algorithmic_bytes_per_launch": b, "avg_launch_us": per_s * 1e6,
+            "launches": r["launches"],
+            "format_bytes_per_launch": fmt,
+            "format_GBs": round(fmt / per_s / 1e9, 1),
+            "format_frac": round(fmt / per_s / 1e9 / hbm_peak, 4),
+            "note": "achieved: CSR-form algorithmic bytes of the product (values + int32 "
+                    "indices, row pointer, X read and Z written once) per launch time; "
+                    "format_*: the stencil form's own bytes (8 coefficients per row)"}
 
 
 def precision_variant(P, case, args, stream, prec="fp64"):

@@ -294,6 +294,11 @@ long long pint_kernel_launches(pint_ctx ctx);
  * row-major each, block b at V + b*n*s. */
 /* Z = J X with J = alpha M + beta K of the current coupling (float64). */
 int pint_inner_apply(pint_op op, const double* X, double* Z, void* stream);
+/* Z = J X with the float32 (PINT_FP32) or bfloat16 (PINT_BF16) copy of J
+ * that the low-precision inner solves use; X, Z float32 N x s (device, must
+ * not alias), float32 accumulation. Asynchronous. */
+int pint_inner_apply_lowp(pint_op op, int precision, const float* X, float* Z,
+                          void* stream);
 /* Z = P^{-1} X for the preconditioner of `precond` (float64), set up from
  * J on first use. */
 int pint_precond_apply(pint_op op, int precond, const double* X, double* Z,

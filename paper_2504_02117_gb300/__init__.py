@@ -98,6 +98,7 @@ _SIGS = {
     "pint_profile_reset": (_i, [_vp]),
     "pint_kernel_launches": (C.c_longlong, [_vp]),
     "pint_inner_apply": (_i, [_vp, _vp, _vp, _vp]),
+    "pint_inner_apply_lowp": (_i, [_vp, _i, _vp, _vp, _vp]),
     "pint_precond_apply": (_i, [_vp, _i, _vp, _vp, _vp]),
     "pint_ilu0_apply_f32": (_i, [_vp, _vp, _vp, _vp]),
     "pint_block_gram": (_i, [_vp, _i, _i64, _i, _i, _vp, _vp, _vp, _vp]),
@@ -300,6 +301,10 @@ def pint_pipeline_run(ctx, prob, A, c, tau, s, y0, nstages, stages_out, opts=Non
 
 def pint_inner_apply(ctx, op, X, Z, stream=None):
     _check(lib.pint_inner_apply(op, _ptr(X), _ptr(Z), _stream(stream)), ctx)
+
+
+def pint_inner_apply_lowp(ctx, op, precision, X, Z, stream=None):
+    _check(lib.pint_inner_apply_lowp(op, precision, _ptr(X), _ptr(Z), _stream(stream)), ctx)
 
 
 def pint_precond_apply(ctx, op, precond, X, Z, stream=None):

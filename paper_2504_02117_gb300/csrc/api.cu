@@ -147,13 +147,16 @@ void op_free_all(pint_op op) {
   const int64_t ne = std::max<int64_t>(op->sell.nelem, 1);
   const size_t esz[3] = {8, 4, 2};
   for (int p = 0; p < 3; ++p)
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < 2; ++j) {
       if (op->sellJ[p][j]) dfree(c, op->sellJ[p][j], esz[p] * op->sell.nelem);
+      if (op->stenJ[p][j]) dfree(c, op->stenJ[p][j], esz[p] * 8 * op->n);
+    }
   dfree(c, op->rowptr, sizeof(int) * (n + 1));
   dfree(c, op->colind, sizeof(int) * nnz);
   dfree(c, op->diagpos, sizeof(int) * n);
   dfree(c, op->Kval, sizeof(double) * nnz);
   dfree(c, op->sellK, sizeof(double) * ne);
+  dfree(c, op->stenK, sizeof(double) * 8 * n);
   dfree(c, op->Mdiag, sizeof(double) * n);
   dfree(c, op->Jval, sizeof(double) * nnz);
   dfree(c, op->Jdiag, sizeof(double) * n);
@@ -166,11 +169,16 @@ void op_free_all(pint_op op) {
 void op_clear_inner_cache(pint_op op) {
   const size_t esz[3] = {8, 4, 2};
   for (int p = 0; p < 3; ++p)
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < 2; ++j) {
       if (op->sellJ[p][j]) {
         dfree(op->ctx, op->sellJ[p][j], esz[p] * op->sell.nelem);
         op->sellJ[p][j] = nullptr;
       }
+      if (op->stenJ[p][j]) {
+        dfree(op->ctx, op->stenJ[p][j], esz[p] * 8 * op->n);
+        op->stenJ[p][j] = nullptr;
+      }
+    }
   if (op->ilu) ilu_destroy(op);
 }
 
@@ -414,6 +422,22 @@ int pint_inner_apply(pint_op op, const double* X, double* Z, void* stream) {
     cudaStream_t st = as_stream(stream);
     if (!op->j_valid) build_inner(op, st);
     launch_inner_spmm(op, PINT_FP64, false, X, Z, nullptr, st);
+    return PINT_OK;
+  });
+}
+
+int pint_inner_apply_lowp(pint_op op, int precision, const float* X, float* Z, void* stream) {
+  if (!op) return PINT_ERR_INVALID;
+  return guard(op->ctx, [&] {
+    PINT_REQUIRE(op->s >= 1, PINT_ERR_INVALID, "coupling not set");
+    PINT_REQUIRE(precision == PINT_FP32 || precision == PINT_BF16, PINT_ERR_INVALID,
+                 "precision must be PINT_FP32 or PINT_BF16");
+    require_aligned(X, "X");
+    require_aligned(Z, "Z");
+    PINT_REQUIRE(X != Z, PINT_ERR_INVALID, "X and Z must not alias");
+    cudaStream_t st = as_stream(stream);
+    if (!op->j_valid) build_inner(op, st);
+    launch_inner_spmm(op, precision, false, X, Z, nullptr, st);
     return PINT_OK;
   });
 }

@@ -239,6 +239,13 @@ struct pint_op_s {
   double* Jinvdiag = nullptr;    // 1 / diag(J)
   // SELL copies of J: [precision][jacobi_scaled]
   void* sellJ[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  // stencil copies of J (grid operators only): [precision][jacobi_scaled],
+  // 8 coefficients per row (see spmm.cu)
+  void* stenJ[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  // float64 stencil copy of K for the coupled residual (grid operators; built
+  // on first use after K's values change)
+  double* stenK = nullptr;
+  bool stenK_valid = false;
   pint::IluState* ilu = nullptr;
   pint::KrylovWork* work = nullptr;
   // nonlinear problem that owns this operator (or nullptr)

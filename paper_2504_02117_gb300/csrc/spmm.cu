@@ -67,6 +67,7 @@ __global__ void k_sell_scatter(int64_t nnz, const int* __restrict__ rowptr_unuse
 }
 
 void sell_scatter(pint_op op, const double* csr_vals, double* sell_vals, cudaStream_t st) {
+  if (sell_vals == op->sellK) op->stenK_valid = false;   // K's values change
   PINT_CUDA(cudaMemsetAsync(sell_vals, 0, sizeof(double) * op->sell.nelem, st));
   k_sell_scatter<double><<<grid_for(op->nnz, 256), 256, 0, st>>>(
       op->nnz, nullptr, op->sell.csr_to_sell, csr_vals, op->colind, nullptr, sell_vals);
@@ -126,37 +127,85 @@ void* inner_sell(pint_op op, int precision, bool jacobi, cudaStream_t st) {
   return slot;
 }
 
+// Stencil copy of a grid operator's CSR values (layout: see the inner SpMM).
+template <typename OT>
+__global__ void k_stencil_coefs(int64_t n, int nx, int ny, int nz, const int* __restrict__ rowptr,
+                                const double* __restrict__ vals,
+                                const double* __restrict__ colscale, OT* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int64_t sxy = (int64_t)nx * ny;
+  const int i = (int)(r % nx), j = (int)((r / nx) % ny), k = (int)(r / sxy);
+  const int64_t nb[7] = {r - sxy, r - nx, r - 1, r, r + 1, r + nx, r + sxy};
+  const bool has[7] = {k > 0, j > 0, i > 0, true, i + 1 < nx, j + 1 < ny, k + 1 < nz};
+  int p = rowptr[r];
+  for (int q = 0; q < 8; ++q) {
+    double v = 0.0;
+    if (q < 7 && has[q]) {
+      v = vals[p++];
+      if (colscale) v *= colscale[nb[q]];
+    }
+    if constexpr (std::is_same<OT, double>::value) out[8 * r + q] = v;
+    else if constexpr (std::is_same<OT, float>::value) out[8 * r + q] = __double2float_rn(v);
+    else out[8 * r + q] = __double2bfloat16(v);
+  }
+}
+
 // --------------------------------------------------- fused coupled residual
 // R_r = d_r (Y_r A1^T) + ((K Y)_r - B_r) A2^T - B0_r  for every row r, with the
 // s x s products unrolled against the kernel-parameter copies of A1, A2.
 // LO > 0: both matrices are lower banded with band LO (entries only at
 // 0 <= i - k <= LO, the shape of the time-stepping matrices), so only that band
 // is unrolled; LO == 0: dense, zero coefficients skipped by uniform branches.
-template <int S, bool EXACT, int LO>
+// STEN: K in the stencil form of the grid operators (8 coefficients per row in
+// CSR order, see the inner SpMM below): the seven rows of Y are loaded at once
+// and accumulated in the same order as the SELL form.
+template <int S, bool EXACT, int LO, bool STEN>
 __global__ void __launch_bounds__(256)
 k_coupled(int64_t n, int s, const int64_t* __restrict__ sptr, const int* __restrict__ col,
           const double* __restrict__ val, const double* __restrict__ Md,
           const double* __restrict__ Y, const double* __restrict__ B,
           const double* __restrict__ B0, double* __restrict__ R,
-          const __grid_constant__ Coupling cp) {
+          const __grid_constant__ Coupling cp, int nx, int64_t sxy) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
-  const int64_t q = row >> 5;
-  const int lane = (int)(row & 31);
-  const int64_t b0 = sptr[q];
-  const int w = (int)((sptr[q + 1] - b0) >> 5);
   double ky[S];
 #pragma unroll
   for (int k = 0; k < S; ++k) ky[k] = 0.0;
-  const double* vp = val + b0 + lane;
-  const int* cpp = col + b0 + lane;
-  for (int t = 0; t < w; ++t) {
-    const double v = __ldg(vp + (int64_t)t * 32);
-    const int c = __ldg(cpp + (int64_t)t * 32);
-    double x[S];
-    load_row<S, EXACT>(Y + (int64_t)c * s, s, x);
+  if constexpr (STEN) {
+    double c[8];
+    const double2* cq = reinterpret_cast<const double2*>(val + 8 * row);
 #pragma unroll
-    for (int k = 0; k < S; ++k) ky[k] = fma(v, x[k], ky[k]);
+    for (int i = 0; i < 4; ++i) {
+      const double2 v = __ldg(cq + i);
+      c[2 * i] = v.x; c[2 * i + 1] = v.y;
+    }
+    const int64_t off[7] = {-sxy, -(int64_t)nx, -1, 0, 1, nx, sxy};
+    double x[7][S];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const int64_t nb = row + off[q];
+      load_row<S, EXACT>(Y + ((nb >= 0 && nb < n) ? nb : row) * s, s, x[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+#pragma unroll
+      for (int k = 0; k < S; ++k) ky[k] = fma(c[q], x[q][k], ky[k]);
+  } else {
+    const int64_t q = row >> 5;
+    const int lane = (int)(row & 31);
+    const int64_t b0 = sptr[q];
+    const int w = (int)((sptr[q + 1] - b0) >> 5);
+    const double* vp = val + b0 + lane;
+    const int* cpp = col + b0 + lane;
+    for (int t = 0; t < w; ++t) {
+      const double v = __ldg(vp + (int64_t)t * 32);
+      const int c = __ldg(cpp + (int64_t)t * 32);
+      double x[S];
+      load_row<S, EXACT>(Y + (int64_t)c * s, s, x);
+#pragma unroll
+      for (int k = 0; k < S; ++k) ky[k] = fma(v, x[k], ky[k]);
+    }
   }
   double y[S], bb[S], out[S];
   load_row<S, EXACT>(Y + row * s, s, y);
@@ -226,16 +275,34 @@ void launch_coupled(pint_op op, const double* Y, const double* B, const double* 
                    8.0 * N * s * (2 + (B ? 1 : 0) + (B0 ? 1 : 0)),
                2.0 * op->nnz * s + 2.0 * N * nza, st);
   const int lo = coupling_band(op->A1, op->A2, s);
+  const bool sten = op->grid_nx > 0;
+  if (sten && !op->stenK_valid) {
+    if (!op->stenK) op->stenK = dalloc_n<double>(op->ctx, 8 * op->n);
+    k_stencil_coefs<double><<<grid_for(op->n, 256), 256, 0, st>>>(
+        op->n, op->grid_nx, op->grid_ny, op->grid_nz, op->rowptr, op->Kval, nullptr, op->stenK);
+    check_launch("k_stencil_coefs(K)");
+    op->ctx->launches += 1;
+    op->stenK_valid = true;
+  }
+  const int nx = op->grid_nx;
+  const int64_t sxy = (int64_t)op->grid_nx * op->grid_ny;
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool E = decltype(E_)::value;
     auto launch = [&](auto kern) {
       kern<<<grid_for(op->n, 256), 256, 0, st>>>(op->n, s, op->sell.slice_ptr, op->sell.col,
-                                                 op->sellK, op->Mdiag, Y, B, B0, R, cp);
+                                                 sten ? op->stenK : op->sellK, op->Mdiag, Y, B,
+                                                 B0, R, cp, nx, sxy);
     };
-    if (lo == 1) launch(k_coupled<S, E, 1>);
-    else if (lo == 2) launch(k_coupled<S, E, 2>);
-    else launch(k_coupled<S, E, 0>);
+    if (sten) {
+      if (lo == 1) launch(k_coupled<S, E, 1, true>);
+      else if (lo == 2) launch(k_coupled<S, E, 2, true>);
+      else launch(k_coupled<S, E, 0, true>);
+    } else {
+      if (lo == 1) launch(k_coupled<S, E, 1, false>);
+      else if (lo == 2) launch(k_coupled<S, E, 2, false>);
+      else launch(k_coupled<S, E, 0, false>);
+    }
   });
   check_launch("k_coupled");
   op->ctx->launches += 1;
@@ -277,8 +344,163 @@ k_spmm(int64_t n, int s, const int64_t* __restrict__ sptr, const int* __restrict
   store_row<S, EXACT>(Z + row * s, s, acc);
 }
 
+// ------------------------------------- inner SpMM, stencil form (a4)
+// Operators of the FV constructors have the natural-order 7-point pattern
+// (5-point in 2-D, 3-point in 1-D): row r holds at most the entries of the
+// columns r - nx ny, r - nx, r - 1, r, r + 1, r + nx, r + nx ny, in this
+// (CSR) order. The stencil copy keeps them 8 to a row in that order (absent
+// neighbours 0, slot 7 padding), so one row's coefficients are one aligned
+// 16- or 32-byte load and the neighbour rows of X are read at fixed offsets
+// by consecutive threads: coalesced, without column indices. The products are
+// accumulated in the same order as the CSR / SELL form, so both forms give
+// the same result.
+void* inner_stencil(pint_op op, int precision, bool jacobi, cudaStream_t st) {
+  void*& slot = op->stenJ[precision][jacobi ? 1 : 0];
+  if (slot) return slot;
+  const size_t es = precision == PINT_FP64 ? 8 : precision == PINT_FP32 ? 4 : 2;
+  slot = dalloc(op->ctx, es * 8 * op->n);
+  const double* cs = jacobi ? op->Jinvdiag : nullptr;
+  const unsigned g = grid_for(op->n, 256);
+  const int nx = op->grid_nx, ny = op->grid_ny, nz = op->grid_nz;
+  if (precision == PINT_FP64)
+    k_stencil_coefs<double><<<g, 256, 0, st>>>(op->n, nx, ny, nz, op->rowptr, op->Jval, cs,
+                                               static_cast<double*>(slot));
+  else if (precision == PINT_FP32)
+    k_stencil_coefs<float><<<g, 256, 0, st>>>(op->n, nx, ny, nz, op->rowptr, op->Jval, cs,
+                                              static_cast<float*>(slot));
+  else
+    k_stencil_coefs<__nv_bfloat16><<<g, 256, 0, st>>>(op->n, nx, ny, nz, op->rowptr, op->Jval,
+                                                      cs, static_cast<__nv_bfloat16*>(slot));
+  check_launch("k_stencil_coefs");
+  op->ctx->launches += 1;
+  return slot;
+}
+
+// the 8 stencil coefficients of one row, as the accumulation type
+template <typename MT, typename A>
+__device__ __forceinline__ void ld_coef8(const MT* __restrict__ p, A (&c)[8]) {
+  if constexpr (std::is_same<MT, double>::value) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double2 v = __ldg(q + i);
+      c[2 * i] = v.x; c[2 * i + 1] = v.y;
+    }
+  } else if constexpr (std::is_same<MT, float>::value) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+  } else {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(h[i]);
+      c[2 * i] = f.x; c[2 * i + 1] = f.y;
+    }
+  }
+}
+
+// MODE 0: Z = J X ; MODE 1: Z = Rin - J X
+// Row mapping: TILED (grids with ny > 1) gives a block of 32 x 8 threads a
+// patch of 32 x-cells by 8 y-lines of one z-plane (grid nx/32 x ny/8 x nz), so
+// most +-1 and +-nx neighbour rows are rows the same block reads; otherwise
+// 256 consecutive rows.
+template <typename MT, typename VT, int S, bool EXACT, int MODE, bool TILED>
+__global__ void __launch_bounds__(256)
+k_stencil(int64_t n, int nx, int ny, int s, const MT* __restrict__ C8,
+          const VT* __restrict__ X, VT* __restrict__ Z, const VT* __restrict__ Rin) {
+  using A = VT;
+  const int64_t sxy = (int64_t)nx * ny;
+  int64_t row;
+  if constexpr (TILED) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    row = i + (int64_t)nx * j + sxy * blockIdx.z;
+  } else {
+    row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+  }
+  A c[8];
+  ld_coef8<MT, A>(C8 + 8 * row, c);
+  // all seven rows are loaded at once (an absent neighbour, whose coefficient
+  // is 0, reads the row itself), then accumulated in the CSR order
+  const int64_t off[7] = {-sxy, -(int64_t)nx, -1, 0, 1, nx, sxy};
+  A x[7][S];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const int64_t nb = row + off[q];
+    load_row<S, EXACT>(X + ((nb >= 0 && nb < n) ? nb : row) * s, s, x[q]);
+  }
+  A acc[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) acc[k] = A(0);
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc[k] = fma(c[q], x[q][k], acc[k]);
+  if constexpr (MODE == 1) {
+    A r[S];
+    load_row<S, EXACT>(Rin + row * s, s, r);
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc[k] = r[k] - acc[k];
+  }
+  store_row<S, EXACT>(Z + row * s, s, acc);
+}
+
+static void launch_stencil_spmm(pint_op op, int precision, bool jacobi, const void* X, void* Z,
+                                const void* Rin, cudaStream_t st) {
+  void* val = inner_stencil(op, precision, jacobi, st);
+  const int s = op->s;
+  const unsigned g = grid_for(op->n, 256);
+  const double vs = precision == PINT_FP64 ? 8.0 : precision == PINT_FP32 ? 4.0 : 2.0;
+  const double xs = precision == PINT_FP64 ? 8.0 : 4.0;
+  // algorithmic bytes of the product in CSR form (values and int32 column
+  // indices of the nnz entries, the row pointer, X read and Z written once,
+  // Rin read once), the same count as the SELL form books; the stencil form
+  // itself moves 8 coefficients per row instead of the nnz values and indices
+  ProfScope ps(op->ctx, PF_SPMM,
+               op->nnz * (vs + 4.0) + 4.0 * (op->n + 1) + xs * op->n * s * (Rin ? 3 : 2),
+               2.0 * op->nnz * s, st);
+  const int nx = op->grid_nx, ny = op->grid_ny, nz = op->grid_nz;
+  const bool tiled = ny > 1;
+  const dim3 tb(32, 8);
+  const dim3 tg((unsigned)((nx + 31) / 32), (unsigned)((ny + 7) / 8), (unsigned)nz);
+  with_s(s, [&](auto S_, auto E_) {
+    constexpr int S = decltype(S_)::value;
+    constexpr bool E = decltype(E_)::value;
+    auto go = [&](auto kflat, auto ktile, const auto* v, const auto* x, auto* z, const auto* rin) {
+      if (tiled) ktile<<<tg, tb, 0, st>>>(op->n, nx, ny, s, v, x, z, rin);
+      else kflat<<<g, 256, 0, st>>>(op->n, nx, ny, s, v, x, z, rin);
+    };
+    if (precision == PINT_FP64) {
+      if (Rin) go(k_stencil<double, double, S, E, 1, false>, k_stencil<double, double, S, E, 1, true>, (const double*)val, (const double*)X,
+                  (double*)Z, (const double*)Rin);
+      else go(k_stencil<double, double, S, E, 0, false>, k_stencil<double, double, S, E, 0, true>, (const double*)val, (const double*)X,
+              (double*)Z, (const double*)nullptr);
+    } else if (precision == PINT_FP32) {
+      if (Rin) go(k_stencil<float, float, S, E, 1, false>, k_stencil<float, float, S, E, 1, true>, (const float*)val, (const float*)X,
+                  (float*)Z, (const float*)Rin);
+      else go(k_stencil<float, float, S, E, 0, false>, k_stencil<float, float, S, E, 0, true>, (const float*)val, (const float*)X, (float*)Z,
+              (const float*)nullptr);
+    } else {
+      if (Rin) go(k_stencil<__nv_bfloat16, float, S, E, 1, false>, k_stencil<__nv_bfloat16, float, S, E, 1, true>, (const __nv_bfloat16*)val,
+                  (const float*)X, (float*)Z, (const float*)Rin);
+      else go(k_stencil<__nv_bfloat16, float, S, E, 0, false>, k_stencil<__nv_bfloat16, float, S, E, 0, true>, (const __nv_bfloat16*)val,
+              (const float*)X, (float*)Z, (const float*)nullptr);
+    }
+  });
+  check_launch("k_stencil");
+  op->ctx->launches += 1;
+}
+
 void launch_inner_spmm(pint_op op, int precision, bool jacobi, const void* X, void* Z,
                        const void* Rin, cudaStream_t st) {
+  if (op->grid_nx > 0) {
+    launch_stencil_spmm(op, precision, jacobi, X, Z, Rin, st);
+    return;
+  }
   void* val = inner_sell(op, precision, jacobi, st);
   const int s = op->s;
   const unsigned g = grid_for(op->n, 256);

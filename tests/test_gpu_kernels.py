@@ -85,12 +85,26 @@ def test_operator_assemble_rejects_bad_csr(P, ctx):
         P.pint_operator_assemble(ctx, 2, rp, ci, np.ones(2))
 
 
+@pytest.mark.parametrize("path", ["stencil", "csr"])
+@pytest.mark.parametrize("dims", [(13, 11, 7), (40, 33, 1), (37, 1, 1)])
 @pytest.mark.parametrize("s", [1, 3, 8, 16])
-def test_inner_apply_and_jacobi(P, ctx, s):
+def test_inner_apply_and_jacobi(P, ctx, s, dims, path):
+    """J X and the Jacobi step against the oracle's CSR product, for grid
+    operators (stencil-form SpMM) and the same matrix assembled as plain CSR
+    (SELL-32 SpMM)."""
     import torch
-    dims = (13, 11, 7)
     D, K, n = _problem(dims, 3)
-    op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), (1.0, -0.5, 0.25))
+    v = (1.0, -0.5, 0.25) if dims[2] > 1 else (1.0, -0.5, 0.0)
+    if dims[1] == 1:
+        v = (1.0, 0.0, 0.0)
+    K = fv.convdiff_matrix(dims, D, v)
+    if path == "stencil":
+        op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), v)
+    else:
+        Kc = K.tocsr()
+        Kc.sort_indices()
+        op = P.pint_operator_assemble(ctx, n, Kc.indptr.astype(np.int32),
+                                      Kc.indices.astype(np.int32), Kc.data)
     try:
         A, _, _ = coupling.sdirk2()
         tau = 0.02
@@ -104,6 +118,41 @@ def test_inner_apply_and_jacobi(P, ctx, s):
         np.testing.assert_allclose(Z.cpu().numpy(), J @ X, rtol=1e-13, atol=1e-10)
         P.pint_precond_apply(ctx, op, P.PINT_PC_JACOBI, _dev(X), Z)
         np.testing.assert_allclose(Z.cpu().numpy(), krylov.jacobi(J.tocsr())(X), rtol=1e-15)
+    finally:
+        P.pint_operator_destroy(op)
+
+
+@pytest.mark.parametrize("path", ["stencil", "csr"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("s", [1, 4, 8, 16])
+def test_inner_apply_low_precision(P, ctx, s, prec, path):
+    """Z = J X with the float32 / bfloat16 copies of J (float32 vectors and
+    accumulation) against the float64 CSR product. Per entry the error is a
+    few roundings of the matrix values (2^-24 / 2^-9 relative) and of the
+    float32 products, relative to sum_j |J_ij| |X_j|."""
+    import torch
+    dims = (21, 13, 9)
+    D, K, n = _problem(dims, 5)
+    if path == "stencil":
+        op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), (1.0, -0.5, 0.25))
+    else:
+        Kc = K.tocsr()
+        Kc.sort_indices()
+        op = P.pint_operator_assemble(ctx, n, Kc.indptr.astype(np.int32),
+                                      Kc.indices.astype(np.int32), Kc.data)
+    try:
+        tau = 0.01
+        P.pint_set_coupling(ctx, op, np.eye(s) / tau, np.eye(s))
+        X = synth.uniform(9, n * s).reshape(n, s).astype(np.float32)
+        Z = torch.empty(n, s, device="cuda", dtype=torch.float32)
+        code = P.PINT_FP32 if prec == "fp32" else P.PINT_BF16
+        P.pint_inner_apply_lowp(ctx, op, code, torch.tensor(X, device="cuda"), Z)
+        torch.cuda.synchronize()
+        J = (sp.identity(n) / tau + K).tocsr()
+        ref = J @ X.astype(np.float64)
+        scale = abs(J) @ np.abs(X.astype(np.float64))
+        rel = 16 * 2.0 ** -24 if prec == "fp32" else 2.0 ** -8
+        assert np.all(np.abs(Z.cpu().numpy() - ref) <= rel * scale + 1e-30)
     finally:
         P.pint_operator_destroy(op)
 

@@ -18,12 +18,21 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a), device="cuda", dtype=torch.float64)
 
 
-def _setup(P, ctx, dims, s, tau, seed=1, v=(1.0, 0.5, 0.0), lognormal=True):
+def _setup(P, ctx, dims, s, tau, seed=1, v=(1.0, 0.5, 0.0), lognormal=True, form="grid"):
+    """form "grid": the FV constructor (stencil-form SpMM, row-of-tiles ILU(0));
+    "csr": the same matrix through pint_operator_assemble (SELL-32 SpMM,
+    level-scheduled ILU(0))."""
     n = int(np.prod(dims))
     D = np.exp(synth.normal(seed, n)).reshape(dims[::-1]) if lognormal else \
         np.ones(dims[::-1])
     K = fv.convdiff_matrix(dims, D, v)
-    op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), v)
+    if form == "grid":
+        op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), v)
+    else:
+        Kc = K.tocsr()
+        Kc.sort_indices()
+        op = P.pint_operator_assemble(ctx, n, Kc.indptr.astype(np.int32),
+                                      Kc.indices.astype(np.int32), Kc.data)
     A, _, _ = coupling.implicit_euler()
     A1, A2, _ = coupling.multistep_matrices(A, s, tau)
     P.pint_set_coupling(ctx, op, A1, A2)
@@ -78,13 +87,14 @@ def test_slab_ilu0_3d(P, ctx, s):
         P.pint_operator_destroy(op)
 
 
+@pytest.mark.parametrize("form", ["grid", "csr"])
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("pc", ["jacobi", "ilu0"])
-def test_slab_mixed_precision_refinement(P, ctx, prec, pc):
+def test_slab_mixed_precision_refinement(P, ctx, prec, pc, form):
     import torch
     dims = (16, 16, 16)
     s = 4
-    op, K, n, A, A1, A2, B = _setup(P, ctx, dims, s, 1e-3, seed=3)
+    op, K, n, A, A1, A2, B = _setup(P, ctx, dims, s, 1e-3, seed=3, form=form)
     try:
         Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
         o = P.pint_opts_default()
