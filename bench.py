@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 METRIC = ("time-step·DOF/s and block-SpMM HBM GB/s (% roofline) at s=1..16, "
           "mixed vs FP64")
 UNIT = "time-step*DOF/s"
-FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (non-tensor and tensor alike)
+FP64_NOMINAL_TFLOPS = 1.25   # nominal GB300 FP64 (context; the rooflines use the measured rate)
 
 
 WORKLOADS = {
@@ -83,8 +83,8 @@ def parse(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true",
                    help="skip the pure-FP64 run of the same workload")
-    p.add_argument("--sweep", action="store_true",
-                   help="also time one solve per (s, precision) for s=1..16")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="skip the s = 1..16 sweep (one timed solve per s and precision)")
     p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=8.0, help="serve: mean arrivals per second")
     p.add_argument("--slots", type=int, default=4, help="serve: concurrent solves")
@@ -186,21 +186,38 @@ def oracle_sample_size(args):
             "serve": 32}[args.workload]
 
 
-def reference_sample_size(args):
-    return {"convdiff3d": 32, "convdiff2d": 64, "diffreact": 64, "richards": 12,
-            "serve": 32}[args.workload]
-
-
-def run_oracle_subprocess(args, n, reps):
+def _oracle_cmd(args, n, reps):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n), "--s", str(args.s),
            "--steps", str(reps), "--workload", args.workload, "--precond", args.precond,
            "--solver", args.solver, "--restart", str(args.restart)]
+    return cmd, env
+
+
+def run_oracle_subprocess(args, n, reps):
+    cmd, env = _oracle_cmd(args, n, reps)
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_all_cores(args, n, cores=None):
+    """The same oracle sample solved by one single-threaded process per host
+    core, all at once: returns (cores, wall seconds, per-process results)."""
+    cores = cores or os.cpu_count() or 1
+    cmd, env = _oracle_cmd(args, n, 1)
+    t = time.perf_counter()
+    procs = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                              env=env) for _ in range(cores)]
+    outs = []
+    for pr in procs:
+        o, e = pr.communicate(timeout=1800)
+        if pr.returncode != 0:
+            raise RuntimeError(e[-2000:])
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    return cores, time.perf_counter() - t, outs
 
 
 # ----------------------------------------------------------------- clocks
@@ -337,7 +354,7 @@ def ncu_traffic(family, workload):
     return e.get("dram_bytes_per_launch")
 
 
-def roofline(fam, prof, hbm_peak, peak_kind, precision, workload):
+def roofline(fam, prof, hbm_peak, peak_kind, precision, workload, fp64_peak):
     tot_ms = prof["ms"]
     if tot_ms <= 0 or prof["launches"] == 0:
         return None
@@ -346,12 +363,12 @@ def roofline(fam, prof, hbm_peak, peak_kind, precision, workload):
     flops_pl = prof["flops"] / prof["launches"]
     gbs = bytes_pl / per_launch_s / 1e9
     t_mem = bytes_pl / (hbm_peak * 1e9)
-    t_alu = flops_pl / (FP64_PEAK_TFLOPS * 1e12) if precision == "fp64" else 0.0
+    t_alu = flops_pl / (fp64_peak * 1e12) if precision == "fp64" else 0.0
     if t_alu > t_mem:
         ach = flops_pl / per_launch_s / 1e12
         return {"kernel": fam, "bound": "alu", "achieved": round(ach, 4),
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "nominal FP64 of GB300 (recipe table)",
+                "peak": round(fp64_peak, 4), "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4),
+                "peak_source": "measured float64 FMA rate (pint_fp64_fma_peak, this run)",
                 "traffic": ncu_traffic(fam, workload),
                 "algorithmic_bytes_per_launch": bytes_pl, "launches": prof["launches"],
                 "avg_launch_us": per_launch_s * 1e6}
@@ -545,10 +562,17 @@ def main():
         samp = oracle_sample_size(args)
         try:
             r = run_oracle_subprocess(args, samp, 1)
-            v = r["steps"] * r["n"] / min(r["times"])
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"one oracle run (FP64, {args.precond}, same recipe) on {r['n']} "
-                             f"cells, {r['steps']} time steps: {min(r['times']):.1f} s"}
+            v1 = r["steps"] * r["n"] / min(r["times"])
+            cores, wall, outs = run_oracle_all_cores(args, samp)
+            work = sum(o["steps"] * o["n"] for o in outs)
+            cpu = {"value": work / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{cores} single-threaded oracle processes (FP64, {args.precond}, "
+                             f"same recipe), one per host core, each solving the same "
+                             f"{r['n']}-cell sample of {r['steps']} time steps at once: "
+                             f"{wall:.1f} s wall",
+                   "one_core": {"value": v1, "cores": 1,
+                                "sample": f"one oracle run on {r['n']} cells, {r['steps']} "
+                                          f"time steps: {min(r['times']):.1f} s"}}
         except Exception as e:          # report, do not hide
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {e}"[:300]}
@@ -565,6 +589,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     ctx = P.pint_create(local)
+    fp64_peak = P.pint_fp64_fma_peak(ctx)
     case = LinearCase(P, ctx, args) if linear(args) else PipelineCase(P, ctx, args)
     stream = torch.cuda.current_stream()
 
@@ -666,9 +691,11 @@ def main():
         "dtype": "f64" if args.precision == "fp64" else f"f64+{args.precision}",
         "data": "synthetic", "config": cfg,
         "roofline": roofline(dominant, fams[dominant], hbm_peak, peak_kind, args.precision,
-                             wl_name),
+                             wl_name, fp64_peak),
         "spmm_roofline": roofline("spmm", fams["spmm"], hbm_peak, peak_kind, args.precision,
-                                  wl_name),
+                                  wl_name, fp64_peak),
+        "fp64_peak": {"tflops": round(fp64_peak, 4), "source": "pint_fp64_fma_peak (measured "
+                      "on this GPU in this run)", "nominal_tflops": FP64_NOMINAL_TFLOPS},
         "kernels": kernels, "profiled_ms_per_step": profiled_ms,
         "iterations": {"outer": stats[-1]["outer_its"], "inner": stats[-1]["inner_its"],
                        "restarts": stats[-1]["restarts"]},
@@ -680,8 +707,9 @@ def main():
     }
     if linear(args):
         out["spmm_full_width"] = spmm_full_width(P, ctx, case, args.precision, hbm_peak)
-    if args.sweep and linear(args):
-        out["sweep"] = sweep(P, ctx, args, case.w)
+    if not args.no_sweep and args.workload == "convdiff3d":
+        out["sweep"] = sweep(P, ctx, args, case.w, fp64_peak)
+        out["sweep_summary"] = sweep_summary(out["sweep"])
     print(json.dumps(out), flush=True)
     case.close()
     P.pint_destroy(ctx)
@@ -740,8 +768,8 @@ def spmm_full_width(P, ctx, case, prec, hbm_peak, reps=20):
 
 def precision_variant(P, case, args, stream, prec="fp64"):
     """Time the same step with another inner-solve precision (one warm-up,
-    then up to two timed steps): FP64 is the "mixed vs FP64" half of the
-    metric, BF16 the bfloat16-matrix variant of the mixed path."""
+    then as many timed steps as the headline): FP64 is the "mixed vs FP64"
+    half of the metric, BF16 the bfloat16-matrix variant of the mixed path."""
     import torch
     prec0, tol0 = case.o.precision, case.o.inner_tol
     case.o.precision = {"fp64": P.PINT_FP64, "fp32": P.PINT_FP32, "bf16": P.PINT_BF16}[prec]
@@ -750,7 +778,7 @@ def precision_variant(P, case, args, stream, prec="fp64"):
     case.o.inner_tol = inner_tol_for(ns, case.s)
     try:
         case.step()
-        k = max(1, min(2, args.steps))
+        k = max(1, args.steps)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -770,7 +798,7 @@ def precision_variant(P, case, args, stream, prec="fp64"):
         case.o.precision, case.o.inner_tol = prec0, tol0
 
 
-def sweep(P, ctx, args, w0):
+def sweep(P, ctx, args, w0, fp64_peak):
     """One timed solve per (precision, s) on the same grid (after one warm-up
     solve each): time-step*DOF/s, SpMM GB/s and the SpMM's s-dependent
     arithmetic-intensity roofline (flop per byte, achieved and attainable
@@ -822,11 +850,24 @@ def sweep(P, ctx, args, w0):
                         "status": st.status, "spmm_GBs": gbs,
                         "spmm_ai_flop_per_byte": ai, "spmm_ai_full_width": ai_full,
                         "spmm_gflops": sp["flops"] / max(sp["ms"], 1e-9) / 1e6,
-                        "spmm_roof_gflops": min(roof, 1e3 * FP64_PEAK_TFLOPS)
+                        "spmm_roof_gflops": min(roof, 1e3 * fp64_peak)
                         if prec_name == "fp64" else roof})
             P.pint_operator_destroy(op)
             del Bd, Y
     return res
+
+
+def sweep_summary(rows):
+    """Per precision: time-step*DOF/s at s = 8 over s = 1 (the s-scaling
+    target is >= 3) and the best width."""
+    out = {}
+    for prec in sorted({r["precision"] for r in rows}):
+        v = {r["s"]: r["value"] for r in rows if r["precision"] == prec and r["status"] == 0}
+        if 1 in v and 8 in v:
+            best = max(v, key=v.get)
+            out[prec] = {"s8_over_s1": round(v[8] / v[1], 3), "best_s": best,
+                         "best_over_s1": round(v[best] / v[1], 3)}
+    return out
 
 
 def serve_main(args, world, rank, local, cpu, desc):
@@ -907,8 +948,8 @@ def serve_main(args, world, rank, local, cpu, desc):
 
 def reference_arm(args, wl_name, desc, world):
     """The oracle as it stands, timed on this host's cores, on a bounded
-    sample of the workload per step."""
-    samp = reference_sample_size(args)
+    sample of the workload per step (the same sample as cpu_baseline)."""
+    samp = oracle_sample_size(args)
     r = run_oracle_subprocess(args, samp, args.warmup + args.steps)
     times = r["times"][args.warmup:]
     per = statistics.mean(times)

@@ -355,6 +355,12 @@ int pint_block_gram_noalloc(int precision, int64_t n, int s, int nb,
  * so the context stays usable. Synchronous. Returns PINT_ERR_TIMEOUT when
  * the wait ran out, as it must. */
 int pint_test_wait_timeout(pint_ctx ctx, int which, double limit_ms, void* stream);
+/* Measured float64 FMA throughput of the context's device (no paper
+ * counterpart; the roofline denominator of the float64 kernels): eight
+ * independent FMA chains per thread on 8 blocks of 256 threads per SM, best
+ * of three CUDA-event-timed launches after a warm-up, 2 flops per FMA.
+ * *tflops receives TFLOP/s. Synchronous; runs on the legacy default stream. */
+int pint_fp64_fma_peak(pint_ctx ctx, double* tflops);
 /* norms[k] = ||X_k||_2 (host array of s doubles). Synchronous. */
 int pint_colnorms(pint_ctx ctx, int precision, int64_t n, int s,
                   const void* X, double* norms, void* stream);

@@ -107,6 +107,7 @@ _SIGS = {
     "pint_cholqr2": (_i, [_vp, _i, _i64, _i, _vp, _vp, _vp]),
     "pint_colnorms": (_i, [_vp, _i, _i64, _i, _vp, _vp, _vp]),
     "pint_test_wait_timeout": (_i, [_vp, _i, _d, _vp]),
+    "pint_fp64_fma_peak": (_i, [_vp, C.POINTER(_d)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -346,6 +347,13 @@ def pint_test_wait_timeout(ctx, which, limit_ms, stream=None):
     """Run one bounded device wait that must run out (0: the ILU(0) flag
     wait, 1: the bulk-copy mbarrier wait); returns the status code."""
     return lib.pint_test_wait_timeout(ctx, which, limit_ms, _stream(stream))
+
+
+def pint_fp64_fma_peak(ctx):
+    """Measured float64 FMA throughput of the device, TFLOP/s."""
+    v = C.c_double()
+    _check(lib.pint_fp64_fma_peak(ctx, C.byref(v)), ctx)
+    return v.value
 
 
 def pint_profile_enable(ctx, on=True):

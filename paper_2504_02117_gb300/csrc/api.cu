@@ -534,6 +534,59 @@ int pint_cholqr2(pint_ctx ctx, int precision, int64_t n, int s, void* W, double*
   });
 }
 
+// Eight independent float64 FMA chains per thread (latency hidden), one
+// result per thread so nothing is optimised away.
+__global__ void __launch_bounds__(256) k_fp64_fma_peak(int iters, double* out) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1e-3 * (threadIdx.x + k);
+  const double b = 0.9999999, c = 1e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v += a[k];
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = v;
+}
+
+int pint_fp64_fma_peak(pint_ctx ctx, double* tflops) {
+  if (!ctx || !tflops) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    const int blocks = ctx->num_sms * 8, threads = 256, iters = 4096;
+    double* out = dalloc_n<double>(ctx, (size_t)blocks * threads);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double best = 0.0;
+    try {
+      PINT_CUDA(cudaEventCreate(&e0));
+      PINT_CUDA(cudaEventCreate(&e1));
+      for (int rep = 0; rep < 4; ++rep) {            // the first is a warm-up
+        PINT_CUDA(cudaEventRecord(e0, nullptr));
+        k_fp64_fma_peak<<<blocks, threads>>>(iters, out);
+        check_launch("k_fp64_fma_peak");
+        PINT_CUDA(cudaEventRecord(e1, nullptr));
+        PINT_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PINT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const double fl = 2.0 * 8.0 * iters * (double)blocks * threads;
+        if (rep > 0 && ms > 0.f) best = std::max(best, fl / (ms * 1e-3) / 1e12);
+      }
+      ctx->launches += 4;
+    } catch (...) {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      dfree(ctx, out, sizeof(double) * blocks * threads);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(ctx, out, sizeof(double) * blocks * threads);
+    *tflops = best;
+    return PINT_OK;
+  });
+}
+
 int pint_test_wait_timeout(pint_ctx ctx, int which, double limit_ms, void* stream) {
   if (!ctx) return PINT_ERR_INVALID;
   return guard(ctx, [&] {

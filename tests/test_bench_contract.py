@@ -36,18 +36,20 @@ def test_inner_tolerances_follow_the_paper():
 def test_roofline_hbm_and_alu_cases():
     # 10 launches, 1 GB each, 100 us each -> 10 TB/s against a 5 TB/s peak
     prof = {"ms": 1.0, "bytes": 10e9, "flops": 1e6, "launches": 10}
-    r = bench.roofline("spmm", prof, 5000.0, "measured", "fp32", "none")
+    r = bench.roofline("spmm", prof, 5000.0, "measured", "fp32", "none", 1.3)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(10000.0) and r["frac"] == pytest.approx(2.0)
     assert r["algorithmic_bytes_per_launch"] == pytest.approx(1e9)
     assert r["avg_launch_us"] == pytest.approx(100.0)
     # float64 with more flop time than byte time: reported against the FP64 rate
     prof = {"ms": 1.0, "bytes": 1e6, "flops": 1e9, "launches": 1}
-    r = bench.roofline("gram", prof, 5000.0, "measured", "fp64", "none")
+    r = bench.roofline("gram", prof, 5000.0, "measured", "fp64", "none", 1.25)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["achieved"] == pytest.approx(1.0) and r["peak"] == bench.FP64_PEAK_TFLOPS
+    # the measured FP64 rate passed in is the denominator
+    assert r["achieved"] == pytest.approx(1.0) and r["peak"] == pytest.approx(1.25)
+    assert r["frac"] == pytest.approx(0.8)
     assert bench.roofline("x", {"ms": 0.0, "bytes": 0, "flops": 0, "launches": 0}, 1, "m",
-                          "fp32", "w") is None
+                          "fp32", "w", 1.0) is None
 
 
 def test_traffic_lookup_only_for_the_captured_sources():
@@ -116,3 +118,13 @@ def test_spbop_byte_model_reduces_to_the_papers_count():
     ai = [bench.spbop_ai(nnz, n, k) for k in (1, 2, 4, 8, 16)]
     assert all(a < b for a, b in zip(ai, ai[1:]))
     assert ai[-1] < 2.0 * nnz / n / (2 * 8)
+
+
+def test_sweep_summary_ratios():
+    rows = [{"precision": "fp32", "s": s, "value": v, "status": 0}
+            for s, v in ((1, 1.0), (2, 2.0), (4, 2.5), (8, 3.5), (16, 3.0))]
+    rows.append({"precision": "fp64", "s": 1, "value": 2.0, "status": 0})
+    rows.append({"precision": "fp64", "s": 8, "value": 1.0, "status": 0})
+    sm = bench.sweep_summary(rows)
+    assert sm["fp32"] == {"s8_over_s1": 3.5, "best_s": 8, "best_over_s1": 3.5}
+    assert sm["fp64"]["s8_over_s1"] == 0.5 and sm["fp64"]["best_s"] == 1
