@@ -105,11 +105,9 @@ k_gram(int64_t n, int s, int nb, const VT* __restrict__ V, int64_t bstride,
 // Same product over a zero-padded row range [0, n_pad): each CTA streams
 // tiles of TR rows of the nb+1 blocks (V_0..V_{nb-1}, W) into shared memory
 // with 1-D bulk copies (cp.async.bulk, completion on an mbarrier) through a
-// ring of kStages stages, so that every SM keeps >100 KB of loads in flight
-// while the threads multiply the previous tiles. Waits on the mbarriers are
-// bounded (globaltimer); a timeout raises *err and the CTA drains without
-// waiting further.
-constexpr int kStages = 4;
+// ring of stages (k_gram_bulk below). Waits on the mbarriers are bounded
+// (globaltimer); a timeout raises *err and the CTA drains without waiting
+// further.
 constexpr unsigned long long kMbarBudgetNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -197,13 +195,28 @@ __device__ __forceinline__ void lds_q(const VT* p, VT (&v)[Q]) {
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+constexpr int kGramMaxStages = 8;
+
+// Warp-specialised form: NT consumer threads and one producer warp (threads
+// NT .. NT+31). The producer fills a ring of ST stages of TR rows of the nb+1
+// blocks with 1-D bulk copies (completion on the stage's "full" mbarrier);
+// each consumer warp arrives on the stage's "empty" mbarrier when it has
+// read the stage, and the producer waits for that before refilling it, so no
+// CTA-wide barrier separates the tiles. Every wait is bounded (globaltimer);
+// a timeout raises *err, stops the producer and the remaining waits, and the
+// producer drains its copies in flight before the CTA reuses the ring.
 template <typename VT, int S, bool EXACT, int Q, int NQPT, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT + 32)
 k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstride,
-            const VT* __restrict__ W, int64_t rows_per_cta, int TR, int TRG,
+            const VT* __restrict__ W, int64_t rows_per_cta, int TR, int TRG, int ST,
             double* __restrict__ partial, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ __align__(8) uint64_t full[kGramMaxStages], empty[kGramMaxStages];
   __shared__ int aborted;
   const int P = nb * s;
   const int NQ = P / Q;                                   // quads (Q | s)
@@ -213,46 +226,21 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r1 = (r0 + rows_per_cta < n_pad) ? r0 + rows_per_cta : n_pad;
   const int ntiles = r1 > r0 ? (int)((r1 - r0) / TR) : 0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int i = 0; i < ST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NT / 32);
+    }
     aborted = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // Copies of one stage: thread t issues the blocks b = t, t + NT, ... <= nb
-  // (one copy each, so every one of the nb + 1 blocks is issued whatever nb);
-  // thread 0 also posts the expected byte count. A copy may complete before
-  // the expect_tx is posted: the phase still needs thread 0's arrival.
-  auto issue = [&](int stage, int tile) {
-    unsigned char* dst = smem_raw + (size_t)stage * stage_bytes;
-    if (threadIdx.x == 0) mbar_expect_tx(&bars[stage], blk_bytes * (nb + 1));
-    const int64_t row = r0 + (int64_t)tile * TR;
-    for (int b = threadIdx.x; b <= nb; b += NT) {
-      const VT* src = (b < nb ? V + (int64_t)b * bstride : W) + row * s;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bulk_g2s(dst + (size_t)b * blk_pitch, src, blk_bytes, &bars[stage]);
-    }
-  };
-  // pending[stage] = parity of a copy issued into the stage and not yet seen
-  // complete by thread 0 (-1: none); used to drain copies after a timeout
-  int pending[kStages];
-  for (int i = 0; i < kStages; ++i) pending[i] = -1;
-  for (int t = 0; t < kStages && t < ntiles; ++t) {
-    issue(t, t);
-    pending[t] = 0;
-  }
-  // this thread: quads q = qbase + j*QSTRIDE (j < NQPT), rows rr = rg + m*TRG
-  const int nthr_q = TRG * ((NQ + NQPT - 1) / NQPT);
-  const bool active = (int)threadIdx.x < nthr_q && threadIdx.x / ((NQ + NQPT - 1) / NQPT) < TRG;
+  const unsigned long long deadline = gtimer() + kMbarBudgetNs;
+  // consumer mapping: quads q = qbase + j*qstride (j < NQPT), rows rg + m*TRG
   const int qstride = (NQ + NQPT - 1) / NQPT;
-  const int qbase = threadIdx.x % qstride, rg = threadIdx.x / qstride;
-  int qoff[NQPT];
-#pragma unroll
-  for (int j = 0; j < NQPT; ++j) {
-    const int q = qbase + j * qstride;
-    const int p = q * Q;
-    qoff[j] = (q < NQ) ? (int)((p / s) * (blk_pitch / sizeof(VT)) + (p % s)) : -1;
-  }
+  const int qbase = tid % qstride, rg = tid / qstride;
+  const bool active = tid < NT && rg < TRG;
   VT acc[NQPT][Q][S];
 #pragma unroll
   for (int j = 0; j < NQPT; ++j)
@@ -260,78 +248,108 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
     for (int i = 0; i < Q; ++i)
 #pragma unroll
       for (int k = 0; k < S; ++k) acc[j][i][k] = VT(0);
-  const unsigned long long deadline = gtimer() + kMbarBudgetNs;
-  for (int t = 0; t < ntiles; ++t) {
-    const int stage = t % kStages;
-    const unsigned parity = (unsigned)((t / kStages) & 1);
-    if (!*(volatile int*)&aborted) {
-      const bool done = mbar_wait_bounded(&bars[stage], parity, deadline, &aborted, err, 3);
-      if (done && threadIdx.x == 0) pending[stage] = -1;
+  int qoff[NQPT];
+#pragma unroll
+  for (int j = 0; j < NQPT; ++j) {
+    const int q = qbase + j * qstride;
+    const int p = q * Q;
+    qoff[j] = (q < NQ) ? (int)((p / s) * (blk_pitch / sizeof(VT)) + (p % s)) : -1;
+  }
+  if (tid >= NT) {
+    // ------------------------------------------------------ producer warp
+    const int lane = tid - NT;
+    int last_t[kGramMaxStages];
+    for (int i = 0; i < kGramMaxStages; ++i) last_t[i] = -1;
+    for (int t = 0; t < ntiles; ++t) {
+      const int st = t % ST;
+      if (t >= ST) {            // the consumers have read the stage's previous tile
+        bool ok = true;
+        if (lane == 0)
+          ok = mbar_wait_bounded(&empty[st], (unsigned)((t / ST - 1) & 1), deadline, &aborted,
+                                 err, 3);
+        if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+      }
+      if (*(volatile int*)&aborted) break;
+      unsigned char* dst = smem_raw + (size_t)st * stage_bytes;
+      if (lane == 0) mbar_expect_tx(&full[st], blk_bytes * (nb + 1));
+      __syncwarp();
+      const int64_t row = r0 + (int64_t)t * TR;
+      for (int b = lane; b <= nb; b += 32) {
+        const VT* src = (b < nb ? V + (int64_t)b * bstride : W) + row * s;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_g2s(dst + (size_t)b * blk_pitch, src, blk_bytes, &full[st]);
+      }
+      last_t[st] = t;
     }
-    const VT* T = reinterpret_cast<const VT*>(smem_raw + (size_t)stage * stage_bytes);
-    const VT* Wt = reinterpret_cast<const VT*>(smem_raw + (size_t)stage * stage_bytes +
-                                               (size_t)nb * blk_pitch);
-    if (active) {
+    // every copy issued has landed before the ring's memory is reused below
+    // (bounded; after a timeout some stages were never consumed)
+    if (lane == 0) {
+      const unsigned long long drain = gtimer() + kMbarBudgetNs;
+      for (int i = 0; i < ST; ++i)
+        if (last_t[i] >= 0)
+          while (!mbar_try_wait(&full[i], (unsigned)((last_t[i] / ST) & 1)) && gtimer() < drain) {
+          }
+    }
+  } else {
+    // ----------------------------------------------------- consumer warps
+    for (int t = 0; t < ntiles; ++t) {
+      const int st = t % ST;
+      if (!*(volatile int*)&aborted)
+        mbar_wait_bounded(&full[st], (unsigned)((t / ST) & 1), deadline, &aborted, err, 3);
+      if (active && !*(volatile int*)&aborted) {
+        const VT* T = reinterpret_cast<const VT*>(smem_raw + (size_t)st * stage_bytes);
+        const VT* Wt = reinterpret_cast<const VT*>(smem_raw + (size_t)st * stage_bytes +
+                                                   (size_t)nb * blk_pitch);
 #pragma unroll 2
-      for (int rr = rg; rr < TR; rr += TRG) {
-        VT w[S];
-        if constexpr (EXACT) {
-          lds_q<VT, S>(Wt + rr * S, w);
-        } else {
+        for (int rr = rg; rr < TR; rr += TRG) {
+          VT w[S];
+          if constexpr (EXACT) {
+            lds_q<VT, S>(Wt + rr * S, w);
+          } else {
 #pragma unroll
-          for (int k = 0; k < S; ++k) w[k] = k < s ? Wt[rr * s + k] : VT(0);
-        }
+            for (int k = 0; k < S; ++k) w[k] = k < s ? Wt[rr * s + k] : VT(0);
+          }
 #pragma unroll
-        for (int j = 0; j < NQPT; ++j) {
-          if (qoff[j] >= 0) {
-            VT v[Q];
-            lds_q<VT, Q>(T + qoff[j] + rr * s, v);
+          for (int j = 0; j < NQPT; ++j) {
+            if (qoff[j] >= 0) {
+              VT v[Q];
+              lds_q<VT, Q>(T + qoff[j] + rr * s, v);
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
+              for (int i = 0; i < Q; ++i)
 #pragma unroll
-              for (int k = 0; k < S; ++k) acc[j][i][k] = fma(v[i], w[k], acc[j][i][k]);
+                for (int k = 0; k < S; ++k) acc[j][i][k] = fma(v[i], w[k], acc[j][i][k]);
+            }
           }
         }
       }
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&empty[st]);
     }
-    __syncthreads();
-    if (t + kStages < ntiles && !aborted) {
-      issue(stage, t + kStages);
-      pending[stage] = (int)(((t + kStages) / kStages) & 1);
-    }
-  }
-  // after a timeout, wait (bounded) for this CTA's copies still in flight
-  if (threadIdx.x == 0 && aborted) {
-    const unsigned long long drain = gtimer() + kMbarBudgetNs;
-    for (int i = 0; i < kStages; ++i)
-      if (pending[i] >= 0)
-        while (!mbar_try_wait(&bars[i], (unsigned)pending[i]) && gtimer() < drain) {
-        }
   }
   __syncthreads();
-  // reduce the TRG row groups in float64 (shared memory), write the partial
+  // the row groups' partial sums, each in its own slot, then summed per entry
+  // in row-group order (float64, deterministic)
   double* red = reinterpret_cast<double*>(smem_raw);
   const int E = P * s;
-  double* out = partial + (int64_t)blockIdx.x * E;
-  for (int rgi = 0; rgi < TRG; ++rgi) {
-    if (active && rg == rgi) {
+  if (active) {
 #pragma unroll
-      for (int j = 0; j < NQPT; ++j) {
-        if (qoff[j] < 0) continue;
-        const int p0 = (qbase + j * qstride) * Q;
+    for (int j = 0; j < NQPT; ++j) {
+      if (qoff[j] < 0) continue;
+      const int p0 = (qbase + j * qstride) * Q;
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
+      for (int i = 0; i < Q; ++i)
 #pragma unroll
-          for (int k = 0; k < S; ++k)
-            if (EXACT || k < s) {
-              const int e = (p0 + i) * s + k;
-              red[e] = (rgi == 0 ? 0.0 : red[e]) + (double)acc[j][i][k];
-            }
-      }
+        for (int k = 0; k < S; ++k)
+          if (EXACT || k < s) red[(size_t)rg * E + (p0 + i) * s + k] = (double)acc[j][i][k];
     }
-    __syncthreads();
   }
-  for (int e = threadIdx.x; e < E; e += NT) out[e] = red[e];
+  __syncthreads();
+  double* out = partial + (int64_t)blockIdx.x * E;
+  for (int e = tid; e < E; e += blockDim.x) {
+    double v = 0.0;
+    for (int g = 0; g < TRG; ++g) v += red[(size_t)g * E + e];
+    out[e] = v;
+  }
 }
 
 // H[e] = sum_blk partial[blk][e]. One warp per entry: lane l sums blocks
@@ -399,51 +417,55 @@ static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V,
   if (n_pad % 64 != 0 || (bstride * es) % 16 != 0 ||
       reinterpret_cast<uintptr_t>(V) % 16 != 0 || reinterpret_cast<uintptr_t>(W) % 16 != 0)
     return false;
-  // tile rows: largest power of two <= 64 with a stage of at most 48 KB
-  // (measured: 512-row tiles were slower at 128^3, s = 8)
-  int TR = 64;
-  while (TR > 4 && (size_t)(nb + 1) * (TR * s * es + kGramPad) > 48 * 1024) TR >>= 1;
-  if ((size_t)(nb + 1) * (TR * s * es + kGramPad) > 48 * 1024) return false;
-  const int64_t want = std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, n_pad / 64));
-  int64_t rpc = (n_pad + want - 1) / want;
-  rpc = std::max<int64_t>(TR, ((rpc + TR - 1) / TR) * TR);
-  if (n_pad % TR != 0) {           // keep whole tiles: fall back to 64-row tiles
-    TR = 64;
-    rpc = ((rpc + 63) / 64) * 64;
-  }
-  const int nblk = (int)((n_pad + rpc - 1) / rpc);
+  // tile rows: the largest power of two <= 1024 dividing n_pad with a stage of
+  // at most 48 KB, so a CTA keeps ~200 KB of loads in flight whatever nb and s
+  // in copies of at least 1 KB per block
+  auto stage_of = [&](int tr) { return (size_t)(nb + 1) * (tr * s * es + kGramPad); };
+  int TR = 1024;
+  while (TR > 4 && (stage_of(TR) > 66 * 1024 || n_pad % TR != 0)) TR >>= 1;
+  if (stage_of(TR) > 66 * 1024 || n_pad % TR != 0) return false;
+  const size_t stage_bytes = stage_of(TR);
+  const int STG = (int)std::max<size_t>(2, std::min<size_t>(kGramMaxStages, (210 * 1024) / stage_bytes));
   const int E = P * s;
-  ensure_partial(ctx, sizeof(double) * (size_t)nblk * E);
-  const size_t stage_bytes = (size_t)(nb + 1) * (TR * s * es + kGramPad);
   bool ok = true;
   with_s(s, [&](auto S_, auto E_) {
     constexpr int S = decltype(S_)::value;
     constexpr bool EX = decltype(E_)::value;
     constexpr int Q = EX ? (S >= 4 ? 4 : S) : 1;
-    constexpr int NT = 256;           // (512 threads measured slower)
+    constexpr int NT = 256;
     const int NQ = P / Q;
     const int npt = NQ <= NT ? 1 : NQ <= 2 * NT ? 2 : 4;
     const int qs = (NQ + npt - 1) / npt;
-    const int TRG = std::max(1, std::min(32, NT / qs));
-    const size_t red = sizeof(double) * (size_t)E;
-    const size_t smem = std::max(kStages * stage_bytes, red);
-    if (smem > 200 * 1024 || NQ > 1024) {
+    int TRG = std::max(1, std::min(64, NT / qs));
+    while (TRG > 1 && (size_t)TRG * E * 8 > 210 * 1024) TRG >>= 1;
+    const size_t smem = std::max((size_t)STG * stage_bytes, (size_t)TRG * E * 8);
+    if (smem > 210 * 1024 || NQ > 1024) {
       ok = false;
       return;
     }
     auto launch = [&](auto kern) {
       smem_attr(kern, smem);
-      kern<<<nblk, NT, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, TRG, ctx->d_partial,
-                                   ctx->d_flag);
+      int per_sm = 0;
+      PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT + 32, smem));
+      int64_t want = std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, per_sm) * ctx->num_sms,
+                                                            n_pad / TR));
+      int64_t rpc = (n_pad + want - 1) / want;
+      rpc = ((rpc + TR - 1) / TR) * TR;
+      const int nblk = (int)((n_pad + rpc - 1) / rpc);
+      ensure_partial(ctx, sizeof(double) * (size_t)nblk * E);
+      kern<<<nblk, NT + 32, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, TRG, STG,
+                                        ctx->d_partial, ctx->d_flag);
+      check_launch("k_gram_bulk");
+      k_gram_reduce_launch(E, nblk, ctx->d_partial, H, st);
+      check_launch("k_gram_reduce");
     };
-    if (npt == 1) launch(k_gram_bulk<VT, S, EX, Q, 1, NT>);
+    // with Q = 4 there are at most 256 quads (P <= 1024): one per thread
+    if constexpr (Q == 4) launch(k_gram_bulk<VT, S, EX, Q, 1, NT>);
+    else if (npt == 1) launch(k_gram_bulk<VT, S, EX, Q, 1, NT>);
     else if (npt == 2) launch(k_gram_bulk<VT, S, EX, Q, 2, NT>);
     else launch(k_gram_bulk<VT, S, EX, Q, 4, NT>);
   });
   if (!ok) return false;
-  check_launch("k_gram_bulk");
-  k_gram_reduce_launch(E, nblk, ctx->d_partial, H, st);
-  check_launch("k_gram_reduce");
   ctx->launches += 2;
   return true;
 }
