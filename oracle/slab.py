@@ -181,6 +181,77 @@ def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
                "history": hist, "converged": bool(np.all(rn <= thr))}
 
 
+def slab_solve_global(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, precond="jacobi",
+                      restart=30, max_outer=200, maxit=100000, Y0=None):
+    """The slab without the splitting (an extension beyond the paper): global
+    GMRES(restart) (Jbilou, Messaoudi, Sadok 1999) on the coupled operator
+    A(V) = M V A1^T + K V A2^T of Eq. general-system-time-steps, in the
+    Frobenius inner product <X, Y> = trace(X^T Y), right-preconditioned column
+    by column with the preconditioner of J = alpha M + beta K. Each cycle
+    solves A(V) = R(Y) from V = 0 and sets Y <- Y - P(V); a cycle stops when
+    its least-squares residual is below tol * min_k ||F_k|| (every column then
+    meets its own tolerance) or after `restart` steps; the slab stops on the
+    per-column test of slab_solve. Orthogonalisation: two classical
+    Gram-Schmidt passes. Returns (Y, info)."""
+    n, s = K.shape[0], A1.shape[0]
+    alpha, beta, _, _ = _split(A1, A2)
+    J = sp.csr_matrix(sp.diags(alpha * Mdiag) + beta * K)
+    J.sort_indices()
+    Pinv = krylov.make_preconditioner(J, precond)
+    F = rhs_F(A2, B, B0, (n, s))
+    Fn = np.linalg.norm(F, axis=0)
+    thr = np.where(Fn > 0.0, tol * Fn, tol)
+    target = thr.min()
+    Y = np.zeros((n, s)) if Y0 is None else np.array(Y0, dtype=np.float64)
+
+    def A(V):
+        return coupled_residual(K, Mdiag, A1, A2, V)
+
+    def frob(X, Z):
+        return float(np.sum(X * Z))
+
+    hist, steps, cycles = [], 0, 0
+    for it in range(max_outer + 1):
+        R = coupled_residual(K, Mdiag, A1, A2, Y, B, B0)
+        rn = np.linalg.norm(R, axis=0)
+        hist.append(rn / np.where(Fn > 0.0, Fn, 1.0))
+        if np.all(rn <= thr) or it == max_outer or steps >= maxit:
+            break
+        cycles += 1
+        beta0 = np.sqrt(frob(R, R))
+        V = [R / beta0]
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = beta0
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        k = 0
+        for j in range(restart):
+            W = A(Pinv(V[j]))
+            for _ in range(2):                      # CGS2 in <., .>_F
+                h = np.array([frob(V[i], W) for i in range(j + 1)])
+                W = W - sum(h[i] * V[i] for i in range(j + 1))
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.sqrt(frob(W, W))
+            V.append(W / H[j + 1, j] if H[j + 1, j] > 0.0 else np.zeros_like(W))
+            for i in range(j):                      # earlier Givens rotations
+                a, b = H[i, j], H[i + 1, j]
+                H[i, j], H[i + 1, j] = cs[i] * a + sn[i] * b, -sn[i] * a + cs[i] * b
+            r = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = (H[j, j] / r, H[j + 1, j] / r) if r > 0.0 else (1.0, 0.0)
+            H[j, j], H[j + 1, j] = r, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            steps += 1
+            k = j + 1
+            if abs(g[j + 1]) <= target or steps >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        Z = sum(y[i] * V[i] for i in range(k))
+        Y = Y - Pinv(Z)
+    return Y, {"outer": len(hist) - 1, "inner": steps, "cycles": cycles, "relres": hist[-1],
+               "history": hist, "converged": bool(np.all(rn <= thr))}
+
+
 def _split(A1, A2):
     from .coupling import splitting
     return splitting(A1, A2)

@@ -226,3 +226,58 @@ def test_sequential_stepping_iterative_stage_solves_equal_lu():
         it = slab.sequential_dirk_linear(K, np.ones(n), A, 1e-3, y0, B, rtol=1e-15)
         rel = np.linalg.norm(it - lu, axis=0) / np.linalg.norm(lu, axis=0)
         assert np.all(rel < 1e-12), rel
+
+
+def _small_slab(s=4, dims=(9, 8, 1), seed=3):
+    import synth
+    n = int(np.prod(dims))
+    D = np.exp(synth.normal(seed, n)).reshape(dims[::-1])
+    K = fv.convdiff_matrix(dims, D, (1.0, 0.5, 0.0))
+    A, _, _ = coupling.implicit_euler()
+    A1, A2, _ = coupling.multistep_matrices(A, s, 1e-3)
+    B = synth.uniform(seed + 1, n * s).reshape(n, s)
+    return K, n, A, A1, A2, B
+
+
+@pytest.mark.parametrize("precond", ["none", "jacobi", "ilu0"])
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_global_gmres_cycle_is_the_minimum_residual_over_its_krylov_space(precond, k):
+    """One cycle of k steps of global GMRES from Y = 0: the residual's
+    Frobenius norm equals min over Z in span{R, A P R, ..., (A P)^(k-1) R} of
+    ||R - A P Z||_F, computed here by a dense least squares on the vec'd
+    Krylov matrices (the defining property of GMRES in the Frobenius inner
+    product, independent of how the iteration gets there)."""
+    K, n, A, A1, A2, B = _small_slab()
+    Y, info = slab.slab_solve_global(K, np.ones(n), A1, A2, B, tol=1e-300, precond=precond,
+                                     restart=k, max_outer=1)
+    assert info["cycles"] == 1 and info["inner"] == k
+    R1 = slab.coupled_residual(K, np.ones(n), A1, A2, Y, B)
+    alpha, beta = A1[0, 0], A2[0, 0]
+    J = sp.csr_matrix(sp.identity(n) * alpha + beta * K)
+    P = krylov.make_preconditioner(J, precond)
+    Aop = lambda V: slab.coupled_residual(K, np.ones(n), A1, A2, V)
+    R0 = slab.coupled_residual(K, np.ones(n), A1, A2, np.zeros_like(B), B)
+    # an orthonormal basis of the Krylov space (each new direction A P q of
+    # the last basis vector, orthonormalised by numpy's QR), well conditioned
+    # unlike the power basis
+    Q = slab.vec(R0)[:, None] / np.linalg.norm(R0)
+    while Q.shape[1] < k:
+        v = slab.vec(Aop(P(slab.unvec(Q[:, -1], n, A1.shape[0]))))
+        Q = np.linalg.qr(np.column_stack([Q, v]))[0]
+    Mk = np.column_stack([slab.vec(Aop(P(slab.unvec(q, n, A1.shape[0])))) for q in Q.T])
+    c, *_ = np.linalg.lstsq(Mk, slab.vec(R0), rcond=None)
+    best = np.linalg.norm(slab.vec(R0) - Mk @ c)
+    assert np.linalg.norm(R1) == pytest.approx(best, rel=1e-7, abs=1e-12 * np.linalg.norm(R0))
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "ilu0"])
+def test_global_gmres_slab_equals_sequential_stepping(precond):
+    K, n, A, A1, A2, B = _small_slab(s=5, dims=(7, 6, 5))
+    Y, info = slab.slab_solve_global(K, np.ones(n), A1, A2, B, tol=1e-13, precond=precond,
+                                     restart=10)
+    assert info["converged"]
+    Yseq = slab.sequential_dirk_linear(K, np.ones(n), A, 1e-3, np.zeros(n), B)
+    Yd = slab.solve_all_at_once_dense(K, np.ones(n), A1, A2, B)
+    for ref in (Yseq, Yd):
+        err = np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert np.all(err < 1e-11), err
