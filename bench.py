@@ -75,7 +75,7 @@ def parse(argv=None):
     p.add_argument("--precond", default=None, choices=["ilu0", "jacobi"])
     p.add_argument("--inner-tol", type=float, default=None)
     p.add_argument("--restart", type=int, default=None, help="GMRES restart length (30)")
-    p.add_argument("--solver", default="gmres", choices=["gmres", "cg", "bicgstab"],
+    p.add_argument("--solver", default="gmres", choices=["gmres", "cg", "bicgstab", "global"],
                    help="inner solver (cg: symmetric systems, e.g. the Richards L-scheme; "
                         "bicgstab: the paper's solver for the linear convection-diffusion "
                         "problem)")
@@ -95,6 +95,8 @@ def parse(argv=None):
     a.s = a.s or ds
     a.precond = a.precond or dpc
     a.precision = a.precision or dprec
+    if a.solver == "global":       # global GMRES on the unsplit operator runs in float64
+        a.precision = "fp64"
     # the nonlinear workloads name no restart length: GMRES(30) stagnates on
     # the Richards L-scheme systems (67 restarts per solve at 96^3) and
     # GMRES(64) needs a fifth of the Arnoldi steps there (and 11 % fewer for
@@ -145,9 +147,13 @@ def oracle_sample(args, n, reps=1):
         B = synth.rhs_block(w)
         for _ in range(reps):
             t = time.perf_counter()
-            slab.slab_solve(K, np.ones(w.n), A1, A2, B, None, tol=w.tol,
-                            inner_tol=1e-2 if s > 1 else 1e-10, precond=args.precond,
-                            restart=args.restart, solver=args.solver)
+            if args.solver == "global":
+                slab.slab_solve_global(K, np.ones(w.n), A1, A2, B, None, tol=w.tol,
+                                       precond=args.precond, restart=args.restart)
+            else:
+                slab.slab_solve(K, np.ones(w.n), A1, A2, B, None, tol=w.tol,
+                                inner_tol=1e-2 if s > 1 else 1e-10, precond=args.precond,
+                                restart=args.restart, solver=args.solver)
             times.append(time.perf_counter() - t)
         return {"n": w.n, "steps": s, "times": times}
     if args.workload == "diffreact":
@@ -312,12 +318,13 @@ def measured_peaks():
 
 def solver_label(args):
     return {"gmres": f"block GMRES({args.restart})", "cg": "block CG",
-            "bicgstab": "block BiCGStab"}[args.solver]
+            "bicgstab": "block BiCGStab",
+            "global": f"global GMRES({args.restart}) on the unsplit operator"}[args.solver]
 
 
 def solver_code(P, name):
     return {"gmres": P.PINT_SOLVER_GMRES, "cg": P.PINT_SOLVER_CG,
-            "bicgstab": P.PINT_SOLVER_BICGSTAB}[name]
+            "bicgstab": P.PINT_SOLVER_BICGSTAB, "global": P.PINT_SOLVER_GLOBAL}[name]
 
 
 # Files whose content fixes a kernel family's device code and launch shape:
@@ -707,7 +714,7 @@ def main():
     }
     if linear(args):
         out["spmm_full_width"] = spmm_full_width(P, ctx, case, args.precision, hbm_peak)
-    if not args.no_sweep and args.workload == "convdiff3d":
+    if not args.no_sweep and args.workload == "convdiff3d" and args.solver != "global":
         out["sweep"] = sweep(P, ctx, args, case.w, fp64_peak)
         out["sweep_summary"] = sweep_summary(out["sweep"])
     print(json.dumps(out), flush=True)

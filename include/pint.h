@@ -70,7 +70,8 @@ enum {
   PINT_BF16 = 2    /* as PINT_FP32 but the SpMM matrix values are bfloat16    */
 };
 
-enum { PINT_SOLVER_GMRES = 0, PINT_SOLVER_CG = 1, PINT_SOLVER_BICGSTAB = 2 };
+enum { PINT_SOLVER_GMRES = 0, PINT_SOLVER_CG = 1, PINT_SOLVER_BICGSTAB = 2,
+       PINT_SOLVER_GLOBAL = 3 };
 
 typedef struct pint_ctx_s* pint_ctx;
 typedef struct pint_op_s* pint_op;
@@ -106,7 +107,14 @@ typedef struct {
                         restart >= 8; a singular s x s system Rt^T V returns
                         PINT_ERR_BREAKDOWN). max_inner counts its iterations
                         (two operator and preconditioner applications each).
-                        Other values: PINT_ERR_INVALID                       */
+                        PINT_SOLVER_GLOBAL (pint_solve_block only, float64):
+                        no splitting; global GMRES(restart) on the coupled
+                        operator V -> M V A1^T + K V A2^T itself in the
+                        Frobenius inner product, right-preconditioned column
+                        by column with precond of J (the fixed point of
+                        Eq. matrix-fixed-point-equation is not used; each
+                        restart corrects Y from its true residual, inner_tol
+                        is not used). Other values: PINT_ERR_INVALID         */
   int reserved[2];
 } pint_opts;
 

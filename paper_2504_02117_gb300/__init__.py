@@ -25,7 +25,7 @@ PINT_MAX_S = 16
 PINT_MEM_HOST, PINT_MEM_DEVICE = 0, 1
 PINT_PC_NONE, PINT_PC_JACOBI, PINT_PC_ILU0 = 0, 1, 2
 PINT_FP64, PINT_FP32, PINT_BF16 = 0, 1, 2
-PINT_SOLVER_GMRES, PINT_SOLVER_CG, PINT_SOLVER_BICGSTAB = 0, 1, 2
+PINT_SOLVER_GMRES, PINT_SOLVER_CG, PINT_SOLVER_BICGSTAB, PINT_SOLVER_GLOBAL = 0, 1, 2, 3
 PINT_PROBLEM_DIFFREACT, PINT_PROBLEM_RICHARDS = 1, 2
 KERNEL_FAMILIES = ["coupled", "spmm", "gram", "update", "cholqr", "hess", "ilu", "norm", "vec",
                    "nl"]

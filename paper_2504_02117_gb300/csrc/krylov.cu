@@ -1600,6 +1600,262 @@ static double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+// ------------------------------------------- global GMRES (unsplit operator)
+// Frobenius products from the block Gram matrix G ((nb s) x s): the trace of
+// each s x s block, h[b] = tr(V_b^T W) = <V_b, W>_F.
+__global__ void k_block_traces(int nb, int s, const double* __restrict__ G,
+                               double* __restrict__ h) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double v = 0.0;
+  for (int i = 0; i < s; ++i) v += G[(size_t)(b * s + i) * s + i];
+  h[b] = v;
+}
+
+// Hm = block column of nb scaled identities: Hm[(b s + i) s + k] = h[b] (i == k)
+__global__ void k_block_scalar(int nb, int s, const double* __restrict__ h,
+                               double* __restrict__ Hm) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nb * s * s) return;
+  const int row = e / s, k = e - row * s;
+  const int b = row / s, i = row - b * s;
+  Hm[e] = (i == k) ? h[b] : 0.0;
+}
+
+// out[0] = sqrt(sum_k c[k]^2) (Frobenius norm from the column norms)
+__global__ void k_frob(int s, const double* __restrict__ c, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double v = 0.0;
+  for (int k = 0; k < s; ++k) v += c[k] * c[k];
+  out[0] = sqrt(v);
+}
+
+// X *= 1 / nrm[0] (zero when nrm is 0)
+__global__ void k_scale_by(int64_t ne, double* __restrict__ X, const double* __restrict__ nrm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const double d = nrm[0];
+  X[i] = d > 0.0 ? X[i] * (1.0 / d) : 0.0;
+}
+
+// Y -= V (float64, n x s)
+__global__ void k_sub(int64_t ne, const double* __restrict__ V, double* __restrict__ Y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ne) Y[i] -= V[i];
+}
+
+// Z = D^-1 X (float64 rows scaled by the inverse diagonal of J)
+__global__ void k_rowscale64(int64_t n, int s, const double* __restrict__ X,
+                             const double* __restrict__ dinv, double* __restrict__ Z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n * s) Z[i] = X[i] * dinv[i / s];
+}
+
+// Slab solve by global GMRES(m) (Jbilou, Messaoudi and Sadok 1999) on the
+// unsplit operator A(V) = M V A1^T + K V A2^T of Eq. general-system-time-steps,
+// right-preconditioned column by column with the preconditioner of
+// J = alpha M + beta K (P = identity, Jacobi or ILU(0)), float64. Each cycle
+// solves A(V) = R(Y) from V = 0 in the Frobenius inner product
+// <X, Y>_F = tr(X^T Y) and applies Y <- Y - P(V): the same defect correction
+// and per-column stopping test as the split method, with the s x s coupling
+// inside the Krylov space instead of in an outer fixed point. Per Arnoldi
+// step: W = A(P(V_j)); two classical Gram-Schmidt passes of Frobenius
+// products (block Gram products and their block traces, block updates with
+// scaled identities); V_{j+1} = W / ||W||_F; the scalar Hessenberg column
+// through the block kernels at width 1. A cycle ends when the least-squares
+// residual estimate is below tol * min_k ||F_k|| (every column then meets its
+// own tolerance) or after m steps.
+static int solve_global_impl(pint_op op, const double* B, const double* B0, double* Y,
+                             const pint_opts* o, pint_stats* stats, cudaStream_t st) {
+  pint_ctx ctx = op->ctx;
+  const double t0 = now_ms();
+  const long l0 = ctx->launches;
+  PINT_REQUIRE(o->precision == PINT_FP64, PINT_ERR_INVALID,
+               "global GMRES runs in float64 (precision PINT_FP64)");
+  const int64_t n = op->n;
+  const int s = op->s, m = o->restart;
+  const bool ilu = o->precond == PINT_PC_ILU0, jac = o->precond == PINT_PC_JACOBI;
+  if (!op->j_valid) build_inner(op, st);
+  double setup_ms = 0.0;
+  if (ilu) {
+    const double ts = now_ms();
+    ilu_setup(op, st);
+    setup_ms = now_ms() - ts;
+  }
+  KrylovWork* w = ensure_work(op, PINT_FP64, m);
+  const int64_t bs = w->bs, np = w->n_pad, ns = n * s;
+  auto Vb = [&](int b) { return (double*)w->V + (size_t)b * bs; };
+  if (s < w->s && np > n)          // narrower than the allocation: clear the padded rows
+    for (int b = 0; b <= m; ++b)
+      PINT_CUDA(cudaMemsetAsync(Vb(b) + ns, 0, 8 * (size_t)(np - n) * s, st));
+  // small state of this call: Frobenius products of the two passes, the
+  // scaled-identity block column, column norms, the norm ||W||_F
+  const size_t nsm = 2 * (size_t)(m + 1) + (size_t)(m + 1) * s * s + kMaxS + 1;
+  double* sm = dalloc_n<double>(ctx, nsm);
+  struct Free {
+    pint_ctx c;
+    double* p;
+    size_t b;
+    ~Free() { dfree(c, p, b); }
+  } fr{ctx, sm, sizeof(double) * nsm};
+  double* h1 = sm;
+  double* h2 = h1 + (m + 1);
+  double* Hm = h2 + (m + 1);
+  double* cn = Hm + (size_t)(m + 1) * s * s;
+  const int ldh = m + 1;
+  smem_attr(k_hess_step, 8 * (size_t)(m + 1));
+  smem_attr(k_hess_old, 8 * ((size_t)(m + 1) + (size_t)m * kSmallLd));
+  smem_attr(k_backsolve, 8 * (size_t)m);
+  PINT_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+  auto precond = [&](const double* X, double* Z) {
+    if (ilu) {
+      ilu_apply(op, PINT_FP64, X, Z, st);
+    } else if (jac) {
+      k_rowscale64<<<grid_for(ns, 256), 256, 0, st>>>(n, s, X, op->Jinvdiag, Z);
+      check_launch("k_rowscale64");
+      ctx->launches += 1;
+    } else {
+      PINT_CUDA(cudaMemcpyAsync(Z, X, 8 * ns, cudaMemcpyDeviceToDevice, st));
+    }
+  };
+  auto block_scalar = [&](int nb, const double* h) {
+    k_block_scalar<<<grid_for((int64_t)nb * s * s, 256), 256, 0, st>>>(nb, s, h, Hm);
+    check_launch("k_block_scalar");
+    ctx->launches += 1;
+  };
+  // ||F_k|| from the residual of Y = 0
+  double* Rf = w->R64;
+  double* zero = (double*)w->Zt;
+  PINT_CUDA(cudaMemsetAsync(zero, 0, 8 * ns, st));
+  launch_coupled(op, zero, B, B0, Rf, st);
+  launch_colnorm(ctx, PINT_FP64, n, s, Rf, w->fnorm, st);
+  double fn[kMaxS], rn[kMaxS];
+  PINT_CUDA(cudaMemcpyAsync(ctx->h_small, w->fnorm, 8 * s, cudaMemcpyDeviceToHost, st));
+  PINT_CUDA(cudaStreamSynchronize(st));
+  double fmin = 0.0;
+  for (int k = 0; k < s; ++k) {
+    fn[k] = ctx->h_small[k];
+    const double thr = fn[k] > 0.0 ? o->tol * fn[k] : o->tol;
+    fmin = k == 0 ? thr : std::min(fmin, thr);
+  }
+  PINT_CUDA(cudaMemcpyAsync(w->target, &fmin, 8, cudaMemcpyHostToDevice, st));
+  int status = PINT_ERR_NOT_CONVERGED, outer = 0, inner = 0, cycles = 0;
+  for (outer = 0; outer <= o->max_outer; ++outer) {
+    launch_coupled(op, Y, B, B0, w->R64, st);
+    launch_colnorm(ctx, PINT_FP64, n, s, w->R64, w->rnorm, st);
+    PINT_CUDA(cudaMemcpyAsync(ctx->h_small, w->rnorm, 8 * s, cudaMemcpyDeviceToHost, st));
+    PINT_CUDA(cudaStreamSynchronize(st));
+    bool done = true, bad = false;
+    for (int k = 0; k < s; ++k) {
+      rn[k] = ctx->h_small[k];
+      if (!std::isfinite(rn[k])) bad = true;
+      if (!(rn[k] <= (fn[k] > 0.0 ? o->tol * fn[k] : o->tol))) done = false;
+    }
+    if (stats)
+      for (int k = 0; k < s; ++k) stats->col_relres[k] = fn[k] > 0.0 ? rn[k] / fn[k] : rn[k];
+    if (bad) {
+      status = PINT_ERR_BREAKDOWN;
+      break;
+    }
+    if (done) {
+      status = PINT_OK;
+      break;
+    }
+    if (outer == o->max_outer || inner >= o->max_inner) break;
+    cycles += 1;
+    // V_0 = R / ||R||_F, right-hand side of the least squares beta e_1
+    {
+      ProfScope ps(ctx, PF_VEC, 16.0 * ns, 1.0 * ns, st);
+      k_frob<<<1, 32, 0, st>>>(s, w->rnorm, w->S);
+      PINT_CUDA(cudaMemcpyAsync(Vb(0), w->R64, 8 * ns, cudaMemcpyDeviceToDevice, st));
+      k_scale_by<<<grid_for(ns, 256), 256, 0, st>>>(ns, Vb(0), w->S);
+      k_gr_init<<<8, 256, 0, st>>>(ldh, 1, w->S, w->Gr);
+      check_launch("global GMRES start");
+      ctx->launches += 3;
+    }
+    int j = 0;
+    bool conv = false;
+    for (j = 0; j < m; ++j) {
+      // W = A(P(V_j))
+      if (ilu || jac) {
+        precond(Vb(j), (double*)w->Zt);
+        launch_coupled(op, (double*)w->Zt, nullptr, nullptr, Vb(j + 1), st);
+      } else {
+        launch_coupled(op, Vb(j), nullptr, nullptr, Vb(j + 1), st);
+      }
+      // two classical Gram-Schmidt passes in the Frobenius inner product
+      for (int pass = 0; pass < 2; ++pass) {
+        double* hp = pass == 0 ? h1 : h2;
+        launch_gram(ctx, PINT_FP64, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg1, st, np);
+        k_block_traces<<<1, 64, 0, st>>>(j + 1, s, w->Hg1, hp);
+        check_launch("k_block_traces");
+        ctx->launches += 1;
+        block_scalar(j + 1, hp);
+        launch_update(ctx, PINT_FP64, n, s, j + 1, w->V, bs, Hm, Vb(j + 1), 0, st);
+      }
+      // V_{j+1} = W / ||W||_F, then the Hessenberg column (h1 + h2; ||W||_F)
+      launch_colnorm(ctx, PINT_FP64, n, s, Vb(j + 1), cn, st);
+      {
+        ProfScope ps(ctx, PF_HESS, 0.0, 4.0 * (j + 2), st);
+        k_frob<<<1, 32, 0, st>>>(s, cn, w->Rn);
+        k_scale_by<<<grid_for(ns, 256), 256, 0, st>>>(ns, Vb(j + 1), w->Rn);
+        k_hess_old<<<1, 32, 8 * ((size_t)(j + 2) + (size_t)j * kSmallLd), st>>>(
+            j, 1, ldh, h1, h2, w->Rn, w->Hb, w->refl);
+        k_hess_step<<<1, 512, 8 * (size_t)(j + 2), st>>>(j, 1, ldh, w->Hb, w->refl, w->Gr,
+                                                         w->target, w->est, w->flag);
+        check_launch("global GMRES Hessenberg");
+        ctx->launches += 4;
+      }
+      PINT_CUDA(cudaMemcpyAsync(ctx->h_flag, w->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      PINT_CUDA(cudaMemcpyAsync(ctx->h_flag + 2, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                                st));
+      PINT_CUDA(cudaStreamSynchronize(st));
+      inner += 1;
+      PINT_REQUIRE(ctx->h_flag[2] == 0, PINT_ERR_TIMEOUT,
+                   "bulk-copy wait in the Gram kernel exceeded its time budget");
+      if (ilu) ilu_check(op);
+      PINT_REQUIRE(ctx->h_flag[1] == 0, PINT_ERR_BREAKDOWN,
+                   "non-finite residual estimate in global GMRES");
+      conv = ctx->h_flag[0] != 0;
+      if (conv || inner >= o->max_inner) {
+        j += 1;
+        break;
+      }
+    }
+    // correction V = P(sum_b y_b V_b), Y <- Y - V
+    const int kd = std::min(j, m);
+    {
+      ProfScope ps(ctx, PF_HESS, 0.0, 1.0 * kd * kd, st);
+      k_backsolve<<<1, 512, 8 * (size_t)kd, st>>>(kd, 1, ldh, w->Hb, w->Gr, w->Yls);
+      check_launch("k_backsolve");
+      ctx->launches += 1;
+    }
+    block_scalar(kd, w->Yls);
+    launch_update(ctx, PINT_FP64, n, s, kd, w->V, bs, Hm, (double*)w->Zt, 1, st);
+    double* corr = Vb(kd);                       // free after the cycle
+    precond((const double*)w->Zt, corr);
+    {
+      ProfScope ps(ctx, PF_VEC, 24.0 * ns, 1.0 * ns, st);
+      k_sub<<<grid_for(ns, 256), 256, 0, st>>>(ns, corr, Y);
+      check_launch("k_sub");
+      ctx->launches += 1;
+    }
+  }
+  PINT_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->status = status;
+    stats->outer_its = outer;
+    stats->inner_its = inner;
+    stats->restarts = cycles;
+    stats->deflations = 0;
+    stats->setup_ms = setup_ms;
+    stats->solve_ms = now_ms() - t0;
+    stats->kernel_launches = (int)(ctx->launches - l0);
+  }
+  if (status == PINT_ERR_BREAKDOWN) throw Error{PINT_ERR_BREAKDOWN, "non-finite outer residual"};
+  return status;
+}
+
 int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
                      const pint_opts* o, pint_stats* stats, cudaStream_t st) {
   pint_ctx ctx = op->ctx;
@@ -1617,8 +1873,9 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
                "precision");
   PINT_REQUIRE(o->precond >= PINT_PC_NONE && o->precond <= PINT_PC_ILU0, PINT_ERR_INVALID,
                "precond");
-  PINT_REQUIRE(o->solver >= PINT_SOLVER_GMRES && o->solver <= PINT_SOLVER_BICGSTAB,
+  PINT_REQUIRE(o->solver >= PINT_SOLVER_GMRES && o->solver <= PINT_SOLVER_GLOBAL,
                PINT_ERR_INVALID, "solver");
+  if (o->solver == PINT_SOLVER_GLOBAL) return solve_global_impl(op, B, B0, Y, o, stats, st);
   const int64_t n = op->n;
   const int s = op->s;
   if (!op->j_valid) build_inner(op, st);

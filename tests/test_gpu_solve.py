@@ -334,3 +334,61 @@ def test_solver_option_is_validated(P, ctx):
         assert ei.value.code == P.PINT_ERR_INVALID
     finally:
         P.pint_operator_destroy(op)
+
+
+@pytest.mark.parametrize("pc", ["none", "jacobi", "ilu0"])
+@pytest.mark.parametrize("s", [4, 8])
+def test_slab_global_gmres_equals_sequential_stepping(P, ctx, pc, s):
+    """Global GMRES on the unsplit operator (pint_opts.solver =
+    PINT_SOLVER_GLOBAL): every column equals sequential implicit Euler to
+    1e-10 (FP64, tol 1e-13), and the Arnoldi steps equal the oracle's global
+    GMRES on the same problem (up to one step of rounding)."""
+    import torch
+    dims = (16, 16, 16)
+    op, K, n, A, A1, A2, B = _setup(P, ctx, dims, s, 1e-3, seed=7)
+    try:
+        o = P.pint_opts_default()
+        o.tol = 1e-13
+        o.precision = P.PINT_FP64
+        o.solver = P.PINT_SOLVER_GLOBAL
+        o.precond = {"none": P.PINT_PC_NONE, "jacobi": P.PINT_PC_JACOBI, "ilu0": P.PINT_PC_ILU0}[pc]
+        Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
+        st = P.pint_solve_block(ctx, op, _dev(B), None, Y, o, raise_on_nonconvergence=True)
+        Yref = slab.sequential_dirk_linear(K, np.ones(n), A, 1e-3, np.zeros(n), B)
+        err = _colerr(Y.cpu().numpy(), Yref)
+        assert np.all(err < 1e-10), err
+        _, info = slab.slab_solve_global(K, np.ones(n), A1, A2, B, tol=1e-13, precond=pc,
+                                         restart=30)
+        assert abs(st.inner_its - info["inner"]) <= 1 + info["cycles"], (st.inner_its, info)
+    finally:
+        P.pint_operator_destroy(op)
+
+
+def test_slab_global_gmres_tiny_grid_with_b0_against_dense(P, ctx):
+    import torch
+    dims = (4, 3, 2)
+    n, s = 24, 3
+    D = np.exp(synth.normal(21, n)).reshape(dims[::-1])
+    K = fv.convdiff_matrix(dims, D, (1.0, 0.5, 0.25))
+    A, _, _ = coupling.theta_method(0.5)
+    A1, A2, e = coupling.multistep_matrices(A, s, 1e-2, eliminate_first=True)
+    B = synth.uniform(22, n * s).reshape(n, s)
+    B0 = synth.uniform(23, n * s).reshape(n, s)
+    op = P.pint_fv_convdiff(ctx, *dims, D.ravel(), (1.0, 0.5, 0.25))
+    try:
+        P.pint_set_coupling(ctx, op, A1, A2)
+        o = P.pint_opts_default()
+        o.tol = 1e-13
+        o.precision = P.PINT_FP64
+        o.solver = P.PINT_SOLVER_GLOBAL
+        o.precond = P.PINT_PC_ILU0
+        Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
+        P.pint_solve_block(ctx, op, _dev(B), _dev(B0), Y, o, raise_on_nonconvergence=True)
+        Yd = slab.solve_all_at_once_dense(K, np.ones(n), A1, A2, B, B0)
+        assert np.all(_colerr(Y.cpu().numpy(), Yd) < 1e-10)
+        o.precision = P.PINT_FP32
+        with pytest.raises(P.PintError) as ei:
+            P.pint_solve_block(ctx, op, _dev(B), _dev(B0), Y, o)
+        assert ei.value.code == P.PINT_ERR_INVALID
+    finally:
+        P.pint_operator_destroy(op)
