@@ -670,11 +670,13 @@ def main():
         return
 
     # ---------------------------------------- the same workload in pure FP64
-    fp64 = bf16 = None
+    fp64 = bf16 = glob = None
     if args.precision != "fp64" and not args.no_fp64:
         fp64 = precision_variant(P, case, args, stream, "fp64")
         if args.precision == "fp32":
             bf16 = precision_variant(P, case, args, stream, "bf16")
+    if linear(args) and args.solver == "gmres" and not args.no_fp64:
+        glob = solver_variant(P, case, args, stream, "global")
 
     hbm_peak, peak_kind = measured_peaks()
     total_prof = sum(f["ms"] for f in fams.values()) or 1.0
@@ -708,7 +710,7 @@ def main():
                        "restarts": stats[-1]["restarts"]},
         "converged": converged, "max_col_relres": max(max(st["col_relres"]) for st in stats),
         "setup": {"first_step_s": setup_s, "precond_setup_ms": st0.setup_ms},
-        "fp64": fp64, "bf16": bf16,
+        "fp64": fp64, "bf16": bf16, "global_fp64": glob,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(), "impl": "pint",
     }
@@ -722,6 +724,38 @@ def main():
     P.pint_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def solver_variant(P, case, args, stream, solver):
+    """Time the same slab with another solver (one warm-up, then as many timed
+    steps as the headline): "global" is global GMRES on the unsplit operator,
+    float64."""
+    import torch
+    saved = (case.o.solver, case.o.precision)
+    case.o.solver = solver_code(P, solver)
+    if solver == "global":
+        case.o.precision = P.PINT_FP64
+    try:
+        case.step()
+        k = max(1, args.steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sts = [case.step().as_dict(case.s) for _ in range(k)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        return {"value": case.time_steps * case.n / (ms / 1e3), "unit": UNIT,
+                "ms_per_step": ms, "steps": k, "solver": solver_label(
+                    argparse.Namespace(**dict(vars(args), solver=solver))),
+                "outer": sts[-1]["outer_its"], "inner": sts[-1]["inner_its"],
+                "converged": all(x["status"] == 0 for x in sts),
+                "max_col_relres": max(max(x["col_relres"]) for x in sts)}
+    except Exception as e:              # report, do not hide
+        return {"value": None, "error": str(e)[:300]}
+    finally:
+        case.o.solver, case.o.precision = saved
 
 
 def spmm_full_width(P, ctx, case, prec, hbm_peak, reps=20):

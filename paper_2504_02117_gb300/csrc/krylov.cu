@@ -1601,27 +1601,6 @@ static double now_ms() {
 }
 
 // ------------------------------------------- global GMRES (unsplit operator)
-// Frobenius products from the block Gram matrix G ((nb s) x s): the trace of
-// each s x s block, h[b] = tr(V_b^T W) = <V_b, W>_F.
-__global__ void k_block_traces(int nb, int s, const double* __restrict__ G,
-                               double* __restrict__ h) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
-  double v = 0.0;
-  for (int i = 0; i < s; ++i) v += G[(size_t)(b * s + i) * s + i];
-  h[b] = v;
-}
-
-// Hm = block column of nb scaled identities: Hm[(b s + i) s + k] = h[b] (i == k)
-__global__ void k_block_scalar(int nb, int s, const double* __restrict__ h,
-                               double* __restrict__ Hm) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nb * s * s) return;
-  const int row = e / s, k = e - row * s;
-  const int b = row / s, i = row - b * s;
-  Hm[e] = (i == k) ? h[b] : 0.0;
-}
-
 // out[0] = sqrt(sum_k c[k]^2) (Frobenius norm from the column norms)
 __global__ void k_frob(int s, const double* __restrict__ c, double* __restrict__ out) {
   if (threadIdx.x != 0) return;
@@ -1636,6 +1615,42 @@ __global__ void k_scale_by(int64_t ne, double* __restrict__ X, const double* __r
   if (i >= ne) return;
   const double d = nrm[0];
   X[i] = d > 0.0 ? X[i] * (1.0 / d) : 0.0;
+}
+
+// Frobenius products h[b] = <V_b, W>_F of nb basis blocks with W, as per-CTA
+// partials partial[cta * nb + b] over the CTA's element range (warp w takes
+// the blocks w, w + 8, ...; the CTA's slice of W is read from L1 by the other
+// warps), summed in a fixed order by k_gram_reduce_w.
+__global__ void __launch_bounds__(256)
+k_frob_dots(int64_t ne, int nb, const double* __restrict__ V, int64_t bstride,
+            const double* __restrict__ W, int64_t per_cta, double* __restrict__ partial) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e0 = (int64_t)blockIdx.x * per_cta;
+  const int64_t e1 = min(ne, e0 + per_cta);
+  for (int b = warp; b < nb; b += 8) {
+    const double* v = V + (int64_t)b * bstride;
+    double acc = 0.0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) acc = fma(__ldg(v + e), __ldg(W + e), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) partial[(int64_t)blockIdx.x * nb + b] = acc;
+  }
+}
+
+// MODE 0: W -= sum_b h[b] V_b ; MODE 1: W = sum_b h[b] V_b (element-wise)
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_scalar_update(int64_t ne, int nb, const double* __restrict__ V, int64_t bstride,
+                const double* __restrict__ h, double* __restrict__ W) {
+  __shared__ double hs[PINT_MAX_RESTART + 1];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hs[b] = h[b];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) acc = fma(hs[b], __ldg(V + (int64_t)b * bstride + e), acc);
+    if (MODE == 0) W[e] -= acc;
+    else W[e] = acc;
+  }
 }
 
 // Y -= V (float64, n x s)
@@ -1660,9 +1675,9 @@ __global__ void k_rowscale64(int64_t n, int s, const double* __restrict__ X,
 // and per-column stopping test as the split method, with the s x s coupling
 // inside the Krylov space instead of in an outer fixed point. Per Arnoldi
 // step: W = A(P(V_j)); two classical Gram-Schmidt passes of Frobenius
-// products (block Gram products and their block traces, block updates with
-// scaled identities); V_{j+1} = W / ||W||_F; the scalar Hessenberg column
-// through the block kernels at width 1. A cycle ends when the least-squares
+// products (k_frob_dots) and element-wise combinations (k_scalar_update);
+// V_{j+1} = W / ||W||_F; the scalar Hessenberg column through the block
+// kernels at width 1. A cycle ends when the least-squares
 // residual estimate is below tol * min_k ||F_k|| (every column then meets its
 // own tolerance) or after m steps.
 static int solve_global_impl(pint_op op, const double* B, const double* B0, double* Y,
@@ -1688,9 +1703,9 @@ static int solve_global_impl(pint_op op, const double* B, const double* B0, doub
   if (s < w->s && np > n)          // narrower than the allocation: clear the padded rows
     for (int b = 0; b <= m; ++b)
       PINT_CUDA(cudaMemsetAsync(Vb(b) + ns, 0, 8 * (size_t)(np - n) * s, st));
-  // small state of this call: Frobenius products of the two passes, the
-  // scaled-identity block column, column norms, the norm ||W||_F
-  const size_t nsm = 2 * (size_t)(m + 1) + (size_t)(m + 1) * s * s + kMaxS + 1;
+  // small state of this call: Frobenius products of the two passes, column
+  // norms
+  const size_t nsm = 2 * (size_t)(m + 1) + kMaxS;
   double* sm = dalloc_n<double>(ctx, nsm);
   struct Free {
     pint_ctx c;
@@ -1700,8 +1715,7 @@ static int solve_global_impl(pint_op op, const double* B, const double* B0, doub
   } fr{ctx, sm, sizeof(double) * nsm};
   double* h1 = sm;
   double* h2 = h1 + (m + 1);
-  double* Hm = h2 + (m + 1);
-  double* cn = Hm + (size_t)(m + 1) * s * s;
+  double* cn = h2 + (m + 1);
   const int ldh = m + 1;
   smem_attr(k_hess_step, 8 * (size_t)(m + 1));
   smem_attr(k_hess_old, 8 * ((size_t)(m + 1) + (size_t)m * kSmallLd));
@@ -1718,9 +1732,26 @@ static int solve_global_impl(pint_op op, const double* B, const double* B0, doub
       PINT_CUDA(cudaMemcpyAsync(Z, X, 8 * ns, cudaMemcpyDeviceToDevice, st));
     }
   };
-  auto block_scalar = [&](int nb, const double* h) {
-    k_block_scalar<<<grid_for((int64_t)nb * s * s, 256), 256, 0, st>>>(nb, s, h, Hm);
-    check_launch("k_block_scalar");
+  // Frobenius products with the first nb basis blocks (PF_GRAM) and the
+  // element-wise combinations (PF_UPDATE); memory-bound, nb FMAs per element
+  const int fblk = (int)std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, (ns + 2047) / 2048));
+  const int64_t fper = (ns + fblk - 1) / fblk;
+  ensure_partial(ctx, sizeof(double) * (size_t)fblk * (m + 1));
+  auto frob_dots = [&](int nb, const double* Wd, double* h) {
+    ProfScope ps(ctx, PF_GRAM, 8.0 * (nb + 1) * ns, 2.0 * nb * ns, st);
+    k_frob_dots<<<fblk, 256, 0, st>>>(ns, nb, Vb(0), bs, Wd, fper, ctx->d_partial);
+    check_launch("k_frob_dots");
+    k_gram_reduce_launch(nb, fblk, ctx->d_partial, h, st);
+    check_launch("k_gram_reduce (Frobenius)");
+    ctx->launches += 2;
+  };
+  auto scalar_update = [&](int nb, const double* h, double* Wd, bool assign) {
+    ProfScope ps(ctx, PF_UPDATE, 8.0 * (nb + (assign ? 1 : 2)) * ns, 2.0 * nb * ns, st);
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(8LL * ctx->num_sms,
+                                                                       (ns + 255) / 256));
+    if (assign) k_scalar_update<1><<<g, 256, 0, st>>>(ns, nb, Vb(0), bs, h, Wd);
+    else k_scalar_update<0><<<g, 256, 0, st>>>(ns, nb, Vb(0), bs, h, Wd);
+    check_launch("k_scalar_update");
     ctx->launches += 1;
   };
   // ||F_k|| from the residual of Y = 0
@@ -1786,12 +1817,8 @@ static int solve_global_impl(pint_op op, const double* B, const double* B0, doub
       // two classical Gram-Schmidt passes in the Frobenius inner product
       for (int pass = 0; pass < 2; ++pass) {
         double* hp = pass == 0 ? h1 : h2;
-        launch_gram(ctx, PINT_FP64, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg1, st, np);
-        k_block_traces<<<1, 64, 0, st>>>(j + 1, s, w->Hg1, hp);
-        check_launch("k_block_traces");
-        ctx->launches += 1;
-        block_scalar(j + 1, hp);
-        launch_update(ctx, PINT_FP64, n, s, j + 1, w->V, bs, Hm, Vb(j + 1), 0, st);
+        frob_dots(j + 1, Vb(j + 1), hp);
+        scalar_update(j + 1, hp, Vb(j + 1), false);
       }
       // V_{j+1} = W / ||W||_F, then the Hessenberg column (h1 + h2; ||W||_F)
       launch_colnorm(ctx, PINT_FP64, n, s, Vb(j + 1), cn, st);
@@ -1830,8 +1857,7 @@ static int solve_global_impl(pint_op op, const double* B, const double* B0, doub
       check_launch("k_backsolve");
       ctx->launches += 1;
     }
-    block_scalar(kd, w->Yls);
-    launch_update(ctx, PINT_FP64, n, s, kd, w->V, bs, Hm, (double*)w->Zt, 1, st);
+    scalar_update(kd, w->Yls, (double*)w->Zt, true);
     double* corr = Vb(kd);                       // free after the cycle
     precond((const double*)w->Zt, corr);
     {
