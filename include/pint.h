@@ -209,6 +209,43 @@ int pint_apply_coupled(pint_op op, const double* Y, const double* B,
 int pint_solve_block(pint_op op, const double* B, const double* B0, double* Y,
                      const pint_opts* opts, pint_stats* stats, void* stream);
 
+/* One slab solve of pint_solve_batch: Y solves M Y A1^T + (K Y - B) A2^T = B0
+ * (Eq. general-system-time-steps) for the operator and coupling of `op`. */
+typedef struct {
+  pint_op op;          /* coupling set; several jobs may share one operator    */
+  const double* B;     /* N x s row-major device, or NULL                      */
+  const double* B0;    /* N x s row-major device, or NULL                      */
+  double* Y;           /* N x s row-major device: in initial guess, out result;
+                          the Y of different jobs must not overlap             */
+} pint_batch_job;
+
+/* Many slab solves (uneven N and s, each with its own operator and coupling)
+ * in ONE persistent kernel launch: thread-block clusters of `cluster_ctas`
+ * CTAs (1..16; 0 = pint_batch_auto_cluster) take jobs from a device queue and
+ * run each whole solve inside the cluster, with no host round trip per
+ * Arnoldi step. The method per job is the one of PINT_SOLVER_GLOBAL in
+ * pint_solve_block (global GMRES(opts->restart) on the unsplit coupled
+ * operator, restarted as defect correction from the true residual, same
+ * stopping test; modified Gram-Schmidt when a job runs on one CTA, two
+ * classical passes on a cluster), float64, right preconditioned by Jacobi of
+ * J = alpha M + beta K or by none: opts->precision must be PINT_FP64 and
+ * opts->precond PINT_PC_JACOBI or PINT_PC_NONE, else PINT_ERR_INVALID.
+ * opts->solver and inner_tol are not used. A job's result does not depend on
+ * the other jobs of the batch (fixed reduction order for a given cluster
+ * size). `stats`: NULL or njobs entries, filled per job (solve_ms is the whole
+ * call). Device memory for (restart + 3) N s doubles per resident cluster is
+ * taken from the context budget for the call. Synchronous. Returns PINT_OK
+ * when every job converged, PINT_ERR_BREAKDOWN if any job met a non-finite
+ * residual, else PINT_ERR_NOT_CONVERGED; per-job status is in stats. */
+int pint_solve_batch(pint_ctx ctx, int njobs, const pint_batch_job* jobs,
+                     const pint_opts* opts, int cluster_ctas, pint_stats* stats,
+                     void* stream);
+
+/* The cluster size pint_solve_batch takes for cluster_ctas = 0: 1 when the
+ * jobs alone occupy every SM, else the largest power of two up to 16 with
+ * njobs * C <= SMs and at least 256 rows per CTA in the smallest job. */
+int pint_batch_auto_cluster(pint_ctx ctx, int njobs, int64_t min_n);
+
 /* shift((Y_1,...,Y_s)) = (Y_2,...,Y_s,Y_s) in place (Sec. 2.2, Eq. shift). */
 int pint_shift(double* Y, int64_t n, int s, void* stream);
 

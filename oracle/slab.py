@@ -182,7 +182,7 @@ def slab_solve(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, inner_tol=1e-2,
 
 
 def slab_solve_global(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, precond="jacobi",
-                      restart=30, max_outer=200, maxit=100000, Y0=None):
+                      restart=30, max_outer=200, maxit=100000, Y0=None, ortho="cgs2"):
     """The slab without the splitting (an extension beyond the paper): global
     GMRES(restart) (Jbilou, Messaoudi, Sadok 1999) on the coupled operator
     A(V) = M V A1^T + K V A2^T of Eq. general-system-time-steps, in the
@@ -191,8 +191,10 @@ def slab_solve_global(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, precond="jac
     solves A(V) = R(Y) from V = 0 and sets Y <- Y - P(V); a cycle stops when
     its least-squares residual is below tol * min_k ||F_k|| (every column then
     meets its own tolerance) or after `restart` steps; the slab stops on the
-    per-column test of slab_solve. Orthogonalisation: two classical
-    Gram-Schmidt passes. Returns (Y, info)."""
+    per-column test of slab_solve. Orthogonalisation in the Frobenius inner
+    product: two classical Gram-Schmidt passes (ortho="cgs2") or modified
+    Gram-Schmidt (ortho="mgs": one basis vector at a time, each product taken
+    with the partly orthogonalised W). Returns (Y, info)."""
     n, s = K.shape[0], A1.shape[0]
     alpha, beta, _, _ = _split(A1, A2)
     J = sp.csr_matrix(sp.diags(alpha * Mdiag) + beta * K)
@@ -227,10 +229,15 @@ def slab_solve_global(K, Mdiag, A1, A2, B=None, B0=None, tol=1e-10, precond="jac
         k = 0
         for j in range(restart):
             W = A(Pinv(V[j]))
-            for _ in range(2):                      # CGS2 in <., .>_F
-                h = np.array([frob(V[i], W) for i in range(j + 1)])
-                W = W - sum(h[i] * V[i] for i in range(j + 1))
-                H[:j + 1, j] += h
+            if ortho == "mgs":
+                for i in range(j + 1):
+                    H[i, j] = frob(V[i], W)
+                    W = W - H[i, j] * V[i]
+            else:
+                for _ in range(2):                  # CGS2 in <., .>_F
+                    h = np.array([frob(V[i], W) for i in range(j + 1)])
+                    W = W - sum(h[i] * V[i] for i in range(j + 1))
+                    H[:j + 1, j] += h
             H[j + 1, j] = np.sqrt(frob(W, W))
             V.append(W / H[j + 1, j] if H[j + 1, j] > 0.0 else np.zeros_like(W))
             for i in range(j):                      # earlier Givens rotations

@@ -47,6 +47,10 @@ class pint_opts(C.Structure):
                 ("precision", C.c_int), ("solver", C.c_int), ("reserved", C.c_int * 2)]
 
 
+class pint_batch_job(C.Structure):
+    _fields_ = [("op", C.c_void_p), ("B", C.c_void_p), ("B0", C.c_void_p), ("Y", C.c_void_p)]
+
+
 class pint_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_its", C.c_int), ("inner_its", C.c_int),
                 ("restarts", C.c_int), ("deflations", C.c_int), ("kernel_launches", C.c_int),
@@ -81,6 +85,9 @@ _SIGS = {
     "pint_coupling_from_dirk": (_i, [_vp, _i, _i, _d, _i, _vp, _vp, _vp, C.POINTER(_i)]),
     "pint_apply_coupled": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pint_solve_block": (_i, [_vp, _vp, _vp, _vp, C.POINTER(pint_opts), C.POINTER(pint_stats), _vp]),
+    "pint_solve_batch": (_i, [_vp, _i, C.POINTER(pint_batch_job), C.POINTER(pint_opts), _i,
+                              C.POINTER(pint_stats), _vp]),
+    "pint_batch_auto_cluster": (_i, [_vp, _i, _i64]),
     "pint_shift": (_i, [_vp, _i64, _i, _vp]),
     "pint_problem_create": (_i, [_vp, C.POINTER(_vp), _i, _i, _i, _i, _vp, _vp, _vp]),
     "pint_problem_destroy": (_i, [_vp]),
@@ -239,6 +246,28 @@ def pint_solve_block(ctx, op, B, B0, Y, opts=None, stream=None, raise_on_nonconv
                               _stream(stream))
     _check(rc, ctx, allow=() if raise_on_nonconvergence else (PINT_ERR_NOT_CONVERGED,))
     return st
+
+
+def pint_solve_batch(ctx, jobs, opts=None, cluster_ctas=0, stream=None,
+                     raise_on_nonconvergence=False):
+    """jobs: sequence of (op, B, B0, Y) (B, B0 may be None). Returns the
+    per-job pint_stats list."""
+    o = opts if opts is not None else pint_opts_default()
+    arr = (pint_batch_job * len(jobs))()
+    for i, (op, B, B0, Y) in enumerate(jobs):
+        arr[i].op = op.value if isinstance(op, C.c_void_p) else op
+        arr[i].B = None if B is None else B.data_ptr()
+        arr[i].B0 = None if B0 is None else B0.data_ptr()
+        arr[i].Y = Y.data_ptr()
+    sts = (pint_stats * len(jobs))()
+    rc = lib.pint_solve_batch(ctx, len(jobs), arr, C.byref(o), int(cluster_ctas), sts,
+                              _stream(stream))
+    _check(rc, ctx, allow=() if raise_on_nonconvergence else (PINT_ERR_NOT_CONVERGED,))
+    return list(sts)
+
+
+def pint_batch_auto_cluster(ctx, njobs, min_n):
+    return lib.pint_batch_auto_cluster(ctx, int(njobs), int(min_n))
 
 
 def pint_shift(Y, n, s, stream=None):

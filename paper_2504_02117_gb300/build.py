@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpint.so")
-SOURCES = ["api.cu", "spmm.cu", "krylov.cu", "ilu.cu", "fv.cu"]
+SOURCES = ["api.cu", "spmm.cu", "krylov.cu", "ilu.cu", "fv.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

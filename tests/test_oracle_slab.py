@@ -239,9 +239,10 @@ def _small_slab(s=4, dims=(9, 8, 1), seed=3):
     return K, n, A, A1, A2, B
 
 
+@pytest.mark.parametrize("ortho", ["cgs2", "mgs"])
 @pytest.mark.parametrize("precond", ["none", "jacobi", "ilu0"])
 @pytest.mark.parametrize("k", [1, 3, 6])
-def test_global_gmres_cycle_is_the_minimum_residual_over_its_krylov_space(precond, k):
+def test_global_gmres_cycle_is_the_minimum_residual_over_its_krylov_space(precond, k, ortho):
     """One cycle of k steps of global GMRES from Y = 0: the residual's
     Frobenius norm equals min over Z in span{R, A P R, ..., (A P)^(k-1) R} of
     ||R - A P Z||_F, computed here by a dense least squares on the vec'd
@@ -249,7 +250,7 @@ def test_global_gmres_cycle_is_the_minimum_residual_over_its_krylov_space(precon
     product, independent of how the iteration gets there)."""
     K, n, A, A1, A2, B = _small_slab()
     Y, info = slab.slab_solve_global(K, np.ones(n), A1, A2, B, tol=1e-300, precond=precond,
-                                     restart=k, max_outer=1)
+                                     restart=k, max_outer=1, ortho=ortho)
     assert info["cycles"] == 1 and info["inner"] == k
     R1 = slab.coupled_residual(K, np.ones(n), A1, A2, Y, B)
     alpha, beta = A1[0, 0], A2[0, 0]
@@ -270,14 +271,47 @@ def test_global_gmres_cycle_is_the_minimum_residual_over_its_krylov_space(precon
     assert np.linalg.norm(R1) == pytest.approx(best, rel=1e-7, abs=1e-12 * np.linalg.norm(R0))
 
 
+@pytest.mark.parametrize("ortho", ["cgs2", "mgs"])
 @pytest.mark.parametrize("precond", ["jacobi", "ilu0"])
-def test_global_gmres_slab_equals_sequential_stepping(precond):
+def test_global_gmres_slab_equals_sequential_stepping(precond, ortho):
     K, n, A, A1, A2, B = _small_slab(s=5, dims=(7, 6, 5))
     Y, info = slab.slab_solve_global(K, np.ones(n), A1, A2, B, tol=1e-13, precond=precond,
-                                     restart=10)
+                                     restart=10, ortho=ortho)
     assert info["converged"]
     Yseq = slab.sequential_dirk_linear(K, np.ones(n), A, 1e-3, np.zeros(n), B)
     Yd = slab.solve_all_at_once_dense(K, np.ones(n), A1, A2, B)
     for ref in (Yseq, Yd):
         err = np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)
         assert np.all(err < 1e-11), err
+
+
+def test_global_gmres_mgs_basis_is_orthonormal_and_satisfies_the_arnoldi_relation():
+    """Modified Gram-Schmidt in the Frobenius inner product: the Krylov basis
+    is orthonormal to rounding level on this well-conditioned slab and the
+    Arnoldi relation A P V_k = V_{k+1} H_k holds; the MGS solver meets tol
+    within one step per restart of the CGS2 one."""
+    K, n, A, A1, A2, B = _small_slab(s=4, dims=(9, 8, 3))
+    alpha, beta = A1[0, 0], A2[0, 0]
+    J = sp.csr_matrix(sp.identity(n) * alpha + beta * K)
+    P = krylov.make_preconditioner(J, "jacobi")
+    Aop = lambda V: slab.coupled_residual(K, np.ones(n), A1, A2, P(V))
+    R0 = slab.coupled_residual(K, np.ones(n), A1, A2, np.zeros_like(B), B)
+    k = 12
+    V = [R0 / np.sqrt(np.sum(R0 * R0))]
+    H = np.zeros((k + 1, k))
+    for j in range(k):                  # the Arnoldi process with MGS, by hand
+        W = Aop(V[j])
+        for i in range(j + 1):
+            H[i, j] = np.sum(V[i] * W)
+            W = W - H[i, j] * V[i]
+        H[j + 1, j] = np.sqrt(np.sum(W * W))
+        V.append(W / H[j + 1, j])
+    G = np.array([[np.sum(a * b) for b in V] for a in V])
+    assert np.max(np.abs(G - np.eye(k + 1))) < 1e-10
+    lhs = np.column_stack([slab.vec(Aop(V[j])) for j in range(k)])
+    rhs = np.column_stack([slab.vec(v) for v in V]) @ H
+    assert np.linalg.norm(lhs - rhs) < 1e-12 * np.linalg.norm(lhs)
+    _, ia = slab.slab_solve_global(K, np.ones(n), A1, A2, B, tol=1e-10, restart=30)
+    Ym, im = slab.slab_solve_global(K, np.ones(n), A1, A2, B, tol=1e-10, restart=30,
+                                    ortho="mgs")
+    assert im["converged"] and abs(im["inner"] - ia["inner"]) <= 1 + ia["cycles"]
