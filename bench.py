@@ -55,6 +55,10 @@ WORKLOADS = {
                  "3-D Richards {n}^3, van Genuchten alpha=1 n=2, K_S=exp(2g) correlated 8 "
                  "cells, implicit Euler tau=1/96 window s=8 pipelined over 8 steps, L-scheme + "
                  "{solver}+{pc}"),
+    "batch": (64, 16, "jacobi", "fp64",
+              "batched persistent solve: {requests} slabs in one launch (captured CUDA graph), "
+              "2-D 32^2-64^2 and 3-D 16^3-32^3 conv.-diffusion, log-normal D, s in 2..16, "
+              "implicit Euler tau=1e-3, {solver}+{pc}, FP64, tol 1e-10"),
     "serve": (128, 16, "ilu0", "fp32",
               "serving: seeded Poisson stream of slab-solve requests (3-D conv.-diffusion, "
               "grids 32^3-{n}^3, s in 2..16, FP32 or FP64 inner solves, {solver}+{pc}, "
@@ -75,19 +79,27 @@ def parse(argv=None):
     p.add_argument("--precond", default=None, choices=["ilu0", "jacobi"])
     p.add_argument("--inner-tol", type=float, default=None)
     p.add_argument("--restart", type=int, default=None, help="GMRES restart length (30)")
-    p.add_argument("--solver", default="gmres", choices=["gmres", "cg", "bicgstab", "global"],
+    p.add_argument("--solver", default="gmres",
+                   choices=["gmres", "cg", "bicgstab", "global", "batch"],
                    help="inner solver (cg: symmetric systems, e.g. the Richards L-scheme; "
                         "bicgstab: the paper's solver for the linear convection-diffusion "
-                        "problem)")
+                        "problem; global: global GMRES on the unsplit operator; batch: the "
+                        "same method in the persistent batched kernel, one cluster per slab)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true",
                    help="skip the pure-FP64 run of the same workload")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the s = 1..16 sweep (one timed solve per s and precision)")
-    p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
+    p.add_argument("--requests", type=int, default=512,
+                   help="serve: requests in the stream; batch: slabs in the launch")
     p.add_argument("--rate", type=float, default=8.0, help="serve: mean arrivals per second")
     p.add_argument("--slots", type=int, default=4, help="serve: concurrent solves")
+    p.add_argument("--no-batch-lane", action="store_true",
+                   help="serve: solve the small float64 requests in the slots as well, "
+                        "not in batched launches")
+    p.add_argument("--batch-max-unknowns", type=int, default=1 << 19,
+                   help="serve: largest N*s a float64 request may have for the batch lane")
     p.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     a = p.parse_args(argv)
     dn, ds, dpc, dprec, _ = WORKLOADS[a.workload]
@@ -95,8 +107,12 @@ def parse(argv=None):
     a.s = a.s or ds
     a.precond = a.precond or dpc
     a.precision = a.precision or dprec
-    if a.solver == "global":       # global GMRES on the unsplit operator runs in float64
+    if a.workload == "batch":
+        a.solver = "batch"
+    if a.solver in ("global", "batch"):   # the unsplit operator's solvers run in float64
         a.precision = "fp64"
+    if a.solver == "batch":               # the batched kernel: Jacobi or none
+        a.precond = "jacobi"
     # the nonlinear workloads name no restart length: GMRES(30) stagnates on
     # the Richards L-scheme systems (67 restarts per solve at 96^3) and
     # GMRES(64) needs a fifth of the Arnoldi steps there (and 11 % fewer for
@@ -106,7 +122,7 @@ def parse(argv=None):
 
 
 def linear(args):
-    return args.workload in ("convdiff3d", "convdiff2d", "serve")
+    return args.workload in ("convdiff3d", "convdiff2d", "serve", "batch")
 
 
 def inner_tol_for(args, s):
@@ -134,6 +150,27 @@ def oracle_sample(args, n, reps=1):
     from oracle import coupling, fv, newton, slab
     s = args.s
     times = []
+    if args.workload == "batch":
+        # the first n slabs of the same seeded mix, solved one after another
+        jobs = synth.batch_jobs(7, n)
+        work = 0
+        sample = []
+        A, _, _ = coupling.implicit_euler()
+        for j in jobs:
+            w = synth.Workload("batch", j["dims"], "convdiff", j["s"], 1e-3, 1e-10, "jacobi",
+                               batch_velocity(j["dims"]), "lognormal_iid", j["seed_coef"],
+                               j["seed_rhs"])
+            K = fv.convdiff_matrix(w.dims, synth.diffusion_field(w), w.velocity)
+            A1, A2, _ = coupling.multistep_matrices(A, j["s"], w.tau)
+            sample.append((K, w.n, A1, A2, synth.rhs_block(w)))
+            work += w.n * j["s"]
+        for _ in range(reps):
+            t = time.perf_counter()
+            for K, nn, A1, A2, B in sample:
+                slab.slab_solve_global(K, np.ones(nn), A1, A2, B, None, tol=1e-10,
+                                       precond="jacobi", restart=args.restart, ortho="mgs")
+            times.append(time.perf_counter() - t)
+        return {"n": work, "steps": 1, "times": times}
     if args.workload in ("convdiff3d", "convdiff2d", "serve"):
         if args.workload == "serve":
             s = 4                     # a mid-size request of the stream
@@ -147,7 +184,7 @@ def oracle_sample(args, n, reps=1):
         B = synth.rhs_block(w)
         for _ in range(reps):
             t = time.perf_counter()
-            if args.solver == "global":
+            if args.solver in ("global", "batch"):
                 slab.slab_solve_global(K, np.ones(w.n), A1, A2, B, None, tol=w.tol,
                                        precond=args.precond, restart=args.restart)
             else:
@@ -189,7 +226,12 @@ def oracle_sample(args, n, reps=1):
 
 def oracle_sample_size(args):
     return {"convdiff3d": 48, "convdiff2d": 64, "diffreact": 160, "richards": 20,
-            "serve": 32}[args.workload]
+            "serve": 32, "batch": 12}[args.workload]
+
+
+def batch_velocity(dims):
+    """Velocity of the batch mix: (1, 0.5) in 2-D, (1, 0.5, 0.25) in 3-D."""
+    return (1.0, 0.5, 0.25) if dims[2] > 1 else (1.0, 0.5, 0.0)
 
 
 def _oracle_cmd(args, n, reps):
@@ -319,12 +361,15 @@ def measured_peaks():
 def solver_label(args):
     return {"gmres": f"block GMRES({args.restart})", "cg": "block CG",
             "bicgstab": "block BiCGStab",
-            "global": f"global GMRES({args.restart}) on the unsplit operator"}[args.solver]
+            "global": f"global GMRES({args.restart}) on the unsplit operator",
+            "batch": f"global GMRES({args.restart}) on the unsplit operator in the batched "
+                     f"persistent kernel"}[args.solver]
 
 
 def solver_code(P, name):
     return {"gmres": P.PINT_SOLVER_GMRES, "cg": P.PINT_SOLVER_CG,
-            "bicgstab": P.PINT_SOLVER_BICGSTAB, "global": P.PINT_SOLVER_GLOBAL}[name]
+            "bicgstab": P.PINT_SOLVER_BICGSTAB, "global": P.PINT_SOLVER_GLOBAL,
+            "batch": P.PINT_SOLVER_GLOBAL}[name]
 
 
 # Files whose content fixes a kernel family's device code and launch shape:
@@ -419,9 +464,14 @@ class LinearCase:
         self.Bd = torch.tensor(self.B, device="cuda", dtype=torch.float64)
         self.Y = torch.zeros(self.n, s, device="cuda", dtype=torch.float64)
         self.nnz = int(P.pint_operator_nnz(self.op))
+        self.plan = None
+        if args.solver == "batch":        # one slab, one cluster, a captured graph
+            self.plan = P.BatchPlan(ctx, [(self.op, self.Bd, None, self.Y)], o)
 
     def step(self):
         self.Y.zero_()
+        if self.plan is not None:
+            return self.plan.run()[0]
         return self.P.pint_solve_block(self.ctx, self.op, self.Bd, None, self.Y, self.o)
 
     def host_buffers(self):
@@ -437,12 +487,105 @@ class LinearCase:
         return st
 
     def describe(self):
-        return {"cells": self.n, "s": self.s, "nnz": self.nnz, "tau": self.w.tau,
-                "tol": self.w.tol, "inner_tol": self.o.inner_tol, "restart": self.o.restart,
-                "solver": self.args.solver}
+        d = {"cells": self.n, "s": self.s, "nnz": self.nnz, "tau": self.w.tau,
+             "tol": self.w.tol, "inner_tol": self.o.inner_tol, "restart": self.o.restart,
+             "solver": self.args.solver}
+        if self.plan is not None:
+            d["launch_shape"] = self.plan.shape()
+        return d
 
     def close(self):
+        if self.plan is not None:
+            self.plan.close()
         self.P.pint_operator_destroy(self.op)
+
+
+class _AggStats:
+    """pint_stats of a batch, summarised like one solve's (worst status and
+    residual, summed steps and operations)."""
+
+    def __init__(self, sts):
+        self.sts = sts
+        self.setup_ms = 0.0
+
+    def as_dict(self, s=None):
+        return {"status": max(x.status for x in self.sts),
+                "outer_its": max(x.outer_its for x in self.sts),
+                "inner_its": sum(x.inner_its for x in self.sts),
+                "restarts": sum(x.restarts for x in self.sts),
+                "col_relres": [max(max(x.col_relres) for x in self.sts)],
+                "flops": sum(x.flops for x in self.sts), "solve_ms": self.sts[0].solve_ms,
+                "max_inner_its": max(x.inner_its for x in self.sts)}
+
+
+class BatchCase:
+    """One step = one batched launch (a replay of the plan's captured graph)
+    solving every slab of the seeded mix from Y = 0; the slabs' B and Y are
+    views of two flat device buffers."""
+
+    def __init__(self, P, ctx, args):
+        import numpy as np
+        import torch
+        import synth
+        self.P, self.ctx, self.args = P, ctx, args
+        self.jobs = synth.batch_jobs(7, args.requests)
+        counts = [j["dims"][0] * j["dims"][1] * j["dims"][2] * j["s"] for j in self.jobs]
+        total = int(sum(counts))
+        self.Bhost = np.empty(total)
+        self.Bflat = torch.empty(total, device="cuda", dtype=torch.float64)
+        self.Yflat = torch.zeros(total, device="cuda", dtype=torch.float64)
+        self.ops, views, off = [], [], 0
+        for j, cnt in zip(self.jobs, counts):
+            w = synth.Workload("batch", j["dims"], "convdiff", j["s"], 1e-3, 1e-10, "jacobi",
+                               batch_velocity(j["dims"]), "lognormal_iid", j["seed_coef"],
+                               j["seed_rhs"])
+            op = P.pint_fv_convdiff(ctx, *w.dims, synth.diffusion_field(w).ravel(), w.velocity)
+            s = j["s"]
+            P.pint_set_coupling(ctx, op, (np.eye(s) - np.eye(s, k=-1)) / w.tau, np.eye(s))
+            self.Bhost[off:off + cnt] = synth.rhs_block(w).ravel()
+            views.append((op, self.Bflat[off:off + cnt].view(w.n, s), None,
+                          self.Yflat[off:off + cnt].view(w.n, s)))
+            self.ops.append(op)
+            off += cnt
+        self.Bflat.copy_(torch.from_numpy(self.Bhost))
+        o = P.pint_opts_default()
+        o.tol = 1e-10
+        o.precond = P.PINT_PC_JACOBI
+        o.precision = P.PINT_FP64
+        o.restart = args.restart
+        self.o = o
+        self.plan = P.BatchPlan(ctx, views, o)
+        self.n, self.time_steps, self.s = total, 1, max(j["s"] for j in self.jobs)
+
+    def step(self):
+        self.Yflat.zero_()
+        return _AggStats(self.plan.run())
+
+    def host_buffers(self):
+        import torch
+        self.Bh = torch.from_numpy(self.Bhost).pin_memory()
+        self.Yh = torch.empty(self.n, dtype=torch.float64).pin_memory()
+        return self.Bh.numel() * 8, self.Yh.numel() * 8
+
+    def e2e_step(self):
+        self.Bflat.copy_(self.Bh, non_blocking=True)
+        st = self.step()
+        self.Yh.copy_(self.Yflat, non_blocking=True)
+        return st
+
+    def describe(self):
+        import collections
+        two = sum(1 for j in self.jobs if j["dims"][2] == 1)
+        return {"slabs": len(self.jobs), "slabs_2d": two, "slabs_3d": len(self.jobs) - two,
+                "dof_time_steps_per_launch": self.n,
+                "s_counts": dict(sorted(collections.Counter(j["s"] for j in self.jobs).items())),
+                "tol": 1e-10, "restart": self.o.restart, "solver": "batch",
+                "launch_shape": self.plan.shape()}
+
+    def close(self):
+        self.plan.close()
+        for op in self.ops:
+            self.P.pint_operator_destroy(op)
 
 
 class PipelineCase:
@@ -555,8 +698,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     desc = WORKLOADS[args.workload][4].format(n=args.n, pc=args.precond,
-                                             solver=solver_label(args))
+                                             solver=solver_label(args), requests=args.requests)
     wl_name = f"{args.workload}_n{args.n}_s{args.s}_{args.precond}"
+    if args.workload == "batch":
+        wl_name = f"batch_{args.requests}slabs_jacobi"
+    elif args.solver == "batch":
+        wl_name += "_batchkernel"
 
     if args.impl == "reference":
         if rank != 0:
@@ -597,7 +744,12 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     ctx = P.pint_create(local)
     fp64_peak = P.pint_fp64_fma_peak(ctx)
-    case = LinearCase(P, ctx, args) if linear(args) else PipelineCase(P, ctx, args)
+    if args.workload == "batch":
+        case = BatchCase(P, ctx, args)
+    elif linear(args):
+        case = LinearCase(P, ctx, args)
+    else:
+        case = PipelineCase(P, ctx, args)
     stream = torch.cuda.current_stream()
 
     # set-up (ILU factorisation happens on the first solve): untimed
@@ -675,8 +827,11 @@ def main():
         fp64 = precision_variant(P, case, args, stream, "fp64")
         if args.precision == "fp32":
             bf16 = precision_variant(P, case, args, stream, "bf16")
+    batchv = None
     if linear(args) and args.solver == "gmres" and not args.no_fp64:
         glob = solver_variant(P, case, args, stream, "global")
+        if args.workload == "convdiff2d":
+            batchv = batch_variant(P, ctx, case, args, stream, fp64_peak)
 
     hbm_peak, peak_kind = measured_peaks()
     total_prof = sum(f["ms"] for f in fams.values()) or 1.0
@@ -693,16 +848,25 @@ def main():
            "l2": "inputs larger than L2 (matrix + Krylov basis >> 129 MB), no flush"
            if case.n >= 1 << 20 else "small workload: partly L2-resident, no flush"}
     cfg.update(case.describe())
+    if args.solver == "batch":
+        rl = batch_roofline(stats, elapsed_ms / args.steps, fp64_peak)
+        kernels = {"k_slab_queue": {"launches": args.steps, "ms": round(elapsed_ms, 3),
+                                    "share": 1.0, "note": "one graph replay per step; the "
+                                    "step time also holds the Y reset and the status read"}}
+        spmm_rl = None
+    else:
+        rl = roofline(dominant, fams[dominant], hbm_peak, peak_kind, args.precision, wl_name,
+                      fp64_peak)
+        spmm_rl = roofline("spmm", fams["spmm"], hbm_peak, peak_kind, args.precision, wl_name,
+                           fp64_peak)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else f"f64+{args.precision}",
         "data": "synthetic", "config": cfg,
-        "roofline": roofline(dominant, fams[dominant], hbm_peak, peak_kind, args.precision,
-                             wl_name, fp64_peak),
-        "spmm_roofline": roofline("spmm", fams["spmm"], hbm_peak, peak_kind, args.precision,
-                                  wl_name, fp64_peak),
+        "roofline": rl,
+        "spmm_roofline": spmm_rl,
         "fp64_peak": {"tflops": round(fp64_peak, 4), "source": "pint_fp64_fma_peak (measured "
                       "on this GPU in this run)", "nominal_tflops": FP64_NOMINAL_TFLOPS},
         "kernels": kernels, "profiled_ms_per_step": profiled_ms,
@@ -710,11 +874,11 @@ def main():
                        "restarts": stats[-1]["restarts"]},
         "converged": converged, "max_col_relres": max(max(st["col_relres"]) for st in stats),
         "setup": {"first_step_s": setup_s, "precond_setup_ms": st0.setup_ms},
-        "fp64": fp64, "bf16": bf16, "global_fp64": glob,
+        "fp64": fp64, "bf16": bf16, "global_fp64": glob, "batch_kernel_fp64": batchv,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(), "impl": "pint",
     }
-    if linear(args):
+    if linear(args) and args.solver != "batch":
         out["spmm_full_width"] = spmm_full_width(P, ctx, case, args.precision, hbm_peak)
     if not args.no_sweep and args.workload == "convdiff3d" and args.solver != "global":
         out["sweep"] = sweep(P, ctx, args, case.w, fp64_peak)
@@ -724,6 +888,65 @@ def main():
     P.pint_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def batch_roofline(stats, ms_per_step, fp64_peak):
+    """The batched kernel is bound by the float64 pipe (about 1/64 of the
+    float32 rate on this GPU), not by HBM: achieved = the algorithmic float64
+    operations the kernel counted (FMA = 2; plain adds, multiplies and square
+    roots 1 each, although each takes a full FMA issue slot) per step over the
+    step time, against the measured float64 FMA rate."""
+    fl = stats[-1].get("flops") or 0.0
+    if fl <= 0 or ms_per_step <= 0:
+        return None
+    ach = fl / (ms_per_step / 1e3) / 1e12
+    return {"kernel": "k_slab_queue", "bound": "alu", "achieved": round(ach, 4),
+            "peak": round(fp64_peak, 4), "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4),
+            "peak_source": "measured float64 FMA rate (pint_fp64_fma_peak, this run)",
+            "flops_per_step": fl, "traffic": None, "launches": 1,
+            "avg_launch_us": ms_per_step * 1e3,
+            "note": "step time (graph replay + Y reset + status read) as the launch time"}
+
+
+def batch_variant(P, ctx, case, args, stream, fp64_peak):
+    """The same slab through the batched persistent kernel (one cluster, a
+    captured graph), float64 + Jacobi: one warm-up, then as many timed steps
+    as the headline."""
+    import torch
+    plan = None
+    try:
+        o = P.pint_opts_default()
+        o.tol = case.o.tol
+        o.precond = P.PINT_PC_JACOBI
+        o.precision = P.PINT_FP64
+        o.restart = case.o.restart
+        plan = P.BatchPlan(ctx, [(case.op, case.Bd, None, case.Y)], o)
+        case.Y.zero_()
+        plan.run()
+        k = max(1, args.steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sts = []
+        for _ in range(k):
+            case.Y.zero_()
+            sts.append(plan.run()[0].as_dict(case.s))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        return {"value": case.time_steps * case.n / (ms / 1e3), "unit": UNIT,
+                "ms_per_step": ms, "steps": k, "launch_shape": plan.shape(),
+                "solver": f"global GMRES({o.restart}) + Jacobi in the batched persistent kernel",
+                "outer": sts[-1]["outer_its"], "inner": sts[-1]["inner_its"],
+                "converged": all(x["status"] == 0 for x in sts),
+                "max_col_relres": max(max(x["col_relres"]) for x in sts),
+                "roofline": batch_roofline(sts, ms, fp64_peak)}
+    except Exception as e:              # report, do not hide
+        return {"value": None, "error": str(e)[:300]}
+    finally:
+        if plan is not None:
+            plan.close()
 
 
 def solver_variant(P, case, args, stream, solver):
@@ -941,7 +1164,9 @@ def serve_main(args, world, rank, local, cpu, desc):
     grids = tuple(g for g in (32, 48, 64, 96, 128) if g <= args.n)
     specs = synth.request_stream(5 + rank, args.requests, args.rate, grids=grids)
     reqs = [make(sp) for sp in specs]
-    srv = serve.SlabServer(slots=args.slots, device=local, keep_results=True)
+    srv = serve.SlabServer(slots=args.slots, device=local, keep_results=True,
+                           batch_lane=not args.no_batch_lane,
+                           batch_max_unknowns=args.batch_max_unknowns)
     try:
         warm = [make({"rid": -1 - i, "arrival": 0.0, "n": grids[0], "s": w, "precision": p})
                 for i, (w, p) in enumerate([(2, "fp32"), (4, "fp64"), (8, "fp32"), (16, "fp64")])]
@@ -949,6 +1174,8 @@ def serve_main(args, world, rank, local, cpu, desc):
         with ClockSampler(torch.cuda.current_device()) as clk:
             summ = srv.run(reqs)
         launches = sum(int(P.pint_kernel_launches(c)) for c in srv._ctx if c is not None)
+        if srv._bctx is not None:
+            launches += int(P.pint_kernel_launches(srv._bctx))
     finally:
         srv.close()
     dist = None
@@ -969,7 +1196,11 @@ def serve_main(args, world, rank, local, cpu, desc):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1,
         "warmup": args.warmup, "ms_per_step": span * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+fp32/f64", "data": "synthetic",
-        "config": {"workload": f"serve_{args.requests}req_rate{args.rate:g}_slots{args.slots}",
+        "config": {"workload": f"serve_{args.requests}req_rate{args.rate:g}_slots{args.slots}"
+                               + ("" if args.no_batch_lane else "_batchlane"),
+                   "batch_lane": None if args.no_batch_lane else
+                   {"max_unknowns": args.batch_max_unknowns, "precision": "fp64",
+                    "method": "global GMRES + Jacobi, one launch per batch, 8-CTA clusters"},
                    "description": desc, "grids": list(grids),
                    "widths": [2, 4, 8, 16], "precisions": ["fp32", "fp64"],
                    "restart": args.restart, "parallelism": f"replicas x{world}",

@@ -76,6 +76,7 @@ enum { PINT_SOLVER_GMRES = 0, PINT_SOLVER_CG = 1, PINT_SOLVER_BICGSTAB = 2,
 typedef struct pint_ctx_s* pint_ctx;
 typedef struct pint_op_s* pint_op;
 typedef struct pint_problem_s* pint_problem;
+typedef struct pint_batch_plan_s* pint_batch_plan;
 
 typedef struct {
   double tol;        /* outer: ||R_k||_2 <= tol ||F_k||_2, F = B A2^T + B0   */
@@ -128,6 +129,9 @@ typedef struct {
   double setup_ms;              /* preconditioner set-up (host clock)        */
   double solve_ms;              /* whole call (host clock)                   */
   double col_relres[PINT_MAX_S];/* final ||R_k|| / ||F_k|| per column        */
+  double flops;                 /* algorithmic float64 operations (FMA = 2)
+                                   when the call counts them (the batched
+                                   solver), else 0                           */
 } pint_stats;
 
 /* Fill `o` with the defaults: tol 1e-10, inner_tol 1e-2, restart 30,
@@ -221,30 +225,57 @@ typedef struct {
 
 /* Many slab solves (uneven N and s, each with its own operator and coupling)
  * in ONE persistent kernel launch: thread-block clusters of `cluster_ctas`
- * CTAs (1..16; 0 = pint_batch_auto_cluster) take jobs from a device queue and
+ * CTAs (1..16; 0 = pint_batch_auto_cluster) of `cta_threads` threads (128,
+ * 256 or 512; 0 = pint_batch_auto_threads) take jobs from a device queue and
  * run each whole solve inside the cluster, with no host round trip per
  * Arnoldi step. The method per job is the one of PINT_SOLVER_GLOBAL in
  * pint_solve_block (global GMRES(opts->restart) on the unsplit coupled
  * operator, restarted as defect correction from the true residual, same
  * stopping test; modified Gram-Schmidt when a job runs on one CTA, two
  * classical passes on a cluster), float64, right preconditioned by Jacobi of
- * J = alpha M + beta K or by none: opts->precision must be PINT_FP64 and
- * opts->precond PINT_PC_JACOBI or PINT_PC_NONE, else PINT_ERR_INVALID.
- * opts->solver and inner_tol are not used. A job's result does not depend on
- * the other jobs of the batch (fixed reduction order for a given cluster
- * size). `stats`: NULL or njobs entries, filled per job (solve_ms is the whole
+ * J = alpha M + beta K or by none: opts->precision must be PINT_FP64,
+ * opts->precond PINT_PC_JACOBI or PINT_PC_NONE and opts->restart at most 32,
+ * else PINT_ERR_INVALID. opts->solver and inner_tol are not used. A job's
+ * result does not depend on the other jobs of the batch (fixed reduction
+ * order for a given cluster size and CTA width). `stats`: NULL or njobs entries, filled per job (solve_ms is the whole
  * call). Device memory for (restart + 3) N s doubles per resident cluster is
  * taken from the context budget for the call. Synchronous. Returns PINT_OK
  * when every job converged, PINT_ERR_BREAKDOWN if any job met a non-finite
  * residual, else PINT_ERR_NOT_CONVERGED; per-job status is in stats. */
 int pint_solve_batch(pint_ctx ctx, int njobs, const pint_batch_job* jobs,
-                     const pint_opts* opts, int cluster_ctas, pint_stats* stats,
-                     void* stream);
+                     const pint_opts* opts, int cluster_ctas, int cta_threads,
+                     pint_stats* stats, void* stream);
+
+/* Resident form of pint_solve_batch for repeated solves of the same jobs
+ * (a serving loop, a bench): pint_batch_plan_create validates the jobs, copies
+ * their couplings and descriptors to the device, allocates the workspace of
+ * every resident cluster once and captures the launch (queue reset + the
+ * persistent kernel) as a CUDA graph; it waits for its own copies on
+ * `stream`. pint_batch_plan_run replays the graph on `stream`, waits for it
+ * and fills `stats` (NULL or njobs entries); it returns as pint_solve_batch.
+ * The caller writes new B, B0 and initial Y into the same device buffers
+ * between runs. The plan borrows the operators and the job buffers: they must
+ * stay alive and unchanged (no pint_set_coupling, pint_operator_update_values
+ * or destroy) until pint_batch_plan_destroy, which waits for the device and
+ * frees the plan's memory. */
+int pint_batch_plan_create(pint_ctx ctx, int njobs, const pint_batch_job* jobs,
+                           const pint_opts* opts, int cluster_ctas, int cta_threads,
+                           pint_batch_plan* plan, void* stream);
+int pint_batch_plan_run(pint_batch_plan plan, pint_stats* stats, void* stream);
+/* The launch shape the plan took: CTAs per cluster, threads per CTA and the
+ * number of clusters launched (resident at once, at most njobs). */
+int pint_batch_plan_shape(pint_batch_plan plan, int* cluster_ctas, int* cta_threads,
+                          int* resident_clusters);
+int pint_batch_plan_destroy(pint_batch_plan plan);
 
 /* The cluster size pint_solve_batch takes for cluster_ctas = 0: 1 when the
  * jobs alone occupy every SM, else the largest power of two up to 16 with
  * njobs * C <= SMs and at least 256 rows per CTA in the smallest job. */
 int pint_batch_auto_cluster(pint_ctx ctx, int njobs, int64_t min_n);
+
+/* The CTA width pint_solve_batch takes for cta_threads = 0 with clusters of
+ * cluster_ctas CTAs: 256 for clusters of 16, else 512. */
+int pint_batch_auto_threads(pint_ctx ctx, int njobs, int cluster_ctas);
 
 /* shift((Y_1,...,Y_s)) = (Y_2,...,Y_s,Y_s) in place (Sec. 2.2, Eq. shift). */
 int pint_shift(double* Y, int64_t n, int s, void* stream);

@@ -55,13 +55,14 @@ class pint_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_its", C.c_int), ("inner_its", C.c_int),
                 ("restarts", C.c_int), ("deflations", C.c_int), ("kernel_launches", C.c_int),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double),
-                ("col_relres", C.c_double * PINT_MAX_S)]
+                ("col_relres", C.c_double * PINT_MAX_S), ("flops", C.c_double)]
 
     def as_dict(self, s=PINT_MAX_S):
         return {"status": self.status, "outer_its": self.outer_its, "inner_its": self.inner_its,
                 "restarts": self.restarts, "deflations": self.deflations,
                 "kernel_launches": self.kernel_launches, "setup_ms": self.setup_ms,
-                "solve_ms": self.solve_ms, "col_relres": list(self.col_relres)[:s]}
+                "solve_ms": self.solve_ms, "col_relres": list(self.col_relres)[:s],
+                "flops": self.flops}
 
 
 if not os.path.exists(LIB_PATH):
@@ -86,8 +87,14 @@ _SIGS = {
     "pint_apply_coupled": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pint_solve_block": (_i, [_vp, _vp, _vp, _vp, C.POINTER(pint_opts), C.POINTER(pint_stats), _vp]),
     "pint_solve_batch": (_i, [_vp, _i, C.POINTER(pint_batch_job), C.POINTER(pint_opts), _i,
-                              C.POINTER(pint_stats), _vp]),
+                              _i, C.POINTER(pint_stats), _vp]),
+    "pint_batch_plan_create": (_i, [_vp, _i, C.POINTER(pint_batch_job), C.POINTER(pint_opts),
+                                    _i, _i, C.POINTER(_vp), _vp]),
+    "pint_batch_plan_run": (_i, [_vp, C.POINTER(pint_stats), _vp]),
+    "pint_batch_plan_shape": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
+    "pint_batch_plan_destroy": (_i, [_vp]),
     "pint_batch_auto_cluster": (_i, [_vp, _i, _i64]),
+    "pint_batch_auto_threads": (_i, [_vp, _i, _i]),
     "pint_shift": (_i, [_vp, _i64, _i, _vp]),
     "pint_problem_create": (_i, [_vp, C.POINTER(_vp), _i, _i, _i, _i, _vp, _vp, _vp]),
     "pint_problem_destroy": (_i, [_vp]),
@@ -248,26 +255,87 @@ def pint_solve_block(ctx, op, B, B0, Y, opts=None, stream=None, raise_on_nonconv
     return st
 
 
-def pint_solve_batch(ctx, jobs, opts=None, cluster_ctas=0, stream=None,
+def pint_solve_batch(ctx, jobs, opts=None, cluster_ctas=0, cta_threads=0, stream=None,
                      raise_on_nonconvergence=False):
     """jobs: sequence of (op, B, B0, Y) (B, B0 may be None). Returns the
     per-job pint_stats list."""
     o = opts if opts is not None else pint_opts_default()
+    arr = _batch_jobs(jobs)
+    sts = (pint_stats * len(jobs))()
+    rc = lib.pint_solve_batch(ctx, len(jobs), arr, C.byref(o), int(cluster_ctas),
+                              int(cta_threads), sts, _stream(stream))
+    _check(rc, ctx, allow=() if raise_on_nonconvergence else (PINT_ERR_NOT_CONVERGED,))
+    return list(sts)
+
+
+def _batch_jobs(jobs):
     arr = (pint_batch_job * len(jobs))()
     for i, (op, B, B0, Y) in enumerate(jobs):
         arr[i].op = op.value if isinstance(op, C.c_void_p) else op
         arr[i].B = None if B is None else B.data_ptr()
         arr[i].B0 = None if B0 is None else B0.data_ptr()
         arr[i].Y = Y.data_ptr()
-    sts = (pint_stats * len(jobs))()
-    rc = lib.pint_solve_batch(ctx, len(jobs), arr, C.byref(o), int(cluster_ctas), sts,
-                              _stream(stream))
+    return arr
+
+
+def pint_batch_plan_create(ctx, jobs, opts=None, cluster_ctas=0, cta_threads=0, stream=None):
+    """jobs: sequence of (op, B, B0, Y) device tensors (B, B0 may be None);
+    the tensors must stay alive until pint_batch_plan_destroy."""
+    o = opts if opts is not None else pint_opts_default()
+    h = C.c_void_p()
+    _check(lib.pint_batch_plan_create(ctx, len(jobs), _batch_jobs(jobs), C.byref(o),
+                                      int(cluster_ctas), int(cta_threads), C.byref(h),
+                                      _stream(stream)), ctx)
+    return h
+
+
+def pint_batch_plan_run(ctx, plan, njobs, stream=None, raise_on_nonconvergence=False):
+    sts = (pint_stats * njobs)()
+    rc = lib.pint_batch_plan_run(plan, sts, _stream(stream))
     _check(rc, ctx, allow=() if raise_on_nonconvergence else (PINT_ERR_NOT_CONVERGED,))
     return list(sts)
 
 
+def pint_batch_plan_shape(ctx, plan):
+    c, t, r = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.pint_batch_plan_shape(plan, C.byref(c), C.byref(t), C.byref(r)), ctx)
+    return {"cluster_ctas": c.value, "cta_threads": t.value, "resident_clusters": r.value}
+
+
+def pint_batch_plan_destroy(plan):
+    return lib.pint_batch_plan_destroy(plan)
+
+
+class BatchPlan:
+    """A resident batched solve over the pint_batch_plan_* calls: the jobs'
+    device buffers are borrowed; write new B / initial Y into them between
+    run() calls."""
+
+    def __init__(self, ctx, jobs, opts=None, cluster_ctas=0, cta_threads=0, stream=None):
+        self.ctx = ctx
+        self.njobs = len(jobs)
+        self._keep = list(jobs)                    # keep the tensors alive
+        self.h = pint_batch_plan_create(ctx, jobs, opts, cluster_ctas, cta_threads, stream)
+
+    def run(self, stream=None, raise_on_nonconvergence=False):
+        return pint_batch_plan_run(self.ctx, self.h, self.njobs, stream,
+                                   raise_on_nonconvergence)
+
+    def shape(self):
+        return pint_batch_plan_shape(self.ctx, self.h)
+
+    def close(self):
+        if self.h:
+            pint_batch_plan_destroy(self.h)
+            self.h = None
+
+
 def pint_batch_auto_cluster(ctx, njobs, min_n):
     return lib.pint_batch_auto_cluster(ctx, int(njobs), int(min_n))
+
+
+def pint_batch_auto_threads(ctx, njobs, cluster_ctas):
+    return lib.pint_batch_auto_threads(ctx, int(njobs), int(cluster_ctas))
 
 
 def pint_shift(Y, n, s, stream=None):

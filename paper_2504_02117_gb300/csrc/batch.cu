@@ -62,11 +62,11 @@ struct BatchJob {
 
 struct BatchOut {
   int status, outer, inner, cycles;
+  long long flops;          // algorithmic float64 operations of the job (FMA = 2)
   double relres[kMaxS];
 };
 
-constexpr int kBatchThreads = 512;
-constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kBatchThreadsMax = 512;  // CTA widths 128, 256, 512 (a template parameter)
 constexpr int kRedSlot = 32;          // values per cluster reduction (m + 1 <= 31, s <= 16)
 
 // Sum over the warp of NV = 2^p values per lane with NV - 1 + 5 - p adds:
@@ -165,8 +165,8 @@ __device__ __forceinline__ void coupled(int s, int64_t r0, int64_t r1, const int
 }
 
 // Squared column norms of rows [r0, r1) of X (N x S): warp partials of
-// column k into red2[k * kBatchWarps + warp].
-template <int S>
+// column k into red2[k * NW + warp].
+template <int S, int NW>
 __device__ __noinline__ void colsq_rows(int64_t r0, int64_t r1, const double* X, double* red2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double acc[S];
@@ -178,15 +178,16 @@ __device__ __noinline__ void colsq_rows(int64_t r0, int64_t r1, const double* X,
 #pragma unroll
   for (int k = 0; k < S; ++k) {
     const double v = warp_sum(acc[k]);
-    if (lane == 0) red2[k * kBatchWarps + warp] = v;
+    if (lane == 0) red2[k * NW + warp] = v;
   }
 }
 
+template <int NW>
 __device__ __forceinline__ void colsq(int s, int64_t r0, int64_t r1, const double* X,
                                       double* red2) {
   switch (s) {
 #define PINT_CASE(SS) \
-  case SS: colsq_rows<SS>(r0, r1, X, red2); break;
+  case SS: colsq_rows<SS, NW>(r0, r1, X, red2); break;
     PINT_CASE(1) PINT_CASE(2) PINT_CASE(3) PINT_CASE(4) PINT_CASE(5) PINT_CASE(6)
     PINT_CASE(7) PINT_CASE(8) PINT_CASE(9) PINT_CASE(10) PINT_CASE(11) PINT_CASE(12)
     PINT_CASE(13) PINT_CASE(14) PINT_CASE(15) PINT_CASE(16)
@@ -196,19 +197,20 @@ __device__ __forceinline__ void colsq(int s, int64_t r0, int64_t r1, const doubl
 }
 
 // Cluster sum of nv <= kRedSlot values: the warp partials of value v are in
-// red2[v * kBatchWarps + w]. Every CTA of the cluster ends with the same sums
+// red2[v * NW + w] (NW warps). Every CTA of the cluster ends with the same sums
 // in res[0..nv): CTA partials (warps in order) go to this CTA's slot, the
 // cluster barrier publishes them, and each CTA adds the slots of ranks
 // 0..C-1 in order. Callers alternate between two slots, so a slot is
 // rewritten only after the next barrier has shown that every CTA is done
 // reading it. With C = 1 the cluster barrier is a CTA barrier.
+template <int NW>
 __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int C, int nv,
                                                const double* red2, double* slot, double* res) {
   __syncthreads();
   const int t = threadIdx.x;
   if (nv == 1) {                  // one value: a tree over the warp partials
     if (t < 32) {
-      double a = t < kBatchWarps ? red2[t] : 0.0;
+      double a = t < NW ? red2[t] : 0.0;
       a = warp_sum(a);
       if (t == 0) {
         if (C == 1) res[0] = a;
@@ -217,7 +219,7 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int C, int
     }
   } else if (t < nv) {
     double a = 0.0;
-    for (int w = 0; w < kBatchWarps; ++w) a += red2[t * kBatchWarps + w];
+    for (int w = 0; w < NW; ++w) a += red2[t * NW + w];
     if (C == 1) res[t] = a;
     else slot[t] = a;
   }
@@ -236,8 +238,8 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int C, int
 
 // Frobenius products of NV consecutive basis blocks P_u = P + u ns with W over
 // the elements [e0, e1) of this CTA; warp partials of product i0 + u go to
-// red2[(i0 + u) * kBatchWarps + warp].
-template <int NV>
+// red2[(i0 + u) * NW + warp].
+template <int NV, int NW>
 __device__ __forceinline__ void dots_chunk(const double* P, int64_t ns, const double* W,
                                            int64_t e0, int64_t e1, int i0, double* red2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -251,39 +253,40 @@ __device__ __forceinline__ void dots_chunk(const double* P, int64_t ns, const do
   }
   const double v = warp_sum_multi<NV>(a);
   constexpr int per = 32 / NV;
-  if (lane % per == 0) red2[(i0 + lane / per) * kBatchWarps + warp] = v;
+  if (lane % per == 0) red2[(i0 + lane / per) * NW + warp] = v;
 }
 
 // Products <V_i, W> for i = 0..j in chunks of 8, 4, 2, 1.
+template <int NW>
 __device__ __forceinline__ void dots_all(const double* V, int64_t ns, const double* W, int j,
                                          int64_t e0, int64_t e1, double* red2) {
   int i0 = 0, left = j + 1;
   while (left >= 8) {
-    dots_chunk<8>(V + (size_t)i0 * ns, ns, W, e0, e1, i0, red2);
+    dots_chunk<8, NW>(V + (size_t)i0 * ns, ns, W, e0, e1, i0, red2);
     i0 += 8;
     left -= 8;
   }
   if (left >= 4) {
-    dots_chunk<4>(V + (size_t)i0 * ns, ns, W, e0, e1, i0, red2);
+    dots_chunk<4, NW>(V + (size_t)i0 * ns, ns, W, e0, e1, i0, red2);
     i0 += 4;
     left -= 4;
   }
   if (left >= 2) {
-    dots_chunk<2>(V + (size_t)i0 * ns, ns, W, e0, e1, i0, red2);
+    dots_chunk<2, NW>(V + (size_t)i0 * ns, ns, W, e0, e1, i0, red2);
     i0 += 2;
     left -= 2;
   }
-  if (left >= 1) dots_chunk<1>(V + (size_t)i0 * ns, ns, W, e0, e1, i0, red2);
+  if (left >= 1) dots_chunk<1, NW>(V + (size_t)i0 * ns, ns, W, e0, e1, i0, red2);
 }
 
-// Dynamic shared memory of k_slab_queue (doubles) for restart length m and
-// largest block width smax: Hessenberg (m+1) x m, g, cs, sn, y, h (m+1 each),
-// warp partials kRedSlot x warps, two cluster slots and the reduced values
-// (kRedSlot each), ||F_k||, ||R_k||, scalars, the coupling staging area
-// (2 smax per thread).
-__host__ __device__ inline size_t batch_smem_doubles(int m, int smax) {
-  return (size_t)(m + 1) * m + 5 * (size_t)(m + 1) + (size_t)kRedSlot * kBatchWarps +
-         3 * kRedSlot + 2 * kMaxS + 8 + 2 * (size_t)smax * kBatchThreads;
+// Dynamic shared memory of k_slab_queue (doubles) for restart length m,
+// largest block width smax and nt threads: Hessenberg (m+1) x m, g, cs, sn,
+// y, h (m+1 each), warp partials kRedSlot x warps, two cluster slots and the
+// reduced values (kRedSlot each), ||F_k||, ||R_k||, scalars, the coupling
+// staging area (2 smax per thread).
+__host__ __device__ inline size_t batch_smem_doubles(int m, int smax, int nt) {
+  return (size_t)(m + 1) * m + 5 * (size_t)(m + 1) + (size_t)kRedSlot * (nt / 32) +
+         3 * kRedSlot + 2 * kMaxS + 8 + 2 * (size_t)smax * nt;
 }
 
 // Per-cluster workspace of one job (doubles): m + 1 basis blocks, R, Z (N s
@@ -296,7 +299,8 @@ __host__ __device__ inline int64_t batch_work_doubles(int m, int64_t n, int s, i
 // the queue is empty. Every branch that brackets a barrier depends only on
 // values that all CTAs of the cluster hold identically (cluster sums, the
 // redundantly updated least-squares state, iteration counters).
-__global__ void __launch_bounds__(kBatchThreads)
+template <int NT>
+__global__ void __launch_bounds__(NT, kBatchThreadsMax / NT)
 k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, int max_outer,
              int max_inner, double* __restrict__ work, int64_t work_stride,
              int* __restrict__ queue, BatchOut* __restrict__ outs) {
@@ -311,7 +315,8 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
   double* y = sn + (m + 1);
   double* hs = y + (m + 1);
   double* red2 = hs + (m + 1);                       // kRedSlot x warps
-  double* slots = red2 + (size_t)kRedSlot * kBatchWarps;   // 2 x kRedSlot
+  constexpr int NW = NT / 32;
+  double* slots = red2 + (size_t)kRedSlot * NW;     // 2 x kRedSlot
   double* res = slots + 2 * kRedSlot;                // kRedSlot
   double* fn = res + kRedSlot;                       // kMaxS
   double* rn = fn + kMaxS;                           // kMaxS
@@ -325,7 +330,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
   int buf = 0;                                       // cluster slot in use
 #define PINT_REDUCE(NV)                                                 \
   do {                                                                  \
-    cluster_reduce(cl, C, (NV), red2, slots + buf * kRedSlot, res);     \
+    cluster_reduce<NW>(cl, C, (NV), red2, slots + buf * kRedSlot, res); \
     buf ^= 1;                                                           \
   } while (0)
 #define PINT_SYNC_ALL() \
@@ -382,7 +387,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
     cl.sync();
     // ||F_k|| from the residual of Y = 0
     coupled<false>(s, r0, r1, J.rowptr, J.colind, J.Kval, J.Mdiag, L, Z, J.B, J.B0, R, xs);
-    colsq(s, r0, r1, R, red2);
+    colsq<NW>(s, r0, r1, R, red2);
     PINT_REDUCE(s);
     if (tid < s) fn[tid] = sqrt(res[tid]);
     __syncthreads();
@@ -392,10 +397,17 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
       target = k == 0 ? thr : fmin(target, thr);
     }
     int status = PINT_ERR_NOT_CONVERGED, outer = 0, inner = 0, cycles = 0;
+    // algorithmic float64 operation count (FMA = 2): residual and Krylov
+    // operator per application, per-step orthogonalisation, per-cycle update
+    const long long nA = L.off2[s];                  // nonzeros of A1 and A2
+    const long long c_pre = 2LL * J.nnz * s + 2LL * n * nA + 2LL * ns;
+    const long long c_res = c_pre + (J.B ? ns : 0) + (J.B0 ? ns : 0);
+    long long flops = (long long)J.nnz + n + c_res + 2LL * ns;
     for (outer = 0; outer <= max_outer; ++outer) {
+      flops += c_res + 2LL * ns;
       PINT_SYNC_ALL();                               // Y rows of every CTA updated
       coupled<false>(s, r0, r1, J.rowptr, J.colind, J.Kval, J.Mdiag, L, J.Y, J.B, J.B0, R, xs);
-      colsq(s, r0, r1, R, red2);
+      colsq<NW>(s, r0, r1, R, red2);
       PINT_REDUCE(s);
       if (tid < s) rn[tid] = sqrt(res[tid]);
       __syncthreads();
@@ -417,6 +429,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
       }
       if (outer == max_outer || inner >= max_inner) break;
       cycles += 1;
+      flops += ns;
       // V_0 = R / ||R||_F, least-squares right-hand side beta e_1
       const double ib = 1.0 / beta;
       for (int64_t e = e0 + tid; e < e1; e += T) V[e] = R[e] * ib;
@@ -470,7 +483,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
           // forms ||W||^2
           double a = 0.0;
           for (int pass = 0; pass < 2; ++pass) {
-            dots_all(V, ns, W, j, e0, e1, red2);
+            dots_all<NW>(V, ns, W, j, e0, e1, red2);
             PINT_REDUCE(j + 1);
             if (tid <= j) {
               hs[tid] = res[tid];
@@ -513,6 +526,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
         }
         __syncthreads();
         inner += 1;
+        flops += c_pre + (mgs ? 4LL : 8LL) * (j + 1) * ns + 3LL * ns;
         const double est = misc[0];
         if (!isfinite(est)) {
           status = PINT_ERR_BREAKDOWN;
@@ -534,6 +548,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
         }
       }
       __syncthreads();
+      flops += 2LL * kd * ns + 2LL * ns;
       // Y <- Y - D^-1 sum_i y_i V_i on this CTA's rows
       for (int64_t r = r0 + tid; r < r1; r += T) {
         const double jr = J.Jinv[r];
@@ -551,6 +566,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
       o->outer = outer;
       o->inner = inner;
       o->cycles = cycles;
+      o->flops = flops;
       for (int k = 0; k < kMaxS; ++k)
         o->relres[k] = k < s ? (fn[k] > 0.0 ? rn[k] / fn[k] : rn[k]) : 0.0;
     }
@@ -568,8 +584,18 @@ namespace {
 // with one CTA per SM and at least 256 rows per CTA in the smallest job
 int auto_cluster(int num_sms, int njobs, int64_t min_n) {
   for (int c = 16; c >= 2; c /= 2)
-    if ((int64_t)njobs * c <= num_sms && min_n / c >= pint::kBatchThreads / 2) return c;
+    if ((int64_t)njobs * c <= num_sms && min_n / c >= 256) return c;
   return 1;
+}
+
+// 512 threads (one CTA per SM), 256 for clusters of 16: measured on the 64 x 64
+// s = 4 slab, one CTA of 512 beats two of 256 per SM on single-CTA jobs
+// (6.2e7 vs 4.8e7 time-step DOF/s for 608 jobs), and 16 x 256 beats 16 x 512
+// (4.1 vs 4.2 ms alone, 5.5 vs 8.1 ms for eight jobs, more clusters resident)
+int auto_threads(int num_sms, int njobs, int C) {
+  (void)num_sms;
+  (void)njobs;
+  return C >= 16 ? 256 : 512;
 }
 
 double batch_now_ms() {
@@ -578,11 +604,11 @@ double batch_now_ms() {
       .count();
 }
 
-cudaLaunchConfig_t batch_config(int grid, size_t smem, cudaStream_t st, cudaLaunchAttribute* attr,
-                                int C) {
+cudaLaunchConfig_t batch_config(int grid, int nt, size_t smem, cudaStream_t st,
+                                cudaLaunchAttribute* attr, int C) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid, 1, 1);
-  cfg.blockDim = dim3(pint::kBatchThreads, 1, 1);
+  cfg.blockDim = dim3((unsigned)nt, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -594,155 +620,227 @@ cudaLaunchConfig_t batch_config(int grid, size_t smem, cudaStream_t st, cudaLaun
   return cfg;
 }
 
+// Sets the kernel's launch attributes and returns how many clusters of C
+// CTAs can be resident at once. The kernel also declares about 6.5 KB of
+// static shared memory, so the dynamic limit is set on every call.
+template <int NT>
+int slab_queue_clusters(int C, size_t smem, int num_sms, cudaStream_t st) {
+  using namespace pint;
+  PINT_CUDA(cudaFuncSetAttribute(k_slab_queue<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  if (C > 8)
+    PINT_CUDA(cudaFuncSetAttribute(k_slab_queue<NT>,
+                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = batch_config(C * num_sms, NT, smem, st, attr, C);
+  int ncl = 0;
+  PINT_CUDA(cudaOccupancyMaxActiveClusters(&ncl, k_slab_queue<NT>, &cfg));
+  return ncl;
+}
+
+template <int NT>
+void slab_queue_launch(int C, int nclusters, size_t smem, cudaStream_t st, int njobs,
+                       const pint::BatchJob* jobs, int m, const pint_opts* o, double* work,
+                       int64_t stride, int* queue, pint::BatchOut* outs) {
+  using namespace pint;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = batch_config(C * nclusters, NT, smem, st, attr, C);
+  PINT_CUDA(cudaLaunchKernelEx(&cfg, k_slab_queue<NT>, njobs, jobs, m, o->tol, o->max_outer,
+                               o->max_inner, work, stride, queue, outs));
+  check_launch("k_slab_queue");
+}
+
 }  // namespace
 
-extern "C" int pint_solve_batch(pint_ctx ctx, int njobs, const pint_batch_job* jobs,
-                                const pint_opts* o, int cluster_ctas, pint_stats* stats,
-                                void* stream) {
+struct pint_batch_plan_s {
+  pint_ctx ctx = nullptr;
+  int njobs = 0, m = 0, C = 1, NT = 512, nclusters = 0;
+  size_t smem = 0;
+  int64_t stride = 0;
+  pint_opts o{};
+  std::vector<std::pair<void*, size_t>> dev;         // device allocations (budgeted)
+  pint::BatchJob* d_jobs = nullptr;
+  pint::BatchOut* d_out = nullptr;
+  double* d_cpl = nullptr;
+  int* d_queue = nullptr;
+  double* work = nullptr;
+  double* d_ones = nullptr;
+  pint::BatchOut* h_out = nullptr;                   // pinned
+  cudaStream_t cap = nullptr;                        // private capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void* plan_alloc(pint_batch_plan p, size_t b) {
+  void* q = pint::dalloc(p->ctx, b);
+  p->dev.push_back({q, b});
+  return q;
+}
+
+void plan_free(pint_batch_plan p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  if (p->h_out) cudaFreeHost(p->h_out);
+  for (auto& x : p->dev) pint::dfree(p->ctx, x.first, x.second);
+  delete p;
+}
+
+// Builds the plan: validates the jobs, forms the device descriptors, sizes
+// and allocates the workspace, and captures the launch (queue reset + the
+// persistent kernel) as a CUDA graph.
+void plan_build(pint_batch_plan p, int njobs, const pint_batch_job* jobs, int cluster_ctas,
+                int cta_threads, cudaStream_t st) {
   using namespace pint;
+  pint_ctx ctx = p->ctx;
+  const pint_opts* o = &p->o;
+  PINT_REQUIRE(njobs >= 1 && jobs, PINT_ERR_INVALID, "batch: need njobs >= 1 and jobs");
+  PINT_REQUIRE(o->precision == PINT_FP64, PINT_ERR_INVALID, "batch: precision must be PINT_FP64");
+  PINT_REQUIRE(o->precond == PINT_PC_JACOBI || o->precond == PINT_PC_NONE, PINT_ERR_INVALID,
+               "batch: precond must be PINT_PC_JACOBI or PINT_PC_NONE");
+  PINT_REQUIRE(o->restart >= 1 && o->restart <= kRedSlot, PINT_ERR_INVALID,
+               "batch: restart must be in 1..32");
+  PINT_REQUIRE(o->max_outer >= 0 && o->max_inner >= 0 && o->tol >= 0.0, PINT_ERR_INVALID,
+               "negative iteration limit or tolerance");
+  PINT_REQUIRE(cluster_ctas >= 0 && cluster_ctas <= 16, PINT_ERR_INVALID,
+               "cluster_ctas must be 0 (automatic) or 1..16");
+  PINT_REQUIRE(cta_threads == 0 || cta_threads == 128 || cta_threads == 256 ||
+                   cta_threads == 512,
+               PINT_ERR_INVALID, "cta_threads must be 0 (automatic), 128, 256 or 512");
+  const int m = o->restart;
+  p->njobs = njobs;
+  p->m = m;
+  int64_t max_work = 1, max_n = 1, min_n = INT64_MAX, ncpl = 0;
+  int smax = 1;
+  for (int i = 0; i < njobs; ++i) {
+    pint_op op = jobs[i].op;
+    PINT_REQUIRE(op && op->ctx == ctx, PINT_ERR_INVALID,
+                 "batch: every job's operator must belong to ctx");
+    PINT_REQUIRE(op->s >= 1, PINT_ERR_INVALID, "coupling not set (pint_set_coupling)");
+    PINT_REQUIRE(jobs[i].Y != nullptr, PINT_ERR_INVALID, "batch: job without Y");
+    if (!op->j_valid) build_inner(op, st);
+    max_work = std::max<int64_t>(max_work, batch_work_doubles(m, op->n, op->s, op->nnz));
+    max_n = std::max<int64_t>(max_n, op->n);
+    min_n = std::min<int64_t>(min_n, op->n);
+    smax = std::max(smax, op->s);
+    ncpl += 2 * op->s * op->s;
+  }
+  p->C = cluster_ctas ? cluster_ctas : auto_cluster(ctx->num_sms, njobs, min_n);
+  p->NT = cta_threads ? cta_threads : auto_threads(ctx->num_sms, njobs, p->C);
+  p->smem = sizeof(double) * batch_smem_doubles(m, smax, p->NT);
+  int ncl = p->NT == 128   ? slab_queue_clusters<128>(p->C, p->smem, ctx->num_sms, st)
+            : p->NT == 256 ? slab_queue_clusters<256>(p->C, p->smem, ctx->num_sms, st)
+                           : slab_queue_clusters<512>(p->C, p->smem, ctx->num_sms, st);
+  PINT_REQUIRE(ncl >= 1, PINT_ERR_INVALID, "batch: a cluster of this size cannot be resident");
+  p->nclusters = std::min(ncl, njobs);
+  p->stride = ((max_work + 31) / 32) * 32;
+  p->d_jobs = static_cast<BatchJob*>(plan_alloc(p, sizeof(BatchJob) * njobs));
+  p->d_out = static_cast<BatchOut*>(plan_alloc(p, sizeof(BatchOut) * njobs));
+  p->d_cpl = static_cast<double*>(plan_alloc(p, sizeof(double) * ncpl));
+  p->d_queue = static_cast<int*>(plan_alloc(p, sizeof(int)));
+  p->work = static_cast<double*>(plan_alloc(p, sizeof(double) * (size_t)p->stride * p->nclusters));
+  PINT_CUDA(cudaMallocHost(&p->h_out, sizeof(BatchOut) * njobs));
+  std::vector<double> ones;
+  if (o->precond == PINT_PC_NONE) {
+    p->d_ones = static_cast<double*>(plan_alloc(p, sizeof(double) * max_n));
+    ones.assign(max_n, 1.0);
+    PINT_CUDA(cudaMemcpyAsync(p->d_ones, ones.data(), sizeof(double) * max_n,
+                              cudaMemcpyHostToDevice, st));
+  }
+  std::vector<double> hcpl((size_t)ncpl);
+  std::vector<BatchJob> hj(njobs);
+  int64_t off = 0;
+  for (int i = 0; i < njobs; ++i) {
+    pint_op op = jobs[i].op;
+    const int s = op->s;
+    for (int a = 0; a < s; ++a)
+      for (int b = 0; b < s; ++b) {
+        hcpl[off + a * s + b] = op->A1[a * kMaxS + b];
+        hcpl[off + s * s + a * s + b] = op->A2[a * kMaxS + b];
+      }
+    BatchJob& J = hj[i];
+    J.n = op->n;
+    J.nnz = op->nnz;
+    J.s = s;
+    J.pad_ = 0;
+    J.rowptr = op->rowptr;
+    J.colind = op->colind;
+    J.Kval = op->Kval;
+    J.Mdiag = op->Mdiag;
+    J.Jinv = p->d_ones ? p->d_ones : op->Jinvdiag;
+    J.cpl = p->d_cpl + off;
+    J.B = jobs[i].B;
+    J.B0 = jobs[i].B0;
+    J.Y = jobs[i].Y;
+    off += 2 * s * s;
+  }
+  PINT_CUDA(cudaMemcpyAsync(p->d_cpl, hcpl.data(), sizeof(double) * ncpl,
+                            cudaMemcpyHostToDevice, st));
+  PINT_CUDA(cudaMemcpyAsync(p->d_jobs, hj.data(), sizeof(BatchJob) * njobs,
+                            cudaMemcpyHostToDevice, st));
+  PINT_CUDA(cudaStreamSynchronize(st));             // host staging vectors go out of scope
+  // the graph: reset the queue counter, run the persistent kernel
+  PINT_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+  PINT_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(p->d_queue, 0, sizeof(int), p->cap);
+  if (p->NT == 128)
+    slab_queue_launch<128>(p->C, p->nclusters, p->smem, p->cap, njobs, p->d_jobs, m, o, p->work,
+                           p->stride, p->d_queue, p->d_out);
+  else if (p->NT == 256)
+    slab_queue_launch<256>(p->C, p->nclusters, p->smem, p->cap, njobs, p->d_jobs, m, o, p->work,
+                           p->stride, p->d_queue, p->d_out);
+  else
+    slab_queue_launch<512>(p->C, p->nclusters, p->smem, p->cap, njobs, p->d_jobs, m, o, p->work,
+                           p->stride, p->d_queue, p->d_out);
+  PINT_CUDA(cudaStreamEndCapture(p->cap, &p->graph));
+  PINT_CUDA(cudaGraphInstantiate(&p->exec, p->graph, 0));
+}
+
+int plan_run(pint_batch_plan p, pint_stats* stats, cudaStream_t st) {
+  using namespace pint;
+  const double t0 = batch_now_ms();
+  PINT_CUDA(cudaGraphLaunch(p->exec, st));
+  check_launch("batch graph");
+  p->ctx->launches += 1;
+  PINT_CUDA(cudaMemcpyAsync(p->h_out, p->d_out, sizeof(BatchOut) * p->njobs,
+                            cudaMemcpyDeviceToHost, st));
+  PINT_CUDA(cudaStreamSynchronize(st));
+  const double t1 = batch_now_ms();
+  int rc = PINT_OK;
+  for (int i = 0; i < p->njobs; ++i) {
+    const BatchOut& h = p->h_out[i];
+    if (stats) {
+      pint_stats& S = stats[i];
+      S = pint_stats{};
+      S.status = h.status;
+      S.outer_its = h.outer;
+      S.inner_its = h.inner;
+      S.restarts = h.cycles;
+      S.kernel_launches = 1;
+      S.solve_ms = t1 - t0;
+      S.flops = (double)h.flops;
+      for (int k = 0; k < kMaxS; ++k) S.col_relres[k] = h.relres[k];
+    }
+    if (h.status == PINT_ERR_BREAKDOWN)
+      rc = PINT_ERR_BREAKDOWN;
+    else if (h.status != PINT_OK && rc == PINT_OK)
+      rc = h.status;
+  }
+  if (rc == PINT_ERR_BREAKDOWN) p->ctx->err = "batch: non-finite residual in a job";
+  else if (rc != PINT_OK) p->ctx->err = "batch: a job did not converge";
+  return rc;
+}
+
+template <typename Fn>
+int batch_guard(pint_ctx ctx, Fn&& fn) {
   if (!ctx) return PINT_ERR_INVALID;
   try {
-    const double t0 = batch_now_ms();
     PINT_CUDA(cudaSetDevice(ctx->device));
-    PINT_REQUIRE(njobs >= 1 && jobs && o, PINT_ERR_INVALID,
-                 "pint_solve_batch: need njobs >= 1, jobs and opts");
-    PINT_REQUIRE(o->precision == PINT_FP64, PINT_ERR_INVALID,
-                 "pint_solve_batch: precision must be PINT_FP64");
-    PINT_REQUIRE(o->precond == PINT_PC_JACOBI || o->precond == PINT_PC_NONE, PINT_ERR_INVALID,
-                 "pint_solve_batch: precond must be PINT_PC_JACOBI or PINT_PC_NONE");
-    PINT_REQUIRE(o->restart >= 1 && o->restart <= PINT_MAX_RESTART, PINT_ERR_INVALID,
-                 "restart out of range");
-    PINT_REQUIRE(o->max_outer >= 0 && o->max_inner >= 0 && o->tol >= 0.0, PINT_ERR_INVALID,
-                 "negative iteration limit or tolerance");
-    PINT_REQUIRE(cluster_ctas >= 0 && cluster_ctas <= 16, PINT_ERR_INVALID,
-                 "cluster_ctas must be 0 (automatic) or 1..16");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int m = o->restart;
-    int64_t max_work = 1, max_n = 1, min_n = INT64_MAX, ncpl = 0;
-    int smax = 1;
-    for (int i = 0; i < njobs; ++i) {
-      pint_op op = jobs[i].op;
-      PINT_REQUIRE(op && op->ctx == ctx, PINT_ERR_INVALID,
-                   "pint_solve_batch: every job's operator must belong to ctx");
-      PINT_REQUIRE(op->s >= 1, PINT_ERR_INVALID, "coupling not set (pint_set_coupling)");
-      PINT_REQUIRE(jobs[i].Y != nullptr, PINT_ERR_INVALID, "pint_solve_batch: job without Y");
-      if (!op->j_valid) build_inner(op, st);
-      max_work = std::max<int64_t>(max_work, batch_work_doubles(m, op->n, op->s, op->nnz));
-      max_n = std::max<int64_t>(max_n, op->n);
-      smax = std::max(smax, op->s);
-      min_n = std::min<int64_t>(min_n, op->n);
-      ncpl += 2 * op->s * op->s;
-    }
-    // dynamic shared memory: the kernel also declares about 6.5 KB
-    // statically, so the limit is set on every call, not only above 48 KB
-    const size_t smem = sizeof(double) * batch_smem_doubles(m, smax);
-    PINT_CUDA(cudaFuncSetAttribute(k_slab_queue, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-    const int C = cluster_ctas ? cluster_ctas : auto_cluster(ctx->num_sms, njobs, min_n);
-    if (C > 8)
-      PINT_CUDA(cudaFuncSetAttribute(k_slab_queue, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    cudaLaunchAttribute attr[1];
-    int nclusters = 0;
-    {
-      cudaLaunchConfig_t cfg = batch_config(C * ctx->num_sms, smem, st, attr, C);
-      PINT_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_slab_queue, &cfg));
-    }
-    PINT_REQUIRE(nclusters >= 1, PINT_ERR_INVALID,
-                 "pint_solve_batch: a cluster of this size cannot be resident");
-    nclusters = std::min(nclusters, njobs);
-    const int64_t stride = ((max_work + 31) / 32) * 32;
-    // device job descriptors, compact couplings, ones for P = identity,
-    // workspace per cluster (batch_work_doubles of the largest job); freed on every exit
-    struct Bufs {
-      pint_ctx c;
-      std::vector<std::pair<void*, size_t>> a;
-      void* get(size_t b) {
-        void* p = dalloc(c, b);
-        a.push_back({p, b});
-        return p;
-      }
-      ~Bufs() {
-        for (auto& x : a) dfree(c, x.first, x.second);
-      }
-    } bufs{ctx, {}};
-    const size_t jb_bytes = sizeof(BatchJob) * njobs, out_bytes = sizeof(BatchOut) * njobs;
-    auto* d_jobs = static_cast<BatchJob*>(bufs.get(jb_bytes));
-    auto* d_out = static_cast<BatchOut*>(bufs.get(out_bytes));
-    auto* d_cpl = static_cast<double*>(bufs.get(sizeof(double) * ncpl));
-    auto* d_queue = static_cast<int*>(bufs.get(sizeof(int)));
-    auto* work = static_cast<double*>(bufs.get(sizeof(double) * (size_t)stride * nclusters));
-    double* d_ones = nullptr;
-    std::vector<double> ones;
-    if (o->precond == PINT_PC_NONE) {
-      d_ones = static_cast<double*>(bufs.get(sizeof(double) * max_n));
-      ones.assign(max_n, 1.0);
-      PINT_CUDA(cudaMemcpyAsync(d_ones, ones.data(), sizeof(double) * max_n,
-                                cudaMemcpyHostToDevice, st));
-    }
-    std::vector<double> hcpl((size_t)ncpl);
-    std::vector<BatchJob> hj(njobs);
-    int64_t off = 0;
-    for (int i = 0; i < njobs; ++i) {
-      pint_op op = jobs[i].op;
-      const int s = op->s;
-      for (int a = 0; a < s; ++a)
-        for (int b = 0; b < s; ++b) {
-          hcpl[off + a * s + b] = op->A1[a * kMaxS + b];
-          hcpl[off + s * s + a * s + b] = op->A2[a * kMaxS + b];
-        }
-      BatchJob& J = hj[i];
-      J.n = op->n;
-      J.nnz = op->nnz;
-      J.s = s;
-      J.pad_ = 0;
-      J.rowptr = op->rowptr;
-      J.colind = op->colind;
-      J.Kval = op->Kval;
-      J.Mdiag = op->Mdiag;
-      J.Jinv = d_ones ? d_ones : op->Jinvdiag;
-      J.cpl = d_cpl + off;
-      J.B = jobs[i].B;
-      J.B0 = jobs[i].B0;
-      J.Y = jobs[i].Y;
-      off += 2 * s * s;
-    }
-    PINT_CUDA(cudaMemcpyAsync(d_cpl, hcpl.data(), sizeof(double) * ncpl, cudaMemcpyHostToDevice,
-                              st));
-    PINT_CUDA(cudaMemcpyAsync(d_jobs, hj.data(), jb_bytes, cudaMemcpyHostToDevice, st));
-    PINT_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
-    {
-      cudaLaunchConfig_t cfg = batch_config(C * nclusters, smem, st, attr, C);
-      PINT_CUDA(cudaLaunchKernelEx(&cfg, k_slab_queue, njobs, (const BatchJob*)d_jobs, m, o->tol,
-                                   o->max_outer, o->max_inner, work, stride, d_queue, d_out));
-      check_launch("k_slab_queue");
-      ctx->launches += 1;
-    }
-    std::vector<BatchOut> ho(njobs);
-    PINT_CUDA(cudaMemcpyAsync(ho.data(), d_out, out_bytes, cudaMemcpyDeviceToHost, st));
-    PINT_CUDA(cudaStreamSynchronize(st));
-    const double t1 = batch_now_ms();
-    int rc = PINT_OK;
-    for (int i = 0; i < njobs; ++i) {
-      if (stats) {
-        pint_stats& S = stats[i];
-        S = pint_stats{};
-        S.status = ho[i].status;
-        S.outer_its = ho[i].outer;
-        S.inner_its = ho[i].inner;
-        S.restarts = ho[i].cycles;
-        S.kernel_launches = 1;
-        S.solve_ms = t1 - t0;
-        for (int k = 0; k < kMaxS; ++k) S.col_relres[k] = ho[i].relres[k];
-      }
-      if (ho[i].status == PINT_ERR_BREAKDOWN)
-        rc = PINT_ERR_BREAKDOWN;
-      else if (ho[i].status != PINT_OK && rc == PINT_OK)
-        rc = ho[i].status;
-    }
-    if (rc == PINT_ERR_BREAKDOWN) ctx->err = "pint_solve_batch: non-finite residual in a job";
-    else if (rc != PINT_OK) ctx->err = "pint_solve_batch: a job did not converge";
-    return rc;
-  } catch (const Error& e) {
+    return fn();
+  } catch (const pint::Error& e) {
     ctx->err = e.msg;
     return e.code;
   } catch (const std::bad_alloc&) {
@@ -751,9 +849,73 @@ extern "C" int pint_solve_batch(pint_ctx ctx, int njobs, const pint_batch_job* j
   }
 }
 
+}  // namespace
+
+extern "C" int pint_batch_plan_create(pint_ctx ctx, int njobs, const pint_batch_job* jobs,
+                                      const pint_opts* opts, int cluster_ctas, int cta_threads,
+                                      pint_batch_plan* plan, void* stream) {
+  if (plan) *plan = nullptr;
+  return batch_guard(ctx, [&] {
+    PINT_REQUIRE(plan && opts, PINT_ERR_INVALID, "batch: need opts and a plan pointer");
+    auto* p = new pint_batch_plan_s;
+    p->ctx = ctx;
+    p->o = *opts;
+    try {
+      plan_build(p, njobs, jobs, cluster_ctas, cta_threads, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+      plan_free(p);
+      throw;
+    }
+    *plan = p;
+    return PINT_OK;
+  });
+}
+
+extern "C" int pint_batch_plan_run(pint_batch_plan plan, pint_stats* stats, void* stream) {
+  if (!plan) return PINT_ERR_INVALID;
+  return batch_guard(plan->ctx,
+                     [&] { return plan_run(plan, stats, static_cast<cudaStream_t>(stream)); });
+}
+
+extern "C" int pint_batch_plan_shape(pint_batch_plan plan, int* cluster_ctas, int* cta_threads,
+                                     int* resident_clusters) {
+  if (!plan) return PINT_ERR_INVALID;
+  if (cluster_ctas) *cluster_ctas = plan->C;
+  if (cta_threads) *cta_threads = plan->NT;
+  if (resident_clusters) *resident_clusters = plan->nclusters;
+  return PINT_OK;
+}
+
+extern "C" int pint_batch_plan_destroy(pint_batch_plan plan) {
+  if (!plan) return PINT_ERR_INVALID;
+  cudaSetDevice(plan->ctx->device);
+  cudaDeviceSynchronize();
+  plan_free(plan);
+  return PINT_OK;
+}
+
+extern "C" int pint_solve_batch(pint_ctx ctx, int njobs, const pint_batch_job* jobs,
+                                const pint_opts* o, int cluster_ctas, int cta_threads,
+                                pint_stats* stats, void* stream) {
+  pint_batch_plan plan = nullptr;
+  int rc = pint_batch_plan_create(ctx, njobs, jobs, o, cluster_ctas, cta_threads, &plan, stream);
+  if (rc != PINT_OK) return rc;
+  rc = pint_batch_plan_run(plan, stats, stream);
+  const std::string err = ctx->err;
+  pint_batch_plan_destroy(plan);
+  ctx->err = err;
+  return rc;
+}
+
 // Cluster size pint_solve_batch picks for cluster_ctas = 0 (exposed for the
 // tuner and the tests).
 extern "C" int pint_batch_auto_cluster(pint_ctx ctx, int njobs, int64_t min_n) {
   if (!ctx || njobs < 1) return 0;
   return auto_cluster(ctx->num_sms, njobs, min_n);
+}
+
+// CTA width pint_solve_batch picks for cta_threads = 0.
+extern "C" int pint_batch_auto_threads(pint_ctx ctx, int njobs, int cluster_ctas) {
+  if (!ctx || njobs < 1 || cluster_ctas < 1) return 0;
+  return auto_threads(ctx->num_sms, njobs, cluster_ctas);
 }

@@ -183,3 +183,22 @@ def request_stream(seed: int, count: int, rate: float, grids=(32, 48, 64, 96, 12
                     "precision": precisions[min(int(u[4 * i + 3] * len(precisions)),
                                                 len(precisions) - 1)]})
     return out
+
+
+def batch_jobs(seed: int, count: int, grids2d=(32, 48, 64), grids3d=(16, 24, 32),
+               widths=(2, 4, 8, 16)) -> list:
+    """Seeded mix of small slab solves for one batched launch: half 2-D
+    (n x n cells), half 3-D (n^3), grid and block width s drawn uniformly.
+    Returns dicts {jid, dims, s, seed_coef, seed_rhs}; each job's diffusion
+    field is log-normal iid from seed_coef, its right-hand side U[-1,1] from
+    seed_rhs."""
+    u = 0.5 * (uniform(seed, 3 * count) + 1.0)          # [0, 1)
+    out = []
+    for i in range(count):
+        three = u[3 * i] >= 0.5
+        g = grids3d if three else grids2d
+        n = int(g[min(int(u[3 * i + 1] * len(g)), len(g) - 1)])
+        s = int(widths[min(int(u[3 * i + 2] * len(widths)), len(widths) - 1)])
+        out.append({"jid": i, "dims": (n, n, n) if three else (n, n, 1), "s": s,
+                    "seed_coef": 1000 + 2 * i, "seed_rhs": 1001 + 2 * i})
+    return out

@@ -59,24 +59,26 @@ def _opts(P, tol, pc="jacobi"):
     return o
 
 
-def _run(P, ctx, jobs, o, cluster, idx=None):
+def _run(P, ctx, jobs, o, cluster, idx=None, threads=0):
     import torch
     idx = range(len(jobs)) if idx is None else idx
     Ys = {i: torch.zeros(jobs[i]["n"], jobs[i]["s"], device="cuda", dtype=torch.float64)
           for i in idx}
     Bs = {i: _dev(jobs[i]["B"]) for i in idx}
     sts = P.pint_solve_batch(ctx, [(jobs[i]["op"], Bs[i], None, Ys[i]) for i in idx], o,
-                             cluster_ctas=cluster)
+                             cluster_ctas=cluster, cta_threads=threads)
     return {i: Ys[i].cpu().numpy() for i in idx}, dict(zip(idx, sts))
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4, 16])
-def test_batch_equals_sequential_stepping(P, ctx, cluster):
+@pytest.mark.parametrize("cluster,threads", [(1, 512), (1, 256), (1, 128), (2, 512),
+                                             (4, 256), (16, 512)])
+def test_batch_equals_sequential_stepping(P, ctx, cluster, threads):
     """Every job of one launch equals sequential implicit Euler to 1e-10 per
-    column (both at relative residual 1e-13), for several cluster sizes."""
+    column (both at relative residual 1e-13), for several cluster sizes and
+    CTA widths."""
     jobs = _make(P, ctx, JOBS)
     try:
-        Y, st = _run(P, ctx, jobs, _opts(P, 1e-13), cluster)
+        Y, st = _run(P, ctx, jobs, _opts(P, 1e-13), cluster, threads=threads)
         for i, j in enumerate(jobs):
             assert st[i].status == P.PINT_OK, (i, st[i].as_dict(j["s"]))
             assert st[i].kernel_launches == 1
@@ -133,16 +135,17 @@ def test_batch_meets_tol_in_oracle_residual_and_matches_solo(P, ctx, cluster):
         _free(P, jobs)
 
 
-@pytest.mark.parametrize("cluster", [1, 4])
-def test_batch_alone_equals_in_mix_bitwise(P, ctx, cluster):
+@pytest.mark.parametrize("cluster,threads", [(1, 256), (4, 512)])
+def test_batch_alone_equals_in_mix_bitwise(P, ctx, cluster, threads):
     """A job's result and iteration counts do not depend on the other jobs of
-    the launch: each job alone gives bitwise the Y it gets in the mix."""
+    the launch: each job alone gives bitwise the Y it gets in the mix (same
+    cluster size and CTA width)."""
     jobs = _make(P, ctx, JOBS, seed0=110)
     try:
         o = _opts(P, 1e-10)
-        Ymix, smix = _run(P, ctx, jobs, o, cluster)
+        Ymix, smix = _run(P, ctx, jobs, o, cluster, threads=threads)
         for i in range(len(jobs)):
-            Y1, s1 = _run(P, ctx, jobs, o, cluster, idx=[i])
+            Y1, s1 = _run(P, ctx, jobs, o, cluster, idx=[i], threads=threads)
             assert np.array_equal(Y1[i], Ymix[i]), i
             assert (s1[i].inner_its, s1[i].outer_its) == (smix[i].inner_its, smix[i].outer_its)
     finally:
@@ -207,18 +210,25 @@ def test_batch_zero_rhs_nonconvergence_and_invalid_arguments(P, ctx):
         bad = []
         o2 = _opts(P, 1e-10)
         o2.precision = P.PINT_FP32
-        bad.append((o2, 0))
+        bad.append((o2, 0, 0))
         o3 = _opts(P, 1e-10)
         o3.precond = P.PINT_PC_ILU0
-        bad.append((o3, 0))
-        bad.append((_opts(P, 1e-10), 17))
-        bad.append((_opts(P, 1e-10), -1))
-        for ob, c in bad:
+        bad.append((o3, 0, 0))
+        bad.append((_opts(P, 1e-10), 17, 0))
+        bad.append((_opts(P, 1e-10), -1, 0))
+        bad.append((_opts(P, 1e-10), 1, 384))
+        o4 = _opts(P, 1e-10)
+        o4.restart = 40                        # at most 32 in the batched solver
+        bad.append((o4, 1, 0))
+        for ob, c, t in bad:
             with pytest.raises(P.PintError) as ei:
-                P.pint_solve_batch(ctx, [(j0["op"], None, None, Y0)], ob, cluster_ctas=c)
+                P.pint_solve_batch(ctx, [(j0["op"], None, None, Y0)], ob, cluster_ctas=c,
+                                   cta_threads=t)
             assert ei.value.code == P.PINT_ERR_INVALID
-        assert P.pint_batch_auto_cluster(ctx, 1, 4096) >= 2
+        assert P.pint_batch_auto_cluster(ctx, 1, 4096) == 16
         assert P.pint_batch_auto_cluster(ctx, 10000, 4096) == 1
+        assert P.pint_batch_auto_threads(ctx, 10000, 1) == 512
+        assert P.pint_batch_auto_threads(ctx, 1, 16) == 256
     finally:
         _free(P, jobs)
 
@@ -259,3 +269,55 @@ def test_batch_c1_size_against_oracle(P, ctx):
                 assert abs(st[q].inner_its - info["inner"]) <= 1 + info["cycles"]
     finally:
         P.pint_operator_destroy(op)
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 512), (16, 256)])
+def test_batch_plan_replays_the_captured_graph(P, ctx, cluster, threads):
+    """The resident plan (descriptors, workspace and a captured CUDA graph made
+    once): a replay gives bitwise the result of the first run and of the
+    one-shot pint_solve_batch with the same shape; new right-hand sides written
+    into the same buffers are solved on the next replay (each equals
+    sequential stepping); the plan reports the launch shape it took."""
+    import torch
+    jobs = _make(P, ctx, JOBS[:4], seed0=190)
+    try:
+        o = _opts(P, 1e-13)
+        Ys = [torch.zeros(j["n"], j["s"], device="cuda", dtype=torch.float64) for j in jobs]
+        Bs = [_dev(j["B"]) for j in jobs]
+        plan = P.BatchPlan(ctx, [(j["op"], Bs[q], None, Ys[q]) for q, j in enumerate(jobs)], o,
+                           cluster_ctas=cluster, cta_threads=threads)
+        try:
+            sh = plan.shape()
+            assert (sh["cluster_ctas"], sh["cta_threads"]) == (cluster, threads)
+            assert 1 <= sh["resident_clusters"] <= len(jobs)
+            st1 = plan.run(raise_on_nonconvergence=True)
+            Y1 = [y.cpu().numpy() for y in Ys]
+            for y in Ys:
+                y.zero_()
+            st2 = plan.run(raise_on_nonconvergence=True)
+            for q in range(len(jobs)):
+                assert np.array_equal(Ys[q].cpu().numpy(), Y1[q])
+                assert st1[q].inner_its == st2[q].inner_its
+            Yo, _ = _run(P, ctx, jobs, o, cluster, threads=threads)
+            for q in range(len(jobs)):
+                assert np.array_equal(Yo[q], Y1[q])
+            # new right-hand sides in the same device buffers
+            newB = [synth.uniform(200 + q, j["n"] * j["s"]).reshape(j["n"], j["s"])
+                    for q, j in enumerate(jobs)]
+            for q in range(len(jobs)):
+                Bs[q].copy_(torch.as_tensor(newB[q]))
+                Ys[q].zero_()
+            plan.run(raise_on_nonconvergence=True)
+            for q, j in enumerate(jobs):
+                Yref = slab.sequential_dirk_linear(j["K"], np.ones(j["n"]), j["A"], TAU,
+                                                   np.zeros(j["n"]), newB[q])
+                assert np.all(_colerr(Ys[q].cpu().numpy(), Yref) < 1e-10), q
+        finally:
+            plan.close()
+        with pytest.raises(P.PintError) as ei:
+            o2 = _opts(P, 1e-10)
+            o2.precond = P.PINT_PC_ILU0
+            P.BatchPlan(ctx, [(jobs[0]["op"], Bs[0], None, Ys[0])], o2)
+        assert ei.value.code == P.PINT_ERR_INVALID
+    finally:
+        _free(P, jobs)

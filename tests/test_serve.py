@@ -79,3 +79,71 @@ def test_failing_solve_does_not_stop_the_server():
     summ = serve.SlabServer(slots=2, hbm_budget=1 << 40, solve=solve).run(reqs)
     assert summ["completed"] == 4 and summ["failed"] == 1
     assert reqs[1].error.startswith("planted")
+
+
+def _lane_requests(k, spread):
+    out = []
+    for i in range(k):
+        small = i % 3 != 2
+        n = 8 if small else 40
+        out.append(serve.SlabRequest(rid=i, arrival=spread * i, dims=(n, n, n), s=4,
+                                     precision="fp64" if i % 4 != 3 else "fp32"))
+    return out
+
+
+def test_batch_lane_takes_small_fp64_requests_in_batches():
+    """Small float64 requests need no slot: each is solved exactly once by the
+    lane, several per launch when they queue up while a batch runs; the rest
+    go through the slots; FIFO admission and the memory budget still hold."""
+    calls, lock = [], threading.Lock()
+
+    def solve_batch(rs):
+        with lock:
+            calls.append([r.rid for r in rs])
+        time.sleep(0.05)
+        return [{"status": 0, "outer": 1, "inner": 3} for _ in rs]
+
+    reqs = _lane_requests(30, 0.004)
+    srv = serve.SlabServer(slots=2, hbm_budget=1 << 40, solve=_fake([], 0.02), batch_lane=True,
+                           batch_max_unknowns=8 ** 3 * 4, solve_batch=solve_batch)
+    summ = srv.run(reqs)
+    assert summ["completed"] == 30 and summ["failed"] == 0
+    lane = [r for r in reqs if srv.batchable(r)]
+    assert lane and all(r.slot == "batch" for r in lane)
+    assert all(r.slot in (0, 1) for r in reqs if not srv.batchable(r))
+    solved = sorted(x for c in calls for x in c)
+    assert solved == sorted(r.rid for r in lane)                 # each exactly once
+    assert summ["batch_launches"] == len(calls) < len(lane)      # batched
+    assert summ["max_batch"] >= 2
+    adm = [r.admitted for r in sorted(reqs, key=lambda r: r.arrival)]
+    assert adm == sorted(adm)
+    # a lane request is never larger than the threshold or float32
+    assert all(r.cells * r.s <= 8 ** 3 * 4 and r.precision == "fp64" for r in lane)
+
+
+def test_batch_lane_failure_marks_its_requests_and_the_server_goes_on():
+    def solve_batch(rs):
+        raise RuntimeError("planted batch failure")
+    reqs = _lane_requests(9, 0.0)
+    srv = serve.SlabServer(slots=2, hbm_budget=1 << 40, solve=_fake([], 0.01), batch_lane=True,
+                           batch_max_unknowns=8 ** 3 * 4, solve_batch=solve_batch)
+    summ = srv.run(reqs)
+    lane = [r for r in reqs if srv.batchable(r)]
+    assert summ["failed"] == len(lane) and summ["completed"] == 9 - len(lane)
+    assert all(r.status == -1 and "planted" in r.error for r in lane)
+
+
+def test_batch_lane_respects_the_memory_budget():
+    reqs = _lane_requests(12, 0.0)
+    srv0 = serve.SlabServer(slots=4, hbm_budget=1 << 40, solve=_fake([]), batch_lane=True,
+                            batch_max_unknowns=8 ** 3 * 4, solve_batch=lambda rs: [{}] * len(rs))
+    need = max(srv0.need_bytes(r) for r in reqs)
+    budget = int(2.5 * need)
+
+    def solve_batch(rs):
+        time.sleep(0.02)
+        return [{"status": 0} for _ in rs]
+    srv = serve.SlabServer(slots=4, hbm_budget=budget, solve=_fake([], 0.02), batch_lane=True,
+                           batch_max_unknowns=8 ** 3 * 4, solve_batch=solve_batch)
+    summ = srv.run(reqs)
+    assert summ["completed"] == 12 and summ["peak_reserved_bytes"] <= budget
