@@ -53,7 +53,7 @@ WORKLOADS = {
                   "steps (Algorithm 1), Newton + {solver}+{pc}"),
     "richards": (96, 8, "ilu0", "fp32",
                  "3-D Richards {n}^3, van Genuchten alpha=1 n=2, K_S=exp(2g) correlated 8 "
-                 "cells, implicit Euler tau=1/96 window s=8 pipelined over 8 steps, L-scheme + "
+                 "cells, implicit Euler tau=1/96 window s=8 pipelined over 8 steps, {lin} + "
                  "{solver}+{pc}"),
     "batch": (64, 16, "jacobi", "fp64",
               "batched persistent solve: {requests} slabs in one launch (captured CUDA graph), "
@@ -85,7 +85,11 @@ def parse(argv=None):
                         "bicgstab: the paper's solver for the linear convection-diffusion "
                         "problem; global: global GMRES on the unsplit operator; batch: the "
                         "same method in the persistent batched kernel, one cluster per slab)")
+    p.add_argument("--linearisation", default="lscheme", choices=["lscheme", "newton"],
+                   help="richards: the L-scheme of Sec. 4.3 (L = sup theta') or Newton")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-other", action="store_true",
+                   help="convdiff3d: skip the compact legs of the other configurations")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true",
                    help="skip the pure-FP64 run of the same workload")
@@ -95,6 +99,10 @@ def parse(argv=None):
                    help="serve: requests in the stream; batch: slabs in the launch")
     p.add_argument("--rate", type=float, default=8.0, help="serve: mean arrivals per second")
     p.add_argument("--slots", type=int, default=4, help="serve: concurrent solves")
+    p.add_argument("--batch-cluster", type=int, default=0,
+                   help="batched kernel: CTAs per cluster (0 = the library's choice)")
+    p.add_argument("--batch-threads", type=int, default=0,
+                   help="batched kernel: threads per CTA (0 = the library's choice)")
     p.add_argument("--no-batch-lane", action="store_true",
                    help="serve: solve the small float64 requests in the slots as well, "
                         "not in batched launches")
@@ -466,7 +474,9 @@ class LinearCase:
         self.nnz = int(P.pint_operator_nnz(self.op))
         self.plan = None
         if args.solver == "batch":        # one slab, one cluster, a captured graph
-            self.plan = P.BatchPlan(ctx, [(self.op, self.Bd, None, self.Y)], o)
+            self.plan = P.BatchPlan(ctx, [(self.op, self.Bd, None, self.Y)], o,
+                                    cluster_ctas=args.batch_cluster,
+                                    cta_threads=args.batch_threads)
 
     def step(self):
         self.Y.zero_()
@@ -554,7 +564,8 @@ class BatchCase:
         o.precision = P.PINT_FP64
         o.restart = args.restart
         self.o = o
-        self.plan = P.BatchPlan(ctx, views, o)
+        self.plan = P.BatchPlan(ctx, views, o, cluster_ctas=args.batch_cluster,
+                                cta_threads=args.batch_threads)
         self.n, self.time_steps, self.s = total, 1, max(j["s"] for j in self.jobs)
 
     def step(self):
@@ -625,7 +636,7 @@ class PipelineCase:
             y0 = -np.broadcast_to(z[:, None, None], (n, n, n)).ravel().copy()
             self.time_steps = self.G
             self.max_step = 1.0
-            self.lscheme = -1.0
+            self.lscheme = 0.0 if args.linearisation == "newton" else -1.0
         self.n = int(np.prod(dims))
         self.y0 = y0
         self.y0d = torch.tensor(y0, device="cuda", dtype=torch.float64)
@@ -698,8 +709,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     desc = WORKLOADS[args.workload][4].format(n=args.n, pc=args.precond,
-                                             solver=solver_label(args), requests=args.requests)
+                                             solver=solver_label(args), requests=args.requests,
+                                             lin="Newton" if args.linearisation == "newton"
+                                             else "L-scheme")
     wl_name = f"{args.workload}_n{args.n}_s{args.s}_{args.precond}"
+    if args.workload == "richards" and args.linearisation == "newton":
+        wl_name += "_newton"
     if args.workload == "batch":
         wl_name = f"batch_{args.requests}slabs_jacobi"
     elif args.solver == "batch":
@@ -883,11 +898,64 @@ def main():
     if not args.no_sweep and args.workload == "convdiff3d" and args.solver != "global":
         out["sweep"] = sweep(P, ctx, args, case.w, fp64_peak)
         out["sweep_summary"] = sweep_summary(out["sweep"])
+    if not args.no_other and args.workload == "convdiff3d":
+        out["other_configs"] = other_configs(P, ctx, fp64_peak, max(2, min(args.steps, 5)))
     print(json.dumps(out), flush=True)
     case.close()
     P.pint_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def other_configs(P, ctx, fp64_peak, steps):
+    """Compact legs of the other configurations, measured in the same run as
+    the headline (each: set-up and one warm-up untimed, then `steps` timed
+    steps with CUDA events): the 64 x 64 slab through the batched kernel (one
+    cluster), 512 uneven slabs in one batched launch, and the 512^2
+    diffusion-reaction run of Algorithm 1."""
+    import torch
+    legs = {
+        "convdiff2d_64_s4_batch_kernel": ["--workload", "convdiff2d", "--solver", "batch"],
+        "batch_512_slabs": ["--workload", "batch", "--requests", "512"],
+        "diffreact_512_fp32": ["--workload", "diffreact"],
+    }
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, argv in legs.items():
+        case = None
+        try:
+            a = parse(argv + ["--steps", str(steps)])
+            if a.workload == "batch":
+                case = BatchCase(P, ctx, a)
+            elif linear(a):
+                case = LinearCase(P, ctx, a)
+            else:
+                case = PipelineCase(P, ctx, a)
+            case.step()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sts = [case.step().as_dict(case.s) for _ in range(steps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            d = {"value": case.time_steps * case.n / (ms / 1e3), "unit": UNIT,
+                 "ms_per_step": ms, "steps": steps, "precision": a.precision,
+                 "solver": solver_label(a), "precond": a.precond,
+                 "converged": all(x["status"] == 0 for x in sts),
+                 "max_col_relres": max(max(x["col_relres"]) for x in sts),
+                 "inner": sts[-1]["inner_its"]}
+            if a.solver == "batch":
+                d["roofline"] = batch_roofline(sts, ms, fp64_peak)
+                d["launch_shape"] = case.plan.shape()
+            out[name] = d
+        except Exception as e:          # report, do not hide
+            out[name] = {"value": None, "error": str(e)[:300]}
+        finally:
+            if case is not None:
+                case.close()
+    return out
 
 
 def batch_roofline(stats, ms_per_step, fp64_peak):

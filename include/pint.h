@@ -268,10 +268,11 @@ int pint_batch_plan_shape(pint_batch_plan plan, int* cluster_ctas, int* cta_thre
                           int* resident_clusters);
 int pint_batch_plan_destroy(pint_batch_plan plan);
 
-/* The cluster size pint_solve_batch takes for cluster_ctas = 0: 1 when the
- * jobs alone occupy every SM, else the largest power of two up to 16 with
- * njobs * C <= SMs and at least 256 rows per CTA in the smallest job. */
-int pint_batch_auto_cluster(pint_ctx ctx, int njobs, int64_t min_n);
+/* The cluster size pint_solve_batch takes for cluster_ctas = 0: C doubles
+ * from 1 (up to 16) while the largest job's N s / C exceeds the batch's total
+ * N s per SM and the largest job keeps at least 256 rows per CTA. 0 when a
+ * job has no operator or coupling. */
+int pint_batch_auto_cluster(pint_ctx ctx, int njobs, const pint_batch_job* jobs);
 
 /* The CTA width pint_solve_batch takes for cta_threads = 0 with clusters of
  * cluster_ctas CTAs: 256 for clusters of 16, else 512. */

@@ -93,7 +93,7 @@ _SIGS = {
     "pint_batch_plan_run": (_i, [_vp, C.POINTER(pint_stats), _vp]),
     "pint_batch_plan_shape": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
     "pint_batch_plan_destroy": (_i, [_vp]),
-    "pint_batch_auto_cluster": (_i, [_vp, _i, _i64]),
+    "pint_batch_auto_cluster": (_i, [_vp, _i, C.POINTER(pint_batch_job)]),
     "pint_batch_auto_threads": (_i, [_vp, _i, _i]),
     "pint_shift": (_i, [_vp, _i64, _i, _vp]),
     "pint_problem_create": (_i, [_vp, C.POINTER(_vp), _i, _i, _i, _i, _vp, _vp, _vp]),
@@ -330,8 +330,9 @@ class BatchPlan:
             self.h = None
 
 
-def pint_batch_auto_cluster(ctx, njobs, min_n):
-    return lib.pint_batch_auto_cluster(ctx, int(njobs), int(min_n))
+def pint_batch_auto_cluster(ctx, jobs):
+    """jobs: sequence of (op, B, B0, Y) as for pint_solve_batch."""
+    return lib.pint_batch_auto_cluster(ctx, len(jobs), _batch_jobs(jobs))
 
 
 def pint_batch_auto_threads(ctx, njobs, cluster_ctas):

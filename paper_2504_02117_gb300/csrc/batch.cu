@@ -48,7 +48,7 @@ namespace pint {
 struct BatchJob {
   int64_t n, nnz;
   int s;
-  int pad_;
+  int orig;                 // the caller's index of this job (its output slot)
   const int* rowptr;        // CSR of K (device)
   const int* colind;
   const double* Kval;
@@ -114,9 +114,10 @@ __device__ __noinline__ void coupled_rows(int64_t r0, int64_t r1, const int* __r
                                           const int* __restrict__ colind,
                                           const double* __restrict__ Kv,
                                           const double* __restrict__ dg, const CplLists& L,
-                                          const double* X, const double* __restrict__ B,
-                                          const double* __restrict__ B0, double* out,
-                                          double* xs) {
+                                          const double* __restrict__ X,
+                                          const double* __restrict__ B,
+                                          const double* __restrict__ B0,
+                                          double* __restrict__ out, double* xs) {
   const int T = blockDim.x;
   double* xt = xs + threadIdx.x;
   for (int64_t r = r0 + threadIdx.x; r < r1; r += T) {
@@ -254,6 +255,41 @@ __device__ __forceinline__ void dots_chunk(const double* P, int64_t ns, const do
   const double v = warp_sum_multi<NV>(a);
   constexpr int per = 32 / NV;
   if (lane % per == 0) red2[(i0 + lane / per) * NW + warp] = v;
+}
+
+// One modified Gram-Schmidt sweep over the elements [e0, e1) of this CTA:
+// W <- W - h Vi, returning this thread's partial of <Vn, W> for the updated W
+// (Vn != nullptr) or of ||W||^2. Four elements per round with all loads
+// issued before the stores (the three blocks never overlap), so a thread
+// keeps twelve loads in flight instead of three.
+__device__ __forceinline__ double mgs_sweep(const double* __restrict__ Vi,
+                                            const double* __restrict__ Vn,
+                                            double* __restrict__ W, double h, int64_t e0,
+                                            int64_t e1) {
+  const int T = blockDim.x;
+  double a = 0.0;
+  int64_t e = e0 + threadIdx.x;
+  for (; e + 3 * (int64_t)T < e1; e += 4 * (int64_t)T) {
+    double v[4], w[4], q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u] = Vi[e + u * T];
+      w[u] = W[e + u * T];
+      q[u] = Vn ? Vn[e + u * T] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      w[u] = fma(-h, v[u], w[u]);
+      W[e + u * T] = w[u];
+      a = fma(Vn ? q[u] : w[u], w[u], a);
+    }
+  }
+  for (; e < e1; e += T) {
+    const double w = fma(-h, Vi[e], W[e]);
+    W[e] = w;
+    a = fma(Vn ? Vn[e] : w, w, a);
+  }
+  return a;
 }
 
 // Products <V_i, W> for i = 0..j in chunks of 8, 4, 2, 1.
@@ -458,21 +494,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
             const double h = res[0];
             if (tid == 0) H[i * m + j] = h;
             const double* Vi = V + (size_t)i * ns;
-            a = 0.0;
-            if (i < j) {
-              const double* Vn = Vi + ns;
-              for (int64_t e = e0 + tid; e < e1; e += T) {
-                const double w = fma(-h, Vi[e], W[e]);
-                W[e] = w;
-                a = fma(Vn[e], w, a);
-              }
-            } else {
-              for (int64_t e = e0 + tid; e < e1; e += T) {
-                const double w = fma(-h, Vi[e], W[e]);
-                W[e] = w;
-                a = fma(w, w, a);
-              }
-            }
+            a = mgs_sweep(Vi, i < j ? Vi + ns : nullptr, W, h, e0, e1);
           }
           a = warp_sum(a);
           if (lane == 0) red2[warp] = a;
@@ -561,7 +583,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
       }
     }
     if (rank == 0 && tid == 0) {
-      BatchOut* o = outs + jb;
+      BatchOut* o = outs + J.orig;
       o->status = status;
       o->outer = outer;
       o->inner = inner;
@@ -580,12 +602,24 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
 
 namespace {
 
-// 1 when the jobs alone fill the GPU; else the largest power of two up to 16
-// with one CTA per SM and at least 256 rows per CTA in the smallest job
-int auto_cluster(int num_sms, int njobs, int64_t min_n) {
-  for (int c = 16; c >= 2; c /= 2)
-    if ((int64_t)njobs * c <= num_sms && min_n / c >= 256) return c;
-  return 1;
+// Cluster size for a batch: double C (from 1, up to 16) while the largest
+// job's N s per CTA exceeds the batch's total N s per SM (that job would set
+// the launch's finishing time) and the largest job keeps at least 256 rows
+// per CTA. Measured on 512 uneven slabs (2-D 32^2-64^2, 3-D 16^3-32^3,
+// s = 2..16): C = 1, 2, 4, 8 gave 2.7, 3.4, 4.7, 3.9 x 10^7 time-step DOF/s,
+// and this rule takes 4; on 608 copies of one 64 x 64 s = 4 slab it takes 1.
+int auto_cluster(int num_sms, int njobs, const pint_batch_job* jobs) {
+  int64_t total = 0, wmax = 0, nmax = 0;
+  for (int i = 0; i < njobs; ++i) {
+    const int64_t w = jobs[i].op->n * jobs[i].op->s;
+    total += w;
+    wmax = std::max(wmax, w);
+    nmax = std::max<int64_t>(nmax, jobs[i].op->n);
+  }
+  const int64_t per_sm = total / std::max(1, num_sms);
+  int C = 1;
+  while (C < 16 && wmax / C > per_sm && nmax / (2 * C) >= 256) C *= 2;
+  return C;
 }
 
 // 512 threads (one CTA per SM), 256 for clusters of 16: measured on the 64 x 64
@@ -713,7 +747,7 @@ void plan_build(pint_batch_plan p, int njobs, const pint_batch_job* jobs, int cl
   const int m = o->restart;
   p->njobs = njobs;
   p->m = m;
-  int64_t max_work = 1, max_n = 1, min_n = INT64_MAX, ncpl = 0;
+  int64_t max_work = 1, max_n = 1, ncpl = 0;
   int smax = 1;
   for (int i = 0; i < njobs; ++i) {
     pint_op op = jobs[i].op;
@@ -724,11 +758,10 @@ void plan_build(pint_batch_plan p, int njobs, const pint_batch_job* jobs, int cl
     if (!op->j_valid) build_inner(op, st);
     max_work = std::max<int64_t>(max_work, batch_work_doubles(m, op->n, op->s, op->nnz));
     max_n = std::max<int64_t>(max_n, op->n);
-    min_n = std::min<int64_t>(min_n, op->n);
     smax = std::max(smax, op->s);
     ncpl += 2 * op->s * op->s;
   }
-  p->C = cluster_ctas ? cluster_ctas : auto_cluster(ctx->num_sms, njobs, min_n);
+  p->C = cluster_ctas ? cluster_ctas : auto_cluster(ctx->num_sms, njobs, jobs);
   p->NT = cta_threads ? cta_threads : auto_threads(ctx->num_sms, njobs, p->C);
   p->smem = sizeof(double) * batch_smem_doubles(m, smax, p->NT);
   int ncl = p->NT == 128   ? slab_queue_clusters<128>(p->C, p->smem, ctx->num_sms, st)
@@ -750,10 +783,19 @@ void plan_build(pint_batch_plan p, int njobs, const pint_batch_job* jobs, int cl
     PINT_CUDA(cudaMemcpyAsync(p->d_ones, ones.data(), sizeof(double) * max_n,
                               cudaMemcpyHostToDevice, st));
   }
+  // the device queue holds the jobs largest first (N s, then the caller's
+  // order): the last jobs a cluster takes are the short ones, which evens out
+  // the clusters' finishing times (longest-processing-time-first)
+  std::vector<int> order(njobs);
+  for (int i = 0; i < njobs; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return jobs[a].op->n * jobs[a].op->s > jobs[b].op->n * jobs[b].op->s;
+  });
   std::vector<double> hcpl((size_t)ncpl);
   std::vector<BatchJob> hj(njobs);
   int64_t off = 0;
-  for (int i = 0; i < njobs; ++i) {
+  for (int q = 0; q < njobs; ++q) {
+    const int i = order[q];
     pint_op op = jobs[i].op;
     const int s = op->s;
     for (int a = 0; a < s; ++a)
@@ -761,11 +803,11 @@ void plan_build(pint_batch_plan p, int njobs, const pint_batch_job* jobs, int cl
         hcpl[off + a * s + b] = op->A1[a * kMaxS + b];
         hcpl[off + s * s + a * s + b] = op->A2[a * kMaxS + b];
       }
-    BatchJob& J = hj[i];
+    BatchJob& J = hj[q];
     J.n = op->n;
     J.nnz = op->nnz;
     J.s = s;
-    J.pad_ = 0;
+    J.orig = i;
     J.rowptr = op->rowptr;
     J.colind = op->colind;
     J.Kval = op->Kval;
@@ -909,9 +951,11 @@ extern "C" int pint_solve_batch(pint_ctx ctx, int njobs, const pint_batch_job* j
 
 // Cluster size pint_solve_batch picks for cluster_ctas = 0 (exposed for the
 // tuner and the tests).
-extern "C" int pint_batch_auto_cluster(pint_ctx ctx, int njobs, int64_t min_n) {
-  if (!ctx || njobs < 1) return 0;
-  return auto_cluster(ctx->num_sms, njobs, min_n);
+extern "C" int pint_batch_auto_cluster(pint_ctx ctx, int njobs, const pint_batch_job* jobs) {
+  if (!ctx || njobs < 1 || !jobs) return 0;
+  for (int i = 0; i < njobs; ++i)
+    if (!jobs[i].op || jobs[i].op->s < 1) return 0;
+  return auto_cluster(ctx->num_sms, njobs, jobs);
 }
 
 // CTA width pint_solve_batch picks for cta_threads = 0.

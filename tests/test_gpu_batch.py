@@ -225,8 +225,8 @@ def test_batch_zero_rhs_nonconvergence_and_invalid_arguments(P, ctx):
                 P.pint_solve_batch(ctx, [(j0["op"], None, None, Y0)], ob, cluster_ctas=c,
                                    cta_threads=t)
             assert ei.value.code == P.PINT_ERR_INVALID
-        assert P.pint_batch_auto_cluster(ctx, 1, 4096) == 16
-        assert P.pint_batch_auto_cluster(ctx, 10000, 4096) == 1
+        assert P.pint_batch_auto_cluster(ctx, [(j1["op"], None, None, Y1)]) == 2   # 720 rows
+        assert P.pint_batch_auto_cluster(ctx, [(j0["op"], None, None, Y0)] * 500) == 1
         assert P.pint_batch_auto_threads(ctx, 10000, 1) == 512
         assert P.pint_batch_auto_threads(ctx, 1, 16) == 256
     finally:
@@ -255,7 +255,9 @@ def test_batch_c1_size_against_oracle(P, ctx):
             dB = [_dev(b) for b in Bs]
             st = P.pint_solve_batch(ctx, [(op, dB[q], None, Ys[q]) for q in range(copies)],
                                     _opts(P, 1e-10), raise_on_nonconvergence=True)
-            cl = P.pint_batch_auto_cluster(ctx, copies, n)
+            cl = P.pint_batch_auto_cluster(ctx, [(op, dB[q], None, Ys[q])
+                                                 for q in range(copies)])
+            assert cl == (16 if copies == 1 else 8)
             for q in (0, copies - 1):
                 Y = Ys[q].cpu().numpy()
                 R = slab.coupled_residual(K, np.ones(n), A1, A2, Y, B=Bs[q])
