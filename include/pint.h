@@ -352,9 +352,39 @@ enum {
   PINT_K_NL,          /* nonlinear pointwise, Jacobian and single-column eval */
   PINT_K_COUNT
 };
-/* Turn event timing on (1) or off (0). Launch, byte and flop counts are
- * always kept. */
+/* Profiler flags: bit 0 = CUDA-event timing per kernel family, bit 1 = an
+ * NVTX range named after the family ("coupled", "spmm", "gram", "update",
+ * "cholqr", "hess", "ilu", "norm", "vec", "nl") around each of its launches
+ * (for ncu --nvtx filtering; free when no tool is attached). 0 turns both
+ * off. Launch, byte and flop counts are always kept. Values outside 0..3:
+ * PINT_ERR_INVALID. */
 int pint_profile_enable(pint_ctx ctx, int on);
+
+/* Per-column residual history of the last pint_solve_block (one row per
+ * outer iteration: ||R_k|| / ||F_k||, k = 0..s-1, the quantity the paper
+ * plots per step in Sec. 4) or pint_pipeline_run (one row per Newton /
+ * L-scheme iteration of the window); pint_newton_step appends a row per
+ * call. `out` (host, may be NULL) receives min(rows, max_rows) rows of s
+ * doubles, row-major; *rows and *s (may be NULL) the recorded row count
+ * and width. Up to 4 Mi values are kept. The batched solver keeps none. */
+int pint_residual_history(pint_ctx ctx, double* out, int max_rows, int* rows, int* s);
+int pint_residual_history_reset(pint_ctx ctx);
+
+/* Checked build (libpint_bounds.so, -DPINT_BOUNDS): every matrix column
+ * index a kernel gathers through (the coupled residual, the SELL SpMM, the
+ * batched solver's operator rows) is checked against the row count before
+ * use; a bad index is counted, the first is recorded and its access is
+ * skipped. pint_bounds_report waits for the device and returns, since the
+ * last report, the count and the first record (site 1 coupled residual, 2
+ * SELL SpMM, 3 batched operator rows, 99 pint_test_bounds; the index and its
+ * bound), then clears them. In the normal build *count = -1. Any output
+ * pointer may be NULL. */
+int pint_bounds_report(pint_ctx ctx, long long* count, int* site, long long* index,
+                       long long* bound);
+/* Test entry of the checked build: evaluates one check of `index` against
+ * `bound` on the device (site 99). Nothing is accessed through the index in
+ * either build; in the checked build a failing check is recorded. */
+int pint_test_bounds(pint_ctx ctx, long long index, long long bound);
 /* Synchronizes the device, folds finished event pairs into the totals and
  * returns family `k`'s totals since the last reset (any pointer may be
  * NULL). */

@@ -12,7 +12,9 @@ import ctypes as C
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpint.so")
+# PINT_LIB may name the checked build (libpint_bounds.so) or another build
+# of the same library; the default is the in-tree libpint.so
+LIB_PATH = os.environ.get("PINT_LIB") or os.path.join(_HERE, "libpint.so")
 
 PINT_OK = 0
 PINT_ERR_INVALID = 1
@@ -110,6 +112,11 @@ _SIGS = {
     "pint_profile_read": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d),
                                C.POINTER(C.c_longlong)]),
     "pint_profile_reset": (_i, [_vp]),
+    "pint_residual_history": (_i, [_vp, _vp, _i, C.POINTER(_i), C.POINTER(_i)]),
+    "pint_residual_history_reset": (_i, [_vp]),
+    "pint_bounds_report": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(_i),
+                                C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "pint_test_bounds": (_i, [_vp, C.c_longlong, C.c_longlong]),
     "pint_kernel_launches": (C.c_longlong, [_vp]),
     "pint_inner_apply": (_i, [_vp, _vp, _vp, _vp]),
     "pint_inner_apply_lowp": (_i, [_vp, _i, _vp, _vp, _vp]),
@@ -454,8 +461,10 @@ def pint_fp64_fma_peak(ctx):
     return v.value
 
 
-def pint_profile_enable(ctx, on=True):
-    _check(lib.pint_profile_enable(ctx, int(bool(on))), ctx)
+def pint_profile_enable(ctx, on=True, nvtx=False):
+    """on: CUDA-event timing per kernel family; nvtx: an NVTX range per
+    family launch."""
+    _check(lib.pint_profile_enable(ctx, int(bool(on)) | (2 if nvtx else 0)), ctx)
 
 
 def pint_profile_read(ctx, k):
@@ -471,3 +480,32 @@ def pint_profile_reset(ctx):
 
 def pint_kernel_launches(ctx):
     return lib.pint_kernel_launches(ctx)
+
+
+def pint_residual_history(ctx):
+    """The last solve's per-column relative residuals: a (rows, s) numpy
+    array, one row per outer (or Newton) iteration."""
+    import numpy as np
+    rows, s = C.c_int(), C.c_int()
+    _check(lib.pint_residual_history(ctx, None, 0, C.byref(rows), C.byref(s)), ctx)
+    out = np.zeros((rows.value, max(s.value, 0)))
+    if rows.value and s.value:
+        _check(lib.pint_residual_history(ctx, _ptr(out), rows.value, C.byref(rows),
+                                         C.byref(s)), ctx)
+    return out
+
+
+def pint_residual_history_reset(ctx):
+    _check(lib.pint_residual_history_reset(ctx), ctx)
+
+
+def pint_bounds_report(ctx):
+    """(count, site, index, bound) of the index checks since the last report;
+    count is -1 when the library was built without them."""
+    c, st, i, b = C.c_longlong(), C.c_int(), C.c_longlong(), C.c_longlong()
+    _check(lib.pint_bounds_report(ctx, C.byref(c), C.byref(st), C.byref(i), C.byref(b)), ctx)
+    return c.value, st.value, i.value, b.value
+
+
+def pint_test_bounds(ctx, index, bound):
+    _check(lib.pint_test_bounds(ctx, int(index), int(bound)), ctx)

@@ -2,6 +2,10 @@
 
 Each translation unit under csrc/ is compiled by nvcc in parallel into
 _build/, then linked into paper_2504_02117_gb300/libpint.so. No cmake.
+build(bounds=True) makes the checked variant libpint_bounds.so (objects in
+_build_bounds/, -DPINT_BOUNDS: matrix index gathers are checked and a bad
+index is recorded instead of used); the package loads it when the
+environment variable PINT_LIB names it.
 """
 from __future__ import annotations
 
@@ -16,6 +20,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpint.so")
+BUILD_BOUNDS = os.path.join(PKG, "_build_bounds")
+LIB_BOUNDS = os.path.join(PKG, "libpint_bounds.so")
 SOURCES = ["api.cu", "spmm.cu", "krylov.cu", "ilu.cu", "fv.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -32,8 +38,8 @@ def flags(extra=()):
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC] + list(extra)
 
 
-def _compile(src, extra, verbose):
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src, extra, verbose, bdir=BUILD):
+    obj = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
@@ -43,37 +49,41 @@ def _compile(src, extra, verbose):
     return obj, r.stderr
 
 
-def _stale(objs):
-    if not os.path.exists(LIB):
+def _stale(objs, lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
         os.path.join(ROOT, "include", "pint.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra=()) -> str:
-    """Compile and link libpint.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and not _stale(None):
-        return LIB
+def build(verbose: bool = False, force: bool = False, extra=(), bounds: bool = False) -> str:
+    """Compile and link libpint.so (or, with bounds=True, the checked
+    libpint_bounds.so); returns its path."""
+    bdir, lib = (BUILD_BOUNDS, LIB_BOUNDS) if bounds else (BUILD, LIB)
+    extra = list(extra) + (["-DPINT_BOUNDS"] if bounds else [])
+    os.makedirs(bdir, exist_ok=True)
+    if not force and not _stale(None, lib):
+        return lib
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra, verbose), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, extra, verbose, bdir), SOURCES))
     objs = [o for o, _ in results]
     if verbose:
         for _, err in results:
             if err.strip():
                 print(err)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
     print(build(verbose=v, force="-f" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [],
+                bounds="--bounds" in sys.argv))

@@ -651,7 +651,81 @@ extern "C" {
 int pint_profile_enable(pint_ctx ctx, int on) {
   if (!ctx) return PINT_ERR_INVALID;
   return guard(ctx, [&] {
-    ctx->prof_on = on != 0;
+    PINT_REQUIRE(on >= 0 && on <= 3, PINT_ERR_INVALID, "profile flags: 0..3");
+    ctx->prof_on = (on & 1) != 0;
+    ctx->nvtx_on = (on & 2) != 0;
+    return PINT_OK;
+  });
+}
+
+int pint_residual_history(pint_ctx ctx, double* out, int max_rows, int* rows, int* s) {
+  if (!ctx) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    PINT_REQUIRE(max_rows >= 0, PINT_ERR_INVALID, "max_rows < 0");
+    const int w = ctx->hist_s;
+    const int nr = w > 0 ? (int)(ctx->hist.size() / w) : 0;
+    if (rows) *rows = nr;
+    if (s) *s = w;
+    if (out && w > 0) {
+      const int k = std::min(nr, max_rows);
+      std::copy(ctx->hist.begin(), ctx->hist.begin() + (size_t)k * w, out);
+    }
+    return PINT_OK;
+  });
+}
+
+namespace {
+// Evaluates one index check of the checked build (site 99) and nothing else:
+// no memory is accessed through the index, in either build.
+__global__ void k_test_bounds(long long i, long long n, int* sink) {
+  if (PINT_INDEX_OK(i, n, 99) && sink) *sink = 1;
+}
+}  // namespace
+
+int pint_test_bounds(pint_ctx ctx, long long index, long long bound) {
+  if (!ctx) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    k_test_bounds<<<1, 1>>>(index, bound, nullptr);
+    check_launch("k_test_bounds");
+    PINT_CUDA(cudaDeviceSynchronize());
+    return PINT_OK;
+  });
+}
+
+int pint_bounds_report(pint_ctx ctx, long long* count, int* site, long long* index,
+                       long long* bound) {
+  if (!ctx) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    PINT_CUDA(cudaDeviceSynchronize());
+#ifdef PINT_BOUNDS
+    unsigned long long rec[3][4];
+    pint_bounds_take(rec[0]);
+    bounds_take_spmm(rec[1]);
+    bounds_take_batch(rec[2]);
+    long long n = 0;
+    int first = -1;
+    for (int t = 0; t < 3; ++t) {
+      n += (long long)rec[t][0];
+      if (first < 0 && rec[t][0] > 0) first = t;
+    }
+    if (count) *count = n;
+    if (site) *site = first >= 0 ? (int)rec[first][1] : 0;
+    if (index) *index = first >= 0 ? (long long)rec[first][2] : 0;
+    if (bound) *bound = first >= 0 ? (long long)rec[first][3] : 0;
+#else
+    if (count) *count = -1;
+    if (site) *site = 0;
+    if (index) *index = 0;
+    if (bound) *bound = 0;
+#endif
+    return PINT_OK;
+  });
+}
+
+int pint_residual_history_reset(pint_ctx ctx) {
+  if (!ctx) return PINT_ERR_INVALID;
+  return guard(ctx, [&] {
+    hist_reset(ctx, 0);
     return PINT_OK;
   });
 }

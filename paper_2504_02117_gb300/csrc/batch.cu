@@ -110,7 +110,8 @@ struct CplLists {
 // products run over the nonzero lists, through a per-thread staging area xs
 // (2 S doubles per thread, stride blockDim.x), in increasing column order.
 template <int S, bool PRE>
-__device__ __noinline__ void coupled_rows(int64_t r0, int64_t r1, const int* __restrict__ rowptr,
+__device__ __noinline__ void coupled_rows(int64_t n, int64_t r0, int64_t r1,
+                                          const int* __restrict__ rowptr,
                                           const int* __restrict__ colind,
                                           const double* __restrict__ Kv,
                                           const double* __restrict__ dg, const CplLists& L,
@@ -127,6 +128,7 @@ __device__ __noinline__ void coupled_rows(int64_t r0, int64_t r1, const int* __r
     const int p1 = rowptr[r + 1];
     for (int p = rowptr[r]; p < p1; ++p) {
       const double v = Kv[p];
+      if (!PINT_INDEX_OK(colind[p], n, 3)) continue;
       const double* xc = X + (int64_t)colind[p] * S;
 #pragma unroll
       for (int k = 0; k < S; ++k) ky[k] = fma(v, __ldcg(xc + k), ky[k]);
@@ -150,13 +152,14 @@ __device__ __noinline__ void coupled_rows(int64_t r0, int64_t r1, const int* __r
 }
 
 template <bool PRE>
-__device__ __forceinline__ void coupled(int s, int64_t r0, int64_t r1, const int* rowptr,
+__device__ __forceinline__ void coupled(int s, int64_t n, int64_t r0, int64_t r1,
+                                        const int* rowptr,
                                         const int* colind, const double* Kv, const double* dg,
                                         const CplLists& L, const double* X, const double* B,
                                         const double* B0, double* out, double* xs) {
   switch (s) {
 #define PINT_CASE(SS) \
-  case SS: coupled_rows<SS, PRE>(r0, r1, rowptr, colind, Kv, dg, L, X, B, B0, out, xs); break;
+  case SS: coupled_rows<SS, PRE>(n, r0, r1, rowptr, colind, Kv, dg, L, X, B, B0, out, xs); break;
     PINT_CASE(1) PINT_CASE(2) PINT_CASE(3) PINT_CASE(4) PINT_CASE(5) PINT_CASE(6)
     PINT_CASE(7) PINT_CASE(8) PINT_CASE(9) PINT_CASE(10) PINT_CASE(11) PINT_CASE(12)
     PINT_CASE(13) PINT_CASE(14) PINT_CASE(15) PINT_CASE(16)
@@ -422,7 +425,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
     for (int64_t e = e0 + tid; e < e1; e += T) Z[e] = 0.0;
     cl.sync();
     // ||F_k|| from the residual of Y = 0
-    coupled<false>(s, r0, r1, J.rowptr, J.colind, J.Kval, J.Mdiag, L, Z, J.B, J.B0, R, xs);
+    coupled<false>(s, n, r0, r1, J.rowptr, J.colind, J.Kval, J.Mdiag, L, Z, J.B, J.B0, R, xs);
     colsq<NW>(s, r0, r1, R, red2);
     PINT_REDUCE(s);
     if (tid < s) fn[tid] = sqrt(res[tid]);
@@ -442,7 +445,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
     for (outer = 0; outer <= max_outer; ++outer) {
       flops += c_res + 2LL * ns;
       PINT_SYNC_ALL();                               // Y rows of every CTA updated
-      coupled<false>(s, r0, r1, J.rowptr, J.colind, J.Kval, J.Mdiag, L, J.Y, J.B, J.B0, R, xs);
+      coupled<false>(s, n, r0, r1, J.rowptr, J.colind, J.Kval, J.Mdiag, L, J.Y, J.B, J.B0, R, xs);
       colsq<NW>(s, r0, r1, R, red2);
       PINT_REDUCE(s);
       if (tid < s) rn[tid] = sqrt(res[tid]);
@@ -479,7 +482,7 @@ k_slab_queue(int njobs, const BatchJob* __restrict__ jobs, int m, double tol, in
         PINT_SYNC_ALL();                             // V_j rows of every CTA written
         const double* Vj = V + (size_t)j * ns;
         double* W = V + (size_t)(j + 1) * ns;
-        coupled<true>(s, r0, r1, J.rowptr, J.colind, Kt, dm, L, Vj, nullptr, nullptr, W, xs);
+        coupled<true>(s, n, r0, r1, J.rowptr, J.colind, Kt, dm, L, Vj, nullptr, nullptr, W, xs);
         __syncthreads();
         double nw2 = 0.0;
         if (mgs) {
@@ -963,3 +966,7 @@ extern "C" int pint_batch_auto_threads(pint_ctx ctx, int njobs, int cluster_ctas
   if (!ctx || njobs < 1 || cluster_ctas < 1) return 0;
   return auto_threads(ctx->num_sms, njobs, cluster_ctas);
 }
+
+namespace pint {
+void bounds_take_batch(unsigned long long* out) { pint_bounds_take(out); }
+}  // namespace pint

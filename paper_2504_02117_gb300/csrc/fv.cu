@@ -536,8 +536,13 @@ static void newton_step(pint_problem p, const double* times, double* Y, const do
   const double f0 = B0 ? ctx->h_small[64] : 0.0;
   const double r0 = ctx->h_small[0];
   const double scale = f0 > 0.0 ? f0 : 1.0;
-  if (stats)
-    for (int k = 0; k < s; ++k) stats->col_relres[k] = ctx->h_small[k] / scale;
+  {
+    double rel[kMaxS];
+    for (int k = 0; k < s; ++k) rel[k] = ctx->h_small[k] / scale;
+    hist_push(ctx, rel, s);
+    if (stats)
+      for (int k = 0; k < s; ++k) stats->col_relres[k] = rel[k];
+  }
   for (int k = 0; k < s; ++k)
     PINT_REQUIRE(std::isfinite(ctx->h_small[k]), PINT_ERR_BREAKDOWN, "non-finite Newton residual");
   if (r0 <= o->tol * scale) {
@@ -825,6 +830,7 @@ int pint_pipeline_run(pint_problem p, const double* A, const double* c, int m, d
   const double t0 = now_ms();
   int newton_total = 0;
   int rc = guard_p(p->ctx, [&] {
+    hist_reset(p->ctx, s);
     PINT_REQUIRE(A && c && y0 && stages_out && m >= 1 && s >= 1 && s <= PINT_MAX_S &&
                      nstages >= 1 && tau > 0.0,
                  PINT_ERR_INVALID, "bad arguments");

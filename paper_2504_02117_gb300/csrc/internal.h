@@ -14,6 +14,8 @@
 
 #include "pint.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace pint {
 
 constexpr int kSellC = 32;          // SELL slice height = warp size
@@ -48,6 +50,41 @@ inline void check_launch(const char* what) {
   if (e != cudaSuccess)
     throw Error{PINT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
 }
+
+// ------------------------------------------------- checked builds
+// With -DPINT_BOUNDS (build.build(bounds=True) makes libpint_bounds.so) an
+// index gathered from a matrix (a CSR or SELL column) is checked against its
+// bound before use. A bad one is counted and the first is recorded as (site,
+// index, bound) in this translation unit's record, and the access is
+// skipped. Without the flag the check is the constant true and compiles
+// away. Sites: 1 coupled residual, 2 SELL SpMM, 3 batched operator rows,
+// 99 the test entry pint_test_bounds.
+#ifdef PINT_BOUNDS
+static __device__ unsigned long long g_pint_bounds[4];   // count, site, index, bound
+__device__ __forceinline__ bool pint_index_ok(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  if (atomicAdd(&g_pint_bounds[0], 1ULL) == 0ULL) {
+    g_pint_bounds[1] = (unsigned long long)site;
+    g_pint_bounds[2] = (unsigned long long)i;
+    g_pint_bounds[3] = (unsigned long long)n;
+  }
+  return false;
+}
+#define PINT_INDEX_OK(i, n, site) ::pint::pint_index_ok((long long)(i), (long long)(n), (site))
+// this translation unit's record (count, site, index, bound), then cleared
+static inline void pint_bounds_take(unsigned long long* out) {
+  cudaMemcpyFromSymbol(out, g_pint_bounds, 4 * sizeof(unsigned long long));
+  const unsigned long long z[4] = {0, 0, 0, 0};
+  cudaMemcpyToSymbol(g_pint_bounds, z, sizeof(z));
+}
+#else
+#define PINT_INDEX_OK(i, n, site) true
+static inline void pint_bounds_take(unsigned long long* out) {
+  out[0] = out[1] = out[2] = out[3] = 0;
+}
+#endif
+void bounds_take_spmm(unsigned long long* out);    // spmm.cu
+void bounds_take_batch(unsigned long long* out);   // batch.cu
 
 // -------------------------------------------------------- device helpers
 template <typename T>
@@ -199,6 +236,11 @@ struct pint_ctx_s {
   long launches = 0;
   // profiler
   bool prof_on = false;
+  bool nvtx_on = false;          // an NVTX range per kernel family launch
+  // relative residual ||R_k|| / ||F_k|| of every column at every outer (or
+  // Newton) iteration since the last reset: rows of hist_s values
+  std::vector<double> hist;
+  int hist_s = 0;
   std::vector<pint::ProfRec> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[pint::PF_COUNT] = {};
@@ -290,13 +332,20 @@ struct ProfScope {
       c->prof_launches[fam] += 1;
       c->prof_bytes[fam] += bytes;
       c->prof_flops[fam] += flops;
+      if (c->nvtx_on) nvtxRangePushA(family_name(fam));
     }
     if (c && c->prof_on) {
       a = take_event();
       cudaEventRecord(a, st);
     }
   }
+  static const char* family_name(int f) {
+    static const char* names[PF_COUNT] = {"coupled", "spmm", "gram",  "update", "cholqr",
+                                          "hess",    "ilu",  "norm",  "vec",    "nl"};
+    return (f >= 0 && f < PF_COUNT) ? names[f] : "other";
+  }
   ~ProfScope() {
+    if (c && c->nvtx_on) nvtxRangePop();
     if (c && c->prof_on && a) {
       cudaEvent_t b = take_event();
       cudaEventRecord(b, st);
@@ -316,6 +365,17 @@ struct ProfScope {
 };
 
 // ----------------------------------------------------------- allocation
+// Residual history: a solve starts a new one; each outer (or Newton)
+// iteration appends its per-column relative residuals.
+inline void hist_reset(pint_ctx ctx, int s) {
+  ctx->hist.clear();
+  ctx->hist_s = s;
+}
+inline void hist_push(pint_ctx ctx, const double* rel, int s) {
+  if (ctx->hist_s != s) hist_reset(ctx, s);
+  if (ctx->hist.size() < (size_t)1 << 22) ctx->hist.insert(ctx->hist.end(), rel, rel + s);
+}
+
 void* dalloc(pint_ctx ctx, size_t bytes);
 void dfree(pint_ctx ctx, void* p, size_t bytes);
 template <typename T>

@@ -1683,6 +1683,7 @@ __global__ void k_rowscale64(int64_t n, int s, const double* __restrict__ X,
 static int solve_global_impl(pint_op op, const double* B, const double* B0, double* Y,
                              const pint_opts* o, pint_stats* stats, cudaStream_t st) {
   pint_ctx ctx = op->ctx;
+  hist_reset(ctx, op->s);
   const double t0 = now_ms();
   const long l0 = ctx->launches;
   PINT_REQUIRE(o->precision == PINT_FP64, PINT_ERR_INVALID,
@@ -1782,8 +1783,13 @@ static int solve_global_impl(pint_op op, const double* B, const double* B0, doub
       if (!std::isfinite(rn[k])) bad = true;
       if (!(rn[k] <= (fn[k] > 0.0 ? o->tol * fn[k] : o->tol))) done = false;
     }
-    if (stats)
-      for (int k = 0; k < s; ++k) stats->col_relres[k] = fn[k] > 0.0 ? rn[k] / fn[k] : rn[k];
+    {
+      double rel[kMaxS];
+      for (int k = 0; k < s; ++k) rel[k] = fn[k] > 0.0 ? rn[k] / fn[k] : rn[k];
+      hist_push(ctx, rel, s);
+      if (stats)
+        for (int k = 0; k < s; ++k) stats->col_relres[k] = rel[k];
+    }
     if (bad) {
       status = PINT_ERR_BREAKDOWN;
       break;
@@ -1885,6 +1891,7 @@ static int solve_global_impl(pint_op op, const double* B, const double* B0, doub
 int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
                      const pint_opts* o, pint_stats* stats, cudaStream_t st) {
   pint_ctx ctx = op->ctx;
+  hist_reset(ctx, op->s);
   const double t0 = now_ms();
   const long l0 = ctx->launches;
   PINT_REQUIRE(op->s >= 1, PINT_ERR_INVALID, "coupling not set (pint_set_coupling)");
@@ -1945,8 +1952,13 @@ int solve_block_impl(pint_op op, const double* B, const double* B0, double* Y,
       const double thr = fn[k] > 0.0 ? o->tol * fn[k] : o->tol;
       if (!(rn[k] <= thr)) done = false;
     }
-    if (stats)
-      for (int k = 0; k < s; ++k) stats->col_relres[k] = fn[k] > 0.0 ? rn[k] / fn[k] : rn[k];
+    {
+      double rel[kMaxS];
+      for (int k = 0; k < s; ++k) rel[k] = fn[k] > 0.0 ? rn[k] / fn[k] : rn[k];
+      hist_push(ctx, rel, s);
+      if (stats)
+        for (int k = 0; k < s; ++k) stats->col_relres[k] = rel[k];
+    }
     if (bad) {
       status = PINT_ERR_BREAKDOWN;
       break;

@@ -201,6 +201,7 @@ k_coupled(int64_t n, int s, const int64_t* __restrict__ sptr, const int* __restr
     for (int t = 0; t < w; ++t) {
       const double v = __ldg(vp + (int64_t)t * 32);
       const int c = __ldg(cpp + (int64_t)t * 32);
+      if (!PINT_INDEX_OK(c, n, 1)) continue;
       double x[S];
       load_row<S, EXACT>(Y + (int64_t)c * s, s, x);
 #pragma unroll
@@ -330,6 +331,7 @@ k_spmm(int64_t n, int s, const int64_t* __restrict__ sptr, const int* __restrict
   for (int t = 0; t < w; ++t) {
     const A v = to_acc(vp[(int64_t)t * 32], A(0));
     const int c = __ldg(cpp + (int64_t)t * 32);
+    if (!PINT_INDEX_OK(c, n, 2)) continue;
     A x[S];
     load_row<S, EXACT>(X + (int64_t)c * s, s, x);
 #pragma unroll
@@ -760,4 +762,8 @@ void launch_step_bound(int precision, int64_t n, int s, const void* X, const dou
   check_launch("k_colmax");
   ctx->launches += 2;
 }
+}  // namespace pint
+
+namespace pint {
+void bounds_take_spmm(unsigned long long* out) { pint_bounds_take(out); }
 }  // namespace pint
