@@ -140,7 +140,11 @@ void pint_opts_default(pint_opts* o);
 
 /* ---------------------------------------------------------------- context */
 /* Create a context on CUDA device `device`. hbm_budget bounds the device
- * bytes the library allocates (0 = 90% of free memory). */
+ * bytes the library allocates (0 = 90% of free memory). The environment
+ * variable PINT_GRAM_FUSE=0, read here, makes the context's block GMRES run
+ * the first update and the second Gram product of block CGS2 as two
+ * launches where it would otherwise fuse them into one pass (float32 inner
+ * solves with s <= 4; same arithmetic, same results; for comparison). */
 int pint_create(pint_ctx* ctx, int device, size_t hbm_budget);
 int pint_destroy(pint_ctx ctx);
 const char* pint_last_error(pint_ctx ctx);

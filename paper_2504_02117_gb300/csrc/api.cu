@@ -4,6 +4,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -219,6 +220,8 @@ int pint_create(pint_ctx* out, int device, size_t budget) {
     size_t fr = 0, tot = 0;
     PINT_CUDA(cudaMemGetInfo(&fr, &tot));
     ctx->budget = budget ? budget : (size_t)(0.9 * (double)fr);
+    const char* fz = std::getenv("PINT_GRAM_FUSE");
+    ctx->gram_fuse = !(fz && fz[0] == '0');
     PINT_CUDA(cudaMallocHost(&ctx->h_flag, 64 * sizeof(int)));
     PINT_CUDA(cudaMallocHost(&ctx->h_small, 4096 * sizeof(double)));
     ctx->d_small = dalloc_n<double>(ctx, kSmallDoubles);

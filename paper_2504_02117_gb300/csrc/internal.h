@@ -237,6 +237,7 @@ struct pint_ctx_s {
   // profiler
   bool prof_on = false;
   bool nvtx_on = false;          // an NVTX range per kernel family launch
+  bool gram_fuse = true;         // block CGS2: first update fused into the second Gram
   // relative residual ||R_k|| / ||F_k|| of every column at every outer (or
   // Newton) iteration since the last reset: rows of hist_s values
   std::vector<double> hist;
@@ -343,6 +344,17 @@ struct ProfScope {
     static const char* names[PF_COUNT] = {"coupled", "spmm", "gram",  "update", "cholqr",
                                           "hess",    "ilu",  "norm",  "vec",    "nl"};
     return (f >= 0 && f < PF_COUNT) ? names[f] : "other";
+  }
+  // nothing was launched in this scope after all: undo the counts
+  void cancel() {
+    if (!c) return;
+    c->prof_launches[fam] -= 1;
+    c->prof_bytes[fam] -= bytes;
+    c->prof_flops[fam] -= flops;
+    if (a) {
+      c->ev_pool.push_back(a);
+      a = nullptr;
+    }
   }
   ~ProfScope() {
     if (c && c->nvtx_on) nvtxRangePop();

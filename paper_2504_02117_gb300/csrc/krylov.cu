@@ -210,11 +210,19 @@ constexpr int kGramMaxStages = 8;
 // CTA-wide barrier separates the tiles. Every wait is bounded (globaltimer);
 // a timeout raises *err, stops the producer and the remaining waits, and the
 // producer drains its copies in flight before the CTA reuses the ring.
-template <typename VT, int S, bool EXACT, int Q, int NQPT, int NT>
+//
+// FUSE: the first update of the second Gram-Schmidt pass is folded in. The
+// kernel receives H1 = [V]^T W of the first pass ((nb*s) x s, float64) and,
+// for every tile, first forms W1 = W - [V] H1 on the tile's rows from the
+// staged blocks (written back to the stage and to Wout, which is W itself:
+// each tile of W is copied in once, before it is overwritten), then takes
+// the products [V]^T W1 of the tile. One pass over the basis instead of two.
+template <typename VT, int S, bool EXACT, int Q, int NQPT, int NT, bool FUSE = false>
 __global__ void __launch_bounds__(NT + 32)
 k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstride,
             const VT* __restrict__ W, int64_t rows_per_cta, int TR, int TRG, int ST,
-            double* __restrict__ partial, int* __restrict__ err) {
+            double* __restrict__ partial, int* __restrict__ err, const double* H1 = nullptr,
+            VT* Wout = nullptr) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kGramMaxStages], empty[kGramMaxStages];
   __shared__ int aborted;
@@ -227,6 +235,14 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
   const int64_t r1 = (r0 + rows_per_cta < n_pad) ? r0 + rows_per_cta : n_pad;
   const int ntiles = r1 > r0 ? (int)((r1 - r0) / TR) : 0;
   const int tid = threadIdx.x;
+  // FUSE: H1 in the vector precision, pitch S, after the ring
+  VT* H1s = reinterpret_cast<VT*>(smem_raw + (((size_t)ST * stage_bytes + 15) & ~(size_t)15));
+  if constexpr (FUSE) {
+    for (int e = tid; e < P * S; e += blockDim.x) {
+      const int p = e / S, k = e - p * S;
+      H1s[e] = (k < s) ? (VT)H1[p * s + k] : VT(0);
+    }
+  }
   if (tid == 0) {
     for (int i = 0; i < ST; ++i) {
       mbar_init(&full[i], 1);
@@ -296,6 +312,47 @@ k_gram_bulk(int64_t n_pad, int s, int nb, const VT* __restrict__ V, int64_t bstr
       const int st = t % ST;
       if (!*(volatile int*)&aborted)
         mbar_wait_bounded(&full[st], (unsigned)((t / ST) & 1), deadline, &aborted, err, 3);
+      if constexpr (FUSE) {
+        // W1 = W - [V] H1 on this tile's rows, a row per consumer thread; the
+        // products below read the updated rows after the consumers' barrier,
+        // which every consumer thread reaches once per tile whatever happened
+        if (!*(volatile int*)&aborted) {
+          VT* Tm = reinterpret_cast<VT*>(smem_raw + (size_t)st * stage_bytes);
+          VT* Wm = reinterpret_cast<VT*>(smem_raw + (size_t)st * stage_bytes +
+                                         (size_t)nb * blk_pitch);
+          const int64_t row0 = r0 + (int64_t)t * TR;
+          for (int rr = tid; rr < TR; rr += NT) {
+            VT acc[S];
+#pragma unroll
+            for (int k = 0; k < S; ++k) acc[k] = VT(0);
+            for (int b = 0; b < nb; ++b) {
+              VT v[S];
+              const VT* vr = Tm + (size_t)b * (blk_pitch / sizeof(VT)) + rr * s;
+              if constexpr (EXACT) {
+                lds_q<VT, S>(vr, v);
+              } else {
+#pragma unroll
+                for (int i = 0; i < S; ++i) v[i] = i < s ? vr[i] : VT(0);
+              }
+              const VT* hb = H1s + b * s * S;
+#pragma unroll
+              for (int i = 0; i < S; ++i) {
+                if (!EXACT && i >= s) break;
+#pragma unroll
+                for (int k = 0; k < S; ++k) acc[k] = fma(v[i], hb[i * S + k], acc[k]);
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+              if (!EXACT && k >= s) break;
+              const VT w1 = Wm[rr * s + k] - acc[k];
+              Wm[rr * s + k] = w1;
+              Wout[(row0 + rr) * s + k] = w1;
+            }
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+      }
       if (active && !*(volatile int*)&aborted) {
         const VT* T = reinterpret_cast<const VT*>(smem_raw + (size_t)st * stage_bytes);
         const VT* Wt = reinterpret_cast<const VT*>(smem_raw + (size_t)st * stage_bytes +
@@ -409,11 +466,18 @@ static void ensure_partial(pint_ctx ctx, size_t bytes) {
   ctx->partial_bytes = bytes;
 }
 
+// H = [V]^T W by k_gram_bulk; with H1 != nullptr the fused form: W <- W -
+// [V] H1 first (in place), then H = [V]^T W of the updated W. Returns false,
+// launching nothing, when the bulk path does not apply.
 template <typename VT>
 static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V, int64_t bstride,
-                        const VT* W, double* H, cudaStream_t st) {
+                        const VT* W, double* H, cudaStream_t st, const double* H1 = nullptr,
+                        VT* Wout = nullptr) {
   const int P = nb * s;
   const size_t es = sizeof(VT);
+  const bool fuse = H1 != nullptr;
+  // FUSE stages H1 (P x S in the vector precision) after the ring
+  const size_t h1_bytes = fuse ? es * (size_t)P * 16 + 16 : 0;
   if (n_pad % 64 != 0 || (bstride * es) % 16 != 0 ||
       reinterpret_cast<uintptr_t>(V) % 16 != 0 || reinterpret_cast<uintptr_t>(W) % 16 != 0)
     return false;
@@ -425,7 +489,9 @@ static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V,
   while (TR > 4 && (stage_of(TR) > 66 * 1024 || n_pad % TR != 0)) TR >>= 1;
   if (stage_of(TR) > 66 * 1024 || n_pad % TR != 0) return false;
   const size_t stage_bytes = stage_of(TR);
-  const int STG = (int)std::max<size_t>(2, std::min<size_t>(kGramMaxStages, (210 * 1024) / stage_bytes));
+  if (2 * stage_bytes + h1_bytes > 210 * 1024) return false;
+  const int STG = (int)std::max<size_t>(
+      2, std::min<size_t>(kGramMaxStages, (210 * 1024 - h1_bytes) / stage_bytes));
   const int E = P * s;
   bool ok = true;
   with_s(s, [&](auto S_, auto E_) {
@@ -438,7 +504,7 @@ static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V,
     const int qs = (NQ + npt - 1) / npt;
     int TRG = std::max(1, std::min(64, NT / qs));
     while (TRG > 1 && (size_t)TRG * E * 8 > 210 * 1024) TRG >>= 1;
-    const size_t smem = std::max((size_t)STG * stage_bytes, (size_t)TRG * E * 8);
+    const size_t smem = std::max((size_t)STG * stage_bytes + h1_bytes, (size_t)TRG * E * 8);
     if (smem > 210 * 1024 || NQ > 1024) {
       ok = false;
       return;
@@ -454,16 +520,30 @@ static bool gram_bulk_t(pint_ctx ctx, int64_t n_pad, int s, int nb, const VT* V,
       const int nblk = (int)((n_pad + rpc - 1) / rpc);
       ensure_partial(ctx, sizeof(double) * (size_t)nblk * E);
       kern<<<nblk, NT + 32, smem, st>>>(n_pad, s, nb, V, bstride, W, rpc, TR, TRG, STG,
-                                        ctx->d_partial, ctx->d_flag);
+                                        ctx->d_partial, ctx->d_flag, H1, Wout);
       check_launch("k_gram_bulk");
       k_gram_reduce_launch(E, nblk, ctx->d_partial, H, st);
       check_launch("k_gram_reduce");
     };
     // with Q = 4 there are at most 256 quads (P <= 1024): one per thread
-    if constexpr (Q == 4) launch(k_gram_bulk<VT, S, EX, Q, 1, NT>);
-    else if (npt == 1) launch(k_gram_bulk<VT, S, EX, Q, 1, NT>);
-    else if (npt == 2) launch(k_gram_bulk<VT, S, EX, Q, 2, NT>);
-    else launch(k_gram_bulk<VT, S, EX, Q, 4, NT>);
+    if (fuse) {
+      // float64 at s = 16 keeps the separate launches: the update's row and
+      // the products' accumulators do not fit in registers together
+      if constexpr (sizeof(VT) == 8 && S == 16) {
+        ok = false;
+        return;
+      } else {
+        if constexpr (Q == 4) launch(k_gram_bulk<VT, S, EX, Q, 1, NT, true>);
+        else if (npt == 1) launch(k_gram_bulk<VT, S, EX, Q, 1, NT, true>);
+        else if (npt == 2) launch(k_gram_bulk<VT, S, EX, Q, 2, NT, true>);
+        else launch(k_gram_bulk<VT, S, EX, Q, 4, NT, true>);
+      }
+    } else {
+      if constexpr (Q == 4) launch(k_gram_bulk<VT, S, EX, Q, 1, NT>);
+      else if (npt == 1) launch(k_gram_bulk<VT, S, EX, Q, 1, NT>);
+      else if (npt == 2) launch(k_gram_bulk<VT, S, EX, Q, 2, NT>);
+      else launch(k_gram_bulk<VT, S, EX, Q, 4, NT>);
+    }
   });
   if (!ok) return false;
   ctx->launches += 2;
@@ -591,6 +671,37 @@ void launch_update(pint_ctx ctx, int precision, int64_t n, int s, int nb, const 
     update_t<double>(ctx, n, s, nb, (const double*)V, bstride, H, (double*)W, mode, st);
   else
     update_t<float>(ctx, n, s, nb, (const float*)V, bstride, H, (float*)W, mode, st);
+}
+
+// W <- W - [V] H1, then H2 = [V]^T W: the first update and the second Gram
+// product of block CGS2, in one pass over the basis (k_gram_bulk<...,
+// FUSE>) for float32 blocks of width s <= 4 on the bulk Gram path, else as
+// the two separate launches. Measured at 128^3 (whole slab solves, float32
+// inner): the fused pass gains 4, 3 and 2.6 % at s = 1, 2, 4 and loses
+// 0.4 % at s = 8, 5 % at s = 16 and 12 % in float64 at s = 8: its update
+// phase runs one row per thread on the eight consumer warps, serialised with
+// the products by a barrier, which the saved read of the basis pays for only
+// while s is small.
+template <typename VT>
+static void update_gram_t(pint_ctx ctx, int64_t n, int s, int nb, const VT* V, int64_t bstride,
+                          const double* H1, VT* W, double* H2, cudaStream_t st, int64_t n_pad) {
+  if (n_pad > 0 && ctx->gram_fuse && sizeof(VT) == 4 && s <= 4) {
+    ProfScope ps(ctx, PF_GRAM, sizeof(VT) * (double)(nb + 2) * n * s, 4.0 * n * nb * s * s, st);
+    if (gram_bulk_t<VT>(ctx, n_pad, s, nb, V, bstride, W, H2, st, H1, W)) return;
+    ps.cancel();
+  }
+  update_t<VT>(ctx, n, s, nb, V, bstride, H1, W, 0, st);
+  gram_t<VT>(ctx, n, s, nb, V, bstride, W, H2, st, PF_GRAM, n_pad);
+}
+
+void launch_update_gram(pint_ctx ctx, int precision, int64_t n, int s, int nb, const void* V,
+                        int64_t bstride, const double* H1, void* W, double* H2, cudaStream_t st,
+                        int64_t n_pad) {
+  if (precision == PINT_FP64)
+    update_gram_t<double>(ctx, n, s, nb, (const double*)V, bstride, H1, (double*)W, H2, st,
+                          n_pad);
+  else
+    update_gram_t<float>(ctx, n, s, nb, (const float*)V, bstride, H1, (float*)W, H2, st, n_pad);
 }
 
 // ------------------------------------------------------------ CholQR (a7)
@@ -1153,8 +1264,7 @@ static InnerResult gmres(pint_op op, const pint_opts* o, KrylovWork* w, cudaStre
       launch_inner_spmm(op, prec, jac, Vb(j), Vb(j + 1), nullptr, sx);
     }
     launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg1, sx, np);
-    launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg1, Vb(j + 1), 0, sx);
-    launch_gram(ctx, vprec, n, s, j + 1, w->V, bs, Vb(j + 1), w->Hg2, sx, np);
+    launch_update_gram(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg1, Vb(j + 1), w->Hg2, sx, np);
     launch_update(ctx, vprec, n, s, j + 1, w->V, bs, w->Hg2, Vb(j + 1), 0, sx);
     cholqr2(ctx, vprec, n, s, Vb(j + 1), w->Rn, w->defl, sx, np);
     ProfScope psh(ctx, PF_HESS, 0.0, 4.0 * (j + 1) * s * s * (s + 1), sx);

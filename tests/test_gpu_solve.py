@@ -392,3 +392,36 @@ def test_slab_global_gmres_tiny_grid_with_b0_against_dense(P, ctx):
         assert ei.value.code == P.PINT_ERR_INVALID
     finally:
         P.pint_operator_destroy(op)
+
+
+@pytest.mark.parametrize("s", [2, 4])
+def test_fused_update_gram_equals_the_separate_launches(P, s):
+    """Block CGS2 with the first update fused into the second Gram pass (the
+    default for float32 inner solves at s <= 4) gives bitwise the solution
+    and the step counts of the two separate launches (a context created with
+    PINT_GRAM_FUSE=0), on the bulk Gram path (a grid operator, 24^3)."""
+    import os
+    import torch
+    out = []
+    for fuse in ("1", "0"):
+        os.environ["PINT_GRAM_FUSE"] = fuse
+        try:
+            c = P.pint_create(0)
+        finally:
+            os.environ.pop("PINT_GRAM_FUSE", None)
+        try:
+            op, K, n, A, A1, A2, B = _setup(P, c, (24, 24, 24), s, 1e-3, seed=41)
+            try:
+                o = P.pint_opts_default()
+                o.precision = P.PINT_FP32
+                o.precond = P.PINT_PC_ILU0
+                Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
+                st = P.pint_solve_block(c, op, _dev(B), None, Y, o,
+                                        raise_on_nonconvergence=True)
+                out.append((Y.cpu().numpy(), st.inner_its, st.outer_its))
+            finally:
+                P.pint_operator_destroy(op)
+        finally:
+            P.pint_destroy(c)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
