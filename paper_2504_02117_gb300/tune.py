@@ -15,6 +15,12 @@ and the device.
 
 The measurement is a callable candidate -> dict(value, converged, ...), so
 the search itself runs without a GPU; `slab_measure` builds the GPU one.
+
+The same search picks the launch shape of the batched persistent solver
+(`BatchShape`: CTAs per cluster and threads per CTA) for a given set of jobs:
+`batch_measure` times one run of a resident plan per shape. The library's own
+rule (pint_batch_auto_cluster / _threads) is fitted to such sweeps; the
+autotuner measures the job set at hand instead.
 """
 from __future__ import annotations
 
@@ -41,6 +47,25 @@ class Candidate:
 
     def key(self) -> str:
         return f"s{self.s}_{self.solver}_{self.precision}_m{self.restart}"
+
+
+@dataclasses.dataclass(frozen=True)
+class BatchShape:
+    cluster_ctas: int             # CTAs per cluster (one job per cluster at a time)
+    cta_threads: int = 512        # threads per CTA
+
+    def __post_init__(self):
+        if not 1 <= self.cluster_ctas <= 16 or self.cta_threads not in (128, 256, 512):
+            raise ValueError(f"invalid batch shape {self}")
+
+    def key(self) -> str:
+        return f"c{self.cluster_ctas}_t{self.cta_threads}"
+
+
+def batch_shapes(clusters: Iterable[int] = (1, 2, 4, 8, 16),
+                 threads: Iterable[int] = (512, 256)) -> list:
+    """All combinations, clusters innermost."""
+    return [BatchShape(c, t) for t in threads for c in clusters]
 
 
 def grid(widths: Iterable[int] = (1, 2, 4, 8, 16), solvers: Iterable[str] = ("gmres", "bicgstab"),
@@ -101,10 +126,27 @@ class TuneCache:
 
     def get(self, key: str) -> Optional[Candidate]:
         e = self.data.get(key)
-        return Candidate(**e["candidate"]) if e else None
+        return Candidate(**e["candidate"]) if e and "candidate" in e else None
 
     def put(self, key: str, cand: Candidate, value: float):
         self.data[key] = {"candidate": dataclasses.asdict(cand), "value": float(value)}
+        self._write()
+
+    @staticmethod
+    def batch_key(sizes, device: str) -> str:
+        """A batch by its jobs' N s values (count, total, largest)."""
+        sizes = [int(x) for x in sizes]
+        return f"batch_{len(sizes)}jobs_sum{sum(sizes)}_max{max(sizes)}_{device}"
+
+    def get_batch(self, key: str) -> Optional[BatchShape]:
+        e = self.data.get(key)
+        return BatchShape(**e["shape"]) if e and "shape" in e else None
+
+    def put_batch(self, key: str, shape: BatchShape, value: float):
+        self.data[key] = {"shape": dataclasses.asdict(shape), "value": float(value)}
+        self._write()
+
+    def _write(self):
         tmp = self.path + ".tmp"
         with open(tmp, "w") as fh:
             json.dump(self.data, fh, indent=1, sort_keys=True)
@@ -172,5 +214,47 @@ def slab_measure(ctx, dims, D, velocity, tau: float, rhs: Callable[[int], object
                     "inner": st.inner_its}
         finally:
             P.pint_operator_destroy(op)
+
+    return measure
+
+
+def batch_measure(ctx, jobs, opts, work):
+    """The GPU measurement of a batch launch shape. jobs: (op, B, B0, Y)
+    device tensors as for pint_solve_batch; work: the batch's time steps x
+    cells (sum of N s). Per shape: a resident plan, one warm-up run, one run
+    timed with CUDA events on the current stream, every Y reset to zero
+    before each run; value = work / seconds. A shape the device cannot make
+    resident, or a job that does not converge, counts as not converged."""
+    import torch
+
+    import paper_2504_02117_gb300 as P
+
+    def reset():
+        for _, _, _, Y in jobs:
+            Y.zero_()
+
+    def measure(shape: BatchShape) -> dict:
+        try:
+            plan = P.BatchPlan(ctx, jobs, opts, cluster_ctas=shape.cluster_ctas,
+                               cta_threads=shape.cta_threads)
+        except P.PintError as err:
+            return {"value": 0.0, "converged": False, "status": err.code, "error": str(err)}
+        try:
+            reset()
+            plan.run()
+            reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            sts = plan.run()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            ok = all(x.status == P.PINT_OK for x in sts)
+            return {"value": work / (ms / 1e3), "converged": ok, "ms": ms,
+                    "inner": sum(x.inner_its for x in sts), "shape": plan.shape()}
+        finally:
+            plan.close()
 
     return measure

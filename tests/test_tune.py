@@ -73,3 +73,29 @@ def test_cache_round_trip(tmp_path):
 def test_inner_tolerance_follows_the_slab_readings():
     assert tune.inner_tol(8, "fp32") == 1e-2 and tune.inner_tol(2, "fp64") == 1e-2
     assert tune.inner_tol(1, "fp64") == 1e-10 and tune.inner_tol(1, "fp32") == 1e-5
+
+
+def test_batch_shape_search_and_cache(tmp_path):
+    """The same search over batched launch shapes: the fastest converging
+    shape wins, a shape that cannot run (not converged) never does, and the
+    choice survives the cache under the batch's key."""
+    vals = {(1, 512): 2.7e7, (2, 512): 3.4e7, (4, 512): 4.7e7, (8, 512): 3.9e7,
+            (16, 512): 2.0e7, (4, 256): 4.1e7}
+
+    def measure(sh):
+        k = (sh.cluster_ctas, sh.cta_threads)
+        return {"value": vals.get(k, 0.0), "converged": k in vals}
+    shapes = tune.batch_shapes((1, 2, 4, 8, 16), (512, 256))
+    assert len(shapes) == 10 and shapes[0] == tune.BatchShape(1, 512)
+    best, table = tune.autotune(measure, shapes, repeats=2)
+    assert best == tune.BatchShape(4, 512)
+    assert not any(e["converged"] for e in table if e["candidate"] == tune.BatchShape(16, 256))
+    cache = tune.TuneCache(str(tmp_path / "t.json"))
+    key = tune.TuneCache.batch_key([4096 * 4] * 8 + [32 ** 3 * 16], "gpu0")
+    cache.put_batch(key, best, table[0]["value"])
+    again = tune.TuneCache(cache.path)
+    assert again.get_batch(key) == best and again.get(key) is None
+    with pytest.raises(ValueError):
+        tune.BatchShape(17)
+    with pytest.raises(ValueError):
+        tune.BatchShape(2, 384)
