@@ -435,13 +435,15 @@ k_ilu_rows(TileGeom g, int s, const VT* __restrict__ C4, const VT* X, VT* Z,
         for (int li = 0; li < TX; ++li)
           if (li < ex) Z[(lbase + li) * s + c] = zv[li];
       }
-      // every face store of the CTA happens-before thread 0's fence and
-      // release through the barrier (which also ends all reads of Ys)
+      // every face store of the CTA precedes thread 0's release store in
+      // causality order through the barrier (which also ends all reads of
+      // Ys): the barrier synchronises the storing threads with thread 0, and
+      // a gpu-scope release is cumulative, so the downstream CTA that
+      // acquires the flag reads the faces without a separate fence (a
+      // __threadfence before the release cost 6.5 % of the 128^3 s = 8
+      // float32 apply, 684 -> 640 us, with bitwise equal results)
       __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(tflags + tile, epoch);
-      }
+      if (threadIdx.x == 0) st_release(tflags + tile, epoch);
       if (mine && !face) {
 #pragma unroll
         for (int li = 0; li < TX; ++li)
