@@ -128,3 +128,47 @@ def test_sweep_summary_ratios():
     sm = bench.sweep_summary(rows)
     assert sm["fp32"] == {"s8_over_s1": 3.5, "best_s": 8, "best_over_s1": 3.5}
     assert sm["fp64"]["s8_over_s1"] == 0.5 and sm["fp64"]["best_s"] == 1
+
+
+def test_batch_workload_and_solver_options():
+    """The batch workload and the batched solver force float64 and Jacobi
+    (the batched kernel's method), name their workloads, and default to the
+    512-slab mix of the seeded generator."""
+    a = bench.parse(["--workload", "batch"])
+    assert (a.solver, a.precision, a.precond, a.requests) == ("batch", "fp64", "jacobi", 512)
+    assert bench.linear(a)
+    b = bench.parse(["--workload", "convdiff2d", "--solver", "batch", "--precision", "fp32",
+                     "--precond", "ilu0"])
+    assert (b.precision, b.precond) == ("fp64", "jacobi")
+    assert bench.solver_label(b).startswith("global GMRES(30)")
+    r = bench.parse(["--workload", "richards", "--linearisation", "newton"])
+    assert r.linearisation == "newton"
+    import synth
+    jobs = synth.batch_jobs(7, 512)
+    assert len(jobs) == 512 and {j["s"] for j in jobs} == {2, 4, 8, 16}
+    assert all(j["dims"][2] == 1 or j["dims"][0] == j["dims"][2] for j in jobs)
+    assert synth.batch_jobs(7, 512) == jobs                  # seeded
+    assert bench.batch_velocity((16, 16, 16)) == (1.0, 0.5, 0.25)
+    assert bench.batch_velocity((32, 32, 1)) == (1.0, 0.5, 0.0)
+
+
+class _St:
+    def __init__(self, status, outer, inner, restarts, rel, flops, ms=2.0):
+        self.status, self.outer_its, self.inner_its, self.restarts = status, outer, inner, restarts
+        self.col_relres = rel + [0.0] * (16 - len(rel))
+        self.flops, self.solve_ms = flops, ms
+
+
+def test_batch_aggregate_and_float64_roofline():
+    """A batch's statistics: worst status and residual, summed steps and
+    operations; the roofline divides the kernel's counted float64
+    operations by the step time and compares them with the measured rate."""
+    agg = bench._AggStats([_St(0, 3, 90, 4, [1e-11, 2e-11], 2e8),
+                           _St(4, 5, 30, 2, [3e-9], 1e8)]).as_dict()
+    assert agg["status"] == 4 and agg["outer_its"] == 5 and agg["inner_its"] == 120
+    assert agg["restarts"] == 6 and agg["flops"] == 3e8 and agg["col_relres"] == [3e-9]
+    assert agg["max_inner_its"] == 90
+    rl = bench.batch_roofline([agg], 0.5, 1.0)          # 3e8 flops in 0.5 ms
+    assert rl["bound"] == "alu" and rl["unit"] == "TFLOP/s"
+    assert rl["achieved"] == pytest.approx(0.6) and rl["frac"] == pytest.approx(0.6)
+    assert bench.batch_roofline([{"flops": 0.0}], 0.5, 1.0) is None
