@@ -97,7 +97,9 @@ def parse(argv=None):
                    help="skip the s = 1..16 sweep (one timed solve per s and precision)")
     p.add_argument("--requests", type=int, default=512,
                    help="serve: requests in the stream; batch: slabs in the launch")
-    p.add_argument("--rate", type=float, default=8.0, help="serve: mean arrivals per second")
+    p.add_argument("--rate", type=float, default=4.0,
+                   help="serve: mean arrivals per second (512 requests at 8/s arrive faster "
+                        "than one GB300 serves them, about 5.4/s)")
     p.add_argument("--slots", type=int, default=4, help="serve: concurrent solves")
     p.add_argument("--batch-cluster", type=int, default=0,
                    help="batched kernel: CTAs per cluster (0 = the library's choice)")
