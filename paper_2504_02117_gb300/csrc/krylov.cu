@@ -620,6 +620,9 @@ k_update(int64_t n, int s, int nb, const VT* __restrict__ V, int64_t bstride,
     VT acc[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) acc[k] = VT(0);
+    // unrolled so that the loads of later blocks issue ahead of this block's
+    // FMAs (5.44 -> 5.57 TB/s at 128^3, s = 8, float32)
+#pragma unroll 4
     for (int b = 0; b < nb; ++b) {
       VT v[S];
       load_row<S, EXACT>(V + (int64_t)b * bstride + r * s, s, v);
