@@ -912,11 +912,13 @@ def main():
 def other_configs(P, ctx, fp64_peak, steps):
     """Compact legs of the other configurations, measured in the same run as
     the headline (each: set-up and one warm-up untimed, then `steps` timed
-    steps with CUDA events): the 64 x 64 slab through the batched kernel (one
-    cluster), 512 uneven slabs in one batched launch, and the 512^2
-    diffusion-reaction run of Algorithm 1."""
+    steps with CUDA events): the headline slab with block BiCGStab inner
+    solves (the paper's solver for this problem), the 64 x 64 slab through
+    the batched kernel (one cluster), 512 uneven slabs in one batched launch,
+    and the 512^2 diffusion-reaction run of Algorithm 1."""
     import torch
     legs = {
+        "convdiff3d_128_s8_bicgstab_fp32": ["--workload", "convdiff3d", "--solver", "bicgstab"],
         "convdiff2d_64_s4_batch_kernel": ["--workload", "convdiff2d", "--solver", "batch"],
         "batch_512_slabs": ["--workload", "batch", "--requests", "512"],
         "diffreact_512_fp32": ["--workload", "diffreact"],
