@@ -323,3 +323,37 @@ def test_batch_plan_replays_the_captured_graph(P, ctx, cluster, threads):
         assert ei.value.code == P.PINT_ERR_INVALID
     finally:
         _free(P, jobs)
+
+
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_batch_operation_count_follows_its_definition(P, ctx, cluster):
+    """pint_stats.flops of a job equals the algorithmic float64 count of the
+    batched method written out (FMA = 2): one GMRES(m) cycle that cannot
+    converge (tol 1e-300, max_outer 1) takes exactly m steps; the count adds
+    the per-job set-up, three residuals with their column norms, the cycle's
+    start, m Arnoldi steps (modified Gram-Schmidt with one CTA per job: 4(j+1)
+    N s per step; two classical passes on a cluster: 8(j+1) N s) and the
+    correction."""
+    import torch
+    jobs = _make(P, ctx, [((20, 18, 1), 4)], seed0=230)
+    try:
+        j = jobs[0]
+        n, s, m = j["n"], j["s"], 6
+        o = _opts(P, 1e-300)
+        o.max_outer = 1
+        o.restart = m
+        Y = torch.zeros(n, s, device="cuda", dtype=torch.float64)
+        st = P.pint_solve_batch(ctx, [(j["op"], _dev(j["B"]), None, Y)], o,
+                                cluster_ctas=cluster)[0]
+        assert (st.outer_its, st.inner_its, st.restarts) == (1, m, 1)
+        nnz = int(P.pint_operator_nnz(j["op"]))
+        nA = int(np.count_nonzero(j["A1"]) + np.count_nonzero(j["A2"]))
+        ns = n * s
+        c_pre = 2 * nnz * s + 2 * n * nA + 2 * ns
+        c_res = c_pre + ns                                # B given, no B0
+        k = 4 if cluster == 1 else 8
+        steps = sum(c_pre + k * (i + 1) * ns + 3 * ns for i in range(m))
+        want = (nnz + n) + 3 * (c_res + 2 * ns) + ns + steps + 2 * m * ns + 2 * ns
+        assert st.flops == want
+    finally:
+        _free(P, jobs)
