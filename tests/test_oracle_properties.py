@@ -107,3 +107,29 @@ def test_slab_equals_sequential_stepping_for_random_slabs(s, seed):
     Ys = slab.sequential_dirk_linear(K, np.ones(n), A, tau, np.zeros(n), B)
     assert info["converged"]
     np.testing.assert_allclose(Y, Ys, rtol=1e-9, atol=1e-12)
+
+
+@settings(**SETTINGS)
+@given(s=st.integers(1, 5), seed=st.integers(0, 2 ** 31 - 1), mgs=st.booleans(),
+       pc=st.sampled_from(["none", "jacobi"]), nx=st.integers(2, 5), ny=st.integers(1, 4))
+def test_global_gmres_reaches_the_dense_solution_with_either_orthogonalisation(
+        s, seed, mgs, pc, nx, ny):
+    """Global GMRES on the unsplit operator, with modified or two classical
+    Gram-Schmidt passes, solves random small slabs (random log-normal
+    diffusion, random velocity, theta-method coupling with its first stage
+    eliminated, random B and B0) to the dense all-at-once solution."""
+    rng = np.random.default_rng(seed)
+    dims = (nx, ny, 2)
+    n = nx * ny * 2
+    D = np.exp(rng.standard_normal(n)).reshape(dims[::-1])
+    K = fv.convdiff_matrix(dims, D, tuple(rng.uniform(0.0, 3.0, 3)))
+    A, _, _ = coupling.theta_method(0.5)
+    A1, A2, _ = coupling.multistep_matrices(A, s, 1e-2, eliminate_first=True)
+    B = rng.standard_normal((n, s))
+    B0 = rng.standard_normal((n, s))
+    Y, info = slab.slab_solve_global(K, np.ones(n), A1, A2, B, B0, tol=1e-12, precond=pc,
+                                     restart=8, ortho="mgs" if mgs else "cgs2")
+    assert info["converged"]
+    Yd = slab.solve_all_at_once_dense(K, np.ones(n), A1, A2, B, B0)
+    err = np.linalg.norm(Y - Yd, axis=0) / np.linalg.norm(Yd, axis=0)
+    assert np.all(err < 1e-9), err
